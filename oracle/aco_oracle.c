@@ -1,0 +1,433 @@
+/*
+ * CPU oracle for the Ant System on the symmetric TSP (Cecilia et al.,
+ * "Parallelization Strategies for Ant Colony Optimisation on GPUs").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The CUDA
+ * path shares no code with it: nothing here is included by, linked into or
+ * generated for the kernels, and nothing here reads anything the kernels wrote.
+ *
+ * It is deliberately plain and slow: single-threaded loops over cities and
+ * ants, in the order the paper states the algorithm (Section II):
+ *
+ *   repeat:  choice_info = tau^alpha * eta^beta          (Section III-A, "choice kernel")
+ *            every ant builds a tour with Eq. 1          (Section II)
+ *            tau <- (1 - rho) tau                        (Eq. 2)
+ *            tau <- tau + sum_k dtau^k, dtau^k = 1/C^k   (Eqs. 3-4)
+ *
+ * Two arithmetic modes:
+ *  - "mirror" (FP32 state, the precision the benchmark configurations fix):
+ *    tau, eta^beta and choice_info are float, the deposit is summed exactly in
+ *    64-bit fixed point and rounded once.  Every value is a fixed function of
+ *    the inputs, so this mode is reproducible bit for bit by any correct
+ *    implementation that follows the same readings.
+ *  - "fp64": the pheromone recurrence of Eqs. 2-4 evaluated in double
+ *    precision on the same tours, the reference for the 1e-5 relative
+ *    tolerance on tau.
+ *
+ * Readings of points the paper leaves open (all written out where used):
+ *  R1 random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+ *     seed, counter = (step, ant, iteration, 0).  Step 0 places the ant:
+ *     start = floor(x0 * n / 2^32) ("ants are randomly placed", Section II).
+ *     Step s >= 1 draws r = x1 * 2^32 + x0.
+ *  R2 Eq. 1 is sampled by an exact integer roulette: with M the largest weight
+ *     among unvisited cities and B = 62 - ceil(log2 n), each unvisited weight
+ *     w_j becomes q_j = floor(w_j * 2^(B-1-ilogb M)); Q = sum q_j; the target is
+ *     T = floor(r * Q / 2^64); the chosen city is the first j (ascending index)
+ *     whose inclusive prefix sum of q exceeds T.  P(j) = q_j / Q.  If M = 0
+ *     the lowest-index unvisited city is taken.
+ *  R3 eta_ij^beta = 1 / d_ij^beta computed in double and rounded to float; for
+ *     beta in {1,2,3} d^beta is formed by exact integer-valued products, for
+ *     other beta with pow().  The diagonal gets 0.
+ *  R4 tau0 = m / C_nn with C_nn the nearest-neighbour tour from city 0 (ties to
+ *     the lowest index); tau_ii = 0.
+ *  R5 dtau^k = (float)(1 / (double)C^k), added to both (a,b) and (b,a).  In
+ *     mirror mode each dtau^k becomes q_k = floor(dtau^k * 2^S) with
+ *     S = 62 - ceil(log2 m) - ilogb(max_k dtau^k); the per-cell sum of q_k is
+ *     exact, converted to float once (round to nearest) and scaled by 2^-S.
+ *     tau' = fl(fl((1-rho) tau) + dep).
+ *  R6 choice = tau * eta^beta for alpha = 1, eta^beta for alpha = 0, and
+ *     powf(tau, alpha) * eta^beta otherwise.
+ *  R7 the best-so-far tour is replaced only by a strictly shorter one; within
+ *     an iteration the lowest ant index wins ties.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared -lm.
+ * -ffp-contract=off matters: a fused multiply-add would change the rounding of
+ * fl(fl(a*b)+c).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from the published description (Salmon et al., SC'11):     */
+/* ten rounds of the 4x32 S-box with multipliers 0xD2511F53 and 0xCD9E8D57,  */
+/* key schedule bumped by the Weyl constants 0x9E3779B9 and 0xBB67AE85       */
+/* between rounds.                                                           */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        uint32_t n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* Philox words for (seed, step, ant, iteration) under reading R1. */
+static void draw(uint64_t seed, uint32_t step, uint32_t ant, uint32_t iteration, uint32_t x[4])
+{
+    uint32_t ctr[4] = {step, ant, iteration, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, x);
+}
+
+/* Smallest c with 2^c >= v (v >= 1). */
+int orc_ceil_log2(int64_t v)
+{
+    int c = 0;
+    while (((int64_t)1 << c) < v) ++c;
+    return c;
+}
+
+/* Unbiased binary exponent of a positive finite float (subnormals included). */
+static int exponent_of(float x)
+{
+    int e;
+    (void)frexp((double)x, &e); /* x = f * 2^e, f in [0.5, 1) */
+    return e - 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. 1 by the integer roulette of reading R2.                               */
+/* w: weights of row i (n entries), visited: 1 for cities in the tabu list.  */
+/* Returns the chosen city, or -1 if every city is visited.                  */
+/* ------------------------------------------------------------------------- */
+int orc_roulette(int n, const float *w, const uint8_t *visited, uint64_t r)
+{
+    float M = 0.0f;
+    int first_unvisited = -1;
+    for (int j = 0; j < n; ++j) {
+        if (visited[j]) continue;
+        if (first_unvisited < 0) first_unvisited = j;
+        if (w[j] > M) M = w[j];
+    }
+    if (first_unvisited < 0) return -1;
+    if (M == 0.0f) return first_unvisited;
+
+    int B = 62 - orc_ceil_log2(n);
+    int scale = B - 1 - exponent_of(M);
+    uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    uint64_t Q = 0;
+    for (int j = 0; j < n; ++j) {
+        q[j] = visited[j] ? 0u : (uint64_t)floor(ldexp((double)w[j], scale));
+        Q += q[j];
+    }
+    uint64_t T = (uint64_t)(((unsigned __int128)r * (unsigned __int128)Q) >> 64);
+    uint64_t prefix = 0;
+    int chosen = -1;
+    for (int j = 0; j < n; ++j) {
+        prefix += q[j];
+        if (prefix > T) { chosen = j; break; }
+    }
+    free(q);
+    return chosen;
+}
+
+/* Exposed for tests: the quantised weights q_j and their sum Q of reading R2. */
+uint64_t orc_roulette_weights(int n, const float *w, const uint8_t *visited, uint64_t *q)
+{
+    float M = 0.0f;
+    for (int j = 0; j < n; ++j)
+        if (!visited[j] && w[j] > M) M = w[j];
+    uint64_t Q = 0;
+    if (M == 0.0f) {
+        for (int j = 0; j < n; ++j) q[j] = 0;
+        return 0;
+    }
+    int scale = 62 - orc_ceil_log2(n) - 1 - exponent_of(M);
+    for (int j = 0; j < n; ++j) {
+        q[j] = visited[j] ? 0u : (uint64_t)floor(ldexp((double)w[j], scale));
+        Q += q[j];
+    }
+    return Q;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Setup: heuristic, nearest-neighbour tour, initial pheromone.              */
+/* ------------------------------------------------------------------------- */
+
+/* eta_ij^beta as float (reading R3), n x n row-major. */
+void orc_heta(int n, const int32_t *d, double beta, float *heta)
+{
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            double v;
+            if (i == j) {
+                v = 0.0;
+            } else {
+                double dd = (double)d[(size_t)i * n + j];
+                if (beta == 0.0) v = 1.0;
+                else if (beta == 1.0) v = 1.0 / dd;
+                else if (beta == 2.0) v = 1.0 / (dd * dd);
+                else if (beta == 3.0) v = 1.0 / (dd * dd * dd);
+                else v = pow(dd, -beta);
+            }
+            heta[(size_t)i * n + j] = (float)v;
+        }
+    }
+}
+
+/* eta_ij^beta in double, for the fp64 mode. */
+static void heta64(int n, const int32_t *d, double beta, double *h)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            h[(size_t)i * n + j] = (i == j) ? 0.0 : pow(1.0 / (double)d[(size_t)i * n + j], beta);
+}
+
+/* Length of the nearest-neighbour tour from city 0, ties to the lowest index (R4). */
+int64_t orc_nn_tour_length(int n, const int32_t *d)
+{
+    uint8_t *seen = (uint8_t *)calloc((size_t)n, 1);
+    int cur = 0;
+    seen[0] = 1;
+    int64_t len = 0;
+    for (int s = 1; s < n; ++s) {
+        int best = -1;
+        for (int j = 0; j < n; ++j) {
+            if (seen[j]) continue;
+            if (best < 0 || d[(size_t)cur * n + j] < d[(size_t)cur * n + best]) best = j;
+        }
+        len += d[(size_t)cur * n + best];
+        seen[best] = 1;
+        cur = best;
+    }
+    len += d[(size_t)cur * n + 0];
+    free(seen);
+    return len;
+}
+
+float orc_tau0(int n, int m, const int32_t *d)
+{
+    return (float)((double)m / (double)orc_nn_tour_length(n, d));
+}
+
+/* choice_info = tau^alpha * eta^beta in float (reading R6). */
+void orc_choice(int n, const float *tau, const float *heta, float alpha, float *choice)
+{
+    for (size_t e = 0; e < (size_t)n * n; ++e) {
+        float t;
+        if (alpha == 1.0f) t = tau[e];
+        else if (alpha == 0.0f) t = 1.0f;
+        else t = powf(tau[e], alpha);
+        choice[e] = t * heta[e];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tour construction (Section II): one ant.                                  */
+/* tour has n+1 entries, tour[n] = tour[0].  Returns C^k.                    */
+/* ------------------------------------------------------------------------- */
+int64_t orc_construct_ant(int n, const float *choice, const int32_t *d, uint64_t seed,
+                          uint32_t iteration, uint32_t ant, int32_t *tour)
+{
+    uint8_t *visited = (uint8_t *)calloc((size_t)n, 1);
+    uint32_t x[4];
+    draw(seed, 0u, ant, iteration, x);
+    int start = (int)(((uint64_t)x[0] * (uint64_t)n) >> 32);
+    tour[0] = start;
+    visited[start] = 1;
+    int cur = start;
+    for (int s = 1; s < n; ++s) {
+        draw(seed, (uint32_t)s, ant, iteration, x);
+        uint64_t r = ((uint64_t)x[1] << 32) | (uint64_t)x[0];
+        int next = orc_roulette(n, choice + (size_t)cur * n, visited, r);
+        tour[s] = next;
+        visited[next] = 1;
+        cur = next;
+    }
+    tour[n] = start;
+    free(visited);
+    int64_t len = 0;
+    for (int s = 0; s < n; ++s) len += d[(size_t)tour[s] * n + tour[s + 1]];
+    return len;
+}
+
+void orc_construct(int n, int m, const float *choice, const int32_t *d, uint64_t seed,
+                   uint32_t iteration, int32_t *tours, int64_t *lens)
+{
+    for (int k = 0; k < m; ++k)
+        lens[k] = orc_construct_ant(n, choice, d, seed, iteration, (uint32_t)k,
+                                    tours + (size_t)k * (n + 1));
+}
+
+/* ------------------------------------------------------------------------- */
+/* Pheromone update, Eqs. 2-4.                                               */
+/* ------------------------------------------------------------------------- */
+
+/* Deposit scale S of reading R5 for this iteration's tour lengths. */
+int orc_deposit_scale(int m, const int64_t *lens)
+{
+    int64_t cmin = lens[0];
+    for (int k = 1; k < m; ++k)
+        if (lens[k] < cmin) cmin = lens[k];
+    float dmax = (float)(1.0 / (double)cmin);
+    return 62 - orc_ceil_log2(m) - exponent_of(dmax);
+}
+
+/* Mirror mode: tau (float, n x n) updated in place. */
+void orc_update_mirror(int n, int m, const int32_t *tours, const int64_t *lens, float rho,
+                       float *tau)
+{
+    int S = orc_deposit_scale(m, lens);
+    uint64_t *acc = (uint64_t *)calloc((size_t)n * n, sizeof(uint64_t));
+    for (int k = 0; k < m; ++k) {
+        float dk = (float)(1.0 / (double)lens[k]);
+        uint64_t qk = (uint64_t)floor(ldexp((double)dk, S));
+        const int32_t *t = tours + (size_t)k * (n + 1);
+        for (int s = 0; s < n; ++s) {
+            int a = t[s], b = t[s + 1];
+            acc[(size_t)a * n + b] += qk;
+            acc[(size_t)b * n + a] += qk;
+        }
+    }
+    float keep = 1.0f - rho;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            size_t e = (size_t)i * n + j;
+            float evaporated = keep * tau[e];                  /* Eq. 2 */
+            float dep = ldexpf((float)acc[e], -S);             /* Eqs. 3-4 */
+            tau[e] = evaporated + dep;
+        }
+    }
+    free(acc);
+}
+
+/* fp64 mode: tau (double) updated in place by Eqs. 2-4 with dtau^k = 1/C^k. */
+void orc_update_fp64(int n, int m, const int32_t *tours, const int64_t *lens, double rho,
+                     double *tau)
+{
+    for (size_t e = 0; e < (size_t)n * n; ++e) tau[e] *= (1.0 - rho);
+    for (int k = 0; k < m; ++k) {
+        double dk = 1.0 / (double)lens[k];
+        const int32_t *t = tours + (size_t)k * (n + 1);
+        for (int s = 0; s < n; ++s) {
+            int a = t[s], b = t[s + 1];
+            tau[(size_t)a * n + b] += dk;
+            tau[(size_t)b * n + a] += dk;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Whole Ant System run (mirror mode), with the fp64 pheromone carried along  */
+/* on the same tours.  Outputs (any may be NULL):                            */
+/*   best_tour[n+1], best_len, tau32[n*n], tau64[n*n], last_tours[m*(n+1)],  */
+/*   last_lens[m], iter_best[iterations] (shortest C^k of each iteration).   */
+/* first_iteration lets a caller continue a run (the counter of R1).         */
+/* ------------------------------------------------------------------------- */
+int orc_run(int n, const int32_t *d, float alpha, float beta, float rho, int m, uint64_t seed,
+            int iterations, int32_t *best_tour, int64_t *best_len, float *tau32_out,
+            double *tau64_out, int32_t *last_tours, int64_t *last_lens, int64_t *iter_best)
+{
+    size_t nn = (size_t)n * n;
+    float *heta = (float *)malloc(nn * sizeof(float));
+    double *h64 = (double *)malloc(nn * sizeof(double));
+    float *tau = (float *)malloc(nn * sizeof(float));
+    double *tau64 = (double *)malloc(nn * sizeof(double));
+    float *choice = (float *)malloc(nn * sizeof(float));
+    int32_t *tours = (int32_t *)malloc((size_t)m * (n + 1) * sizeof(int32_t));
+    int64_t *lens = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    if (!heta || !h64 || !tau || !tau64 || !choice || !tours || !lens) return -2;
+
+    orc_heta(n, d, (double)beta, heta);
+    heta64(n, d, (double)beta, h64);
+    int64_t cnn = orc_nn_tour_length(n, d);
+    float tau0 = (float)((double)m / (double)cnn);
+    double tau0_64 = (double)m / (double)cnn;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            tau[(size_t)i * n + j] = (i == j) ? 0.0f : tau0;
+            tau64[(size_t)i * n + j] = (i == j) ? 0.0 : tau0_64;
+        }
+
+    int64_t best = INT64_MAX;
+    for (int it = 0; it < iterations; ++it) {
+        orc_choice(n, tau, heta, alpha, choice);
+        orc_construct(n, m, choice, d, seed, (uint32_t)it, tours, lens);
+        int kbest = 0;
+        for (int k = 1; k < m; ++k)
+            if (lens[k] < lens[kbest]) kbest = k;
+        if (iter_best) iter_best[it] = lens[kbest];
+        if (lens[kbest] < best) {
+            best = lens[kbest];
+            if (best_tour) memcpy(best_tour, tours + (size_t)kbest * (n + 1), (size_t)(n + 1) * sizeof(int32_t));
+        }
+        orc_update_mirror(n, m, tours, lens, rho, tau);
+        orc_update_fp64(n, m, tours, lens, (double)rho, tau64);
+    }
+    if (best_len) *best_len = best;
+    if (tau32_out) memcpy(tau32_out, tau, nn * sizeof(float));
+    if (tau64_out) memcpy(tau64_out, tau64, nn * sizeof(double));
+    if (last_tours) memcpy(last_tours, tours, (size_t)m * (n + 1) * sizeof(int32_t));
+    if (last_lens) memcpy(last_lens, lens, (size_t)m * sizeof(int64_t));
+    (void)h64;
+    free(heta); free(h64); free(tau); free(tau64); free(choice); free(tours); free(lens);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Brute-force optimum for tiny instances (n <= 11): city 0 fixed first,     */
+/* every permutation of the rest enumerated.                                 */
+/* ------------------------------------------------------------------------- */
+static void bf_rec(int n, const int32_t *d, int depth, int *perm, uint8_t *used, int64_t acc,
+                   int64_t *best, int *best_perm)
+{
+    if (acc >= *best) return; /* distances are non-negative */
+    if (depth == n) {
+        int64_t total = acc + d[(size_t)perm[n - 1] * n + perm[0]];
+        if (total < *best) {
+            *best = total;
+            memcpy(best_perm, perm, (size_t)n * sizeof(int));
+        }
+        return;
+    }
+    for (int c = 1; c < n; ++c) {
+        if (used[c]) continue;
+        used[c] = 1;
+        perm[depth] = c;
+        bf_rec(n, d, depth + 1, perm, used, acc + d[(size_t)perm[depth - 1] * n + c], best, best_perm);
+        used[c] = 0;
+    }
+}
+
+int64_t orc_brute_force(int n, const int32_t *d, int32_t *tour)
+{
+    if (n < 2 || n > 11) return -1;
+    int perm[11], best_perm[11];
+    uint8_t used[11] = {0};
+    perm[0] = 0;
+    used[0] = 1;
+    int64_t best = INT64_MAX;
+    bf_rec(n, d, 1, perm, used, 0, &best, best_perm);
+    if (tour) {
+        for (int i = 0; i < n; ++i) tour[i] = best_perm[i];
+        tour[n] = best_perm[0];
+    }
+    return best;
+}

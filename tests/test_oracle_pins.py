@@ -1,0 +1,339 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms, invariants of Eqs. 1-4, brute force, or a
+statistical test against the probabilities of Eq. 1.  The cases are chosen so
+that a plausible slip in the oracle (a dropped term, rho in place of 1 - rho, a
+transposed operand, >= in place of >, the wrong row) fails at least one test.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1101_2678_gb300 import instances as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (the random numbers of reading R1)
+# --------------------------------------------------------------------------
+
+def _kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(x, 16) for x in line.split()]
+            rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_philox_known_answers(orc):
+    rows = _kat()
+    assert len(rows) == 3
+    for ctr, key, out in rows:
+        assert list(orc.philox4x32_10(ctr, key)) == out
+
+
+def test_philox_uniformity(orc):
+    # 4 * 20000 words: the top 4 bits should be uniform over 16 bins.
+    from scipy.stats import chisquare
+    words = np.concatenate([orc.philox4x32_10([i, 7, 3, 0], [11, 13]) for i in range(20000)])
+    hist = np.bincount((words >> 28).astype(np.int64), minlength=16)
+    assert chisquare(hist).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Eq. 1: the random proportional rule, sampled by the integer roulette
+# --------------------------------------------------------------------------
+
+def test_ceil_log2(orc):
+    for v, c in [(1, 0), (2, 1), (3, 2), (4, 2), (5, 3), (48, 6), (1002, 10), (1024, 10),
+                 (1025, 11), (2392, 12), (4096, 12)]:
+        assert orc.ceil_log2(v) == c
+
+
+def test_roulette_weights_are_proportional(orc):
+    # q_j / Q must equal w_j / sum(w) (Eq. 1) up to the quantisation step,
+    # i.e. |q_j/Q - p_j| <= n / 2^(B-1) with B = 62 - ceil(log2 n).
+    rng = np.random.default_rng(0)
+    for n in [3, 6, 48, 1002]:
+        w = rng.lognormal(0.0, 3.0, size=n).astype(np.float32)
+        vis = (rng.uniform(size=n) < 0.3).astype(np.uint8)
+        vis[int(np.argmax(w))] = 0
+        q, Q = orc.roulette_weights(w, vis)
+        assert Q == int(q.sum()) and Q < 2**62
+        W = sum(Fraction(float(x)) for x, v in zip(w, vis) if not v)
+        B = 62 - orc.ceil_log2(n)
+        for j in range(n):
+            if vis[j]:
+                assert q[j] == 0
+                continue
+            p = Fraction(float(w[j])) / W
+            assert abs(Fraction(int(q[j]), Q) - p) <= Fraction(n, 2 ** (B - 1))
+
+
+def test_roulette_boundaries_pick_first_prefix_above_target(orc):
+    # T = floor(r Q / 2^64); the chosen city is the first j with prefix_j > T.
+    w = np.array([0.5, 0.0, 2.0, 1.25, 0.75, 3.0], np.float32)
+    vis = np.array([0, 0, 0, 1, 0, 0], np.uint8)
+    q, Q = orc.roulette_weights(w, vis)
+    prefix = np.cumsum(q.astype(object))
+
+    def r_for(T):  # smallest r with floor(r Q / 2^64) == T
+        return -((-T << 64) // Q)
+
+    for j in range(len(w)):
+        if q[j] == 0:
+            continue
+        lo = int(prefix[j] - q[j])
+        hi = int(prefix[j]) - 1
+        assert orc.roulette(w, vis, r_for(lo)) == j
+        assert orc.roulette(w, vis, r_for(hi)) == j
+    assert orc.roulette(w, vis, 0) == 0
+    assert orc.roulette(w, vis, 2**64 - 1) == 5
+
+
+def test_roulette_degenerate_cases(orc):
+    w = np.zeros(5, np.float32)
+    vis = np.array([1, 1, 0, 0, 1], np.uint8)
+    # all unvisited weights zero: the lowest-index unvisited city
+    assert orc.roulette(w, vis, 12345) == 2
+    # only one unvisited city: always it, whatever r
+    vis1 = np.array([1, 1, 1, 0, 1], np.uint8)
+    w1 = np.array([5, 5, 5, 1e-30, 5], np.float32)
+    for r in [0, 1, 2**63, 2**64 - 1]:
+        assert orc.roulette(w1, vis1, r) == 3
+    # everything visited
+    assert orc.roulette(w1, np.ones(5, np.uint8), 7) == -1
+    # subnormal weights are weighted exactly like normal ones
+    ws = np.array([2.0**-149, 2.0**-148, 0, 0], np.float32)
+    q, Q = orc.roulette_weights(ws, np.zeros(4, np.uint8))
+    assert q[1] == 2 * q[0] and Q == 3 * q[0]
+
+
+@pytest.mark.parametrize("visited", [[], [1, 4]])
+def test_roulette_chi_squared_against_eq1(orc, visited):
+    # Frequencies of the first move out of city 0 versus p_0j of Eq. 1.
+    from scipy.stats import chisquare
+    n = 6
+    w = np.array([0.0, 0.9, 0.05, 2.5, 0.3, 1.25], np.float32)
+    vis = np.zeros(n, np.uint8)
+    vis[0] = 1
+    vis[visited] = 1
+    draws = 100_000
+    counts = np.zeros(n, np.int64)
+    for i in range(draws):
+        x = orc.philox4x32_10([1, i, 0, 0], [99, 0])
+        r = (int(x[1]) << 32) | int(x[0])
+        counts[orc.roulette(w, vis, r)] += 1
+    cand = [j for j in range(n) if not vis[j]]
+    p = np.array([w[j] for j in cand], np.float64)
+    p /= p.sum()
+    assert counts[vis == 1].sum() == 0
+    res = chisquare(counts[cand], p * draws)
+    assert res.pvalue > 0.01, (counts, p * draws)
+
+
+def test_first_step_uses_row_of_current_city(orc):
+    # With an asymmetric choice matrix the second city of each tour must follow
+    # row tour[0] (not the column): per start city, chi-squared against Eq. 1.
+    from scipy.stats import chisquare
+    n = 4
+    ch = np.array([[0, 1, 2, 5],
+                   [3, 0, 1, 1],
+                   [1, 8, 0, 1],
+                   [2, 2, 4, 0]], np.float32)
+    d = np.ones((n, n), np.int32) - np.eye(n, dtype=np.int32)
+    counts = np.zeros((n, n), np.int64)
+    for it in range(60):
+        tours, _ = orc.construct(ch, d, 500, seed=5, iteration=it)
+        np.add.at(counts, (tours[:, 0], tours[:, 1]), 1)
+    for i in range(n):
+        row = ch[i].astype(np.float64)
+        cand = [j for j in range(n) if j != i]
+        p = row[cand] / row[cand].sum()
+        assert counts[i, i] == 0
+        assert chisquare(counts[i, cand], p * counts[i].sum()).pvalue > 0.01
+
+
+def test_start_city_is_uniform(orc):
+    from scipy.stats import chisquare
+    n = 7
+    ch = np.ones((n, n), np.float32)
+    d = np.ones((n, n), np.int32) - np.eye(n, dtype=np.int32)
+    starts = np.concatenate([orc.construct(ch, d, 700, 3, it)[0][:, 0] for it in range(20)])
+    assert chisquare(np.bincount(starts, minlength=n)).pvalue > 0.01
+
+
+# --------------------------------------------------------------------------
+# Tours (Section II: each ant visits every city exactly once; C^k = sum of d)
+# --------------------------------------------------------------------------
+
+def test_tours_are_closed_permutations_with_summed_lengths(orc):
+    inst = I.uniform_instance(37, 1000, seed=9)
+    h = orc.heta(inst.dist, 2.0)
+    ch = orc.choice(np.where(np.eye(37) > 0, 0, 0.01).astype(np.float32), h, 1.0)
+    tours, lens = orc.construct(ch, inst.dist, 29, seed=4, iteration=3)
+    for k in range(29):
+        t = tours[k]
+        assert sorted(t[:-1].tolist()) == list(range(37)) and t[-1] == t[0]
+        assert lens[k] == int(inst.dist[t[:-1], t[1:]].astype(np.int64).sum())
+
+
+# --------------------------------------------------------------------------
+# Setup: heuristic (eta = 1/d, Section II), nearest-neighbour tour, tau0
+# --------------------------------------------------------------------------
+
+def test_heta_is_inverse_distance_power(orc):
+    inst = I.uniform_instance(50, 1000, seed=2)
+    d = inst.dist.astype(np.float64)
+    off = ~np.eye(50, dtype=bool)
+    for beta in [1.0, 2.0, 3.0, 2.5, 0.0]:
+        h = orc.heta(inst.dist, beta).astype(np.float64)
+        assert np.all(np.diag(h) == 0)
+        # h * d^beta == 1 up to one float rounding (plus the double rounding)
+        err = np.abs(h[off] * d[off] ** beta - 1.0)
+        assert err.max() <= 2.0 ** -23
+
+
+def test_nearest_neighbour_tour_closed_forms(orc):
+    # cities on a line at x = 0..n-1: the NN tour walks out and back, 2(n-1)
+    n = 12
+    coords = np.stack([np.arange(n), np.zeros(n)], axis=1)
+    d = I.distance_matrix(coords)
+    assert orc.nn_tour_length(d) == 2 * (n - 1)
+    assert orc.tau0(d, 30) == np.float32(30 / (2 * (n - 1)))
+    # shuffled line: from any start the greedy walk sweeps to one end, jumps
+    # back past the start and sweeps to the other end: again 2(n-1)
+    for s in range(5):
+        perm = np.random.default_rng(s).permutation(n)
+        assert orc.nn_tour_length(I.distance_matrix(coords[perm])) == 2 * (n - 1)
+    # a tie at the first step: (10,0) and (0,10) are both 10 away from city 0;
+    # the lower index (1) gives 10 + 14 + 22 + 32 = 78, the other choice 86
+    pts = np.array([[0, 0], [10, 0], [0, 10], [10, 30]])
+    assert orc.nn_tour_length(I.distance_matrix(pts)) == 78
+
+
+# --------------------------------------------------------------------------
+# Pheromone update, Eqs. 2-4
+# --------------------------------------------------------------------------
+
+def _random_tours(n, m, seed):
+    rng = np.random.default_rng(seed)
+    tours = np.zeros((m, n + 1), np.int32)
+    for k in range(m):
+        p = rng.permutation(n)
+        tours[k, :n] = p
+        tours[k, n] = p[0]
+    return tours
+
+
+def _lens(d, tours):
+    return d[tours[:, :-1], tours[:, 1:]].astype(np.int64).sum(axis=1)
+
+
+@pytest.mark.parametrize("rho", [0.3, 0.5, 1.0])
+def test_single_ant_update_closed_form(orc, rho):
+    # m = 1: on-tour edges get (1-rho) tau + 1/C, off-tour edges (1-rho) tau (Eqs. 2-4).
+    n = 9
+    inst = I.uniform_instance(n, 1000, seed=4)
+    rng = np.random.default_rng(3)
+    tau = rng.uniform(0.1, 2.0, size=(n, n)).astype(np.float32)
+    tau = ((tau + tau.T) / 2).astype(np.float32)
+    np.fill_diagonal(tau, 0)
+    tours = _random_tours(n, 1, 5)
+    lens = _lens(inst.dist, tours)
+    out = orc.update_mirror(tau, tours, lens, rho)
+    keep = np.float32(1.0) - np.float32(rho)
+    dk = np.float32(1.0 / float(lens[0]))
+    on = np.zeros((n, n), bool)
+    t = tours[0]
+    on[t[:-1], t[1:]] = True
+    on[t[1:], t[:-1]] = True
+    expect = (keep * tau).astype(np.float32)
+    expect[on] = (expect[on] + dk).astype(np.float32)
+    assert np.array_equal(out, expect)
+    out64 = orc.update_fp64(tau.astype(np.float64), tours, lens, rho)
+    e64 = (1 - rho) * tau.astype(np.float64)
+    e64[on] += 1.0 / float(lens[0])
+    assert np.allclose(out64, e64, rtol=1e-15, atol=0)
+
+
+def test_update_invariants(orc):
+    # Total deposit = 2 n sum_k 1/C^k (each tour has n edges, each counted in
+    # both directions); tau stays symmetric; mirror within 1e-6 of fp64.
+    n, m, rho = 31, 40, 0.5
+    inst = I.uniform_instance(n, 1000, seed=6)
+    tau = np.full((n, n), 0.02, np.float32)
+    np.fill_diagonal(tau, 0)
+    tours = _random_tours(n, m, 8)
+    # make several ants share edges (the converged case)
+    tours[10:20] = tours[0]
+    lens = _lens(inst.dist, tours)
+    out = orc.update_mirror(tau, tours, lens, rho)
+    out64 = orc.update_fp64(tau.astype(np.float64), tours, lens, rho)
+    assert np.array_equal(out, out.T)
+    assert np.allclose(out64, out64.T, rtol=1e-14)
+    dep64 = out64 - (1 - rho) * tau.astype(np.float64)
+    assert math.isclose(dep64.sum(), 2 * n * float((1.0 / lens).sum()), rel_tol=1e-12)
+    rel = np.abs(out.astype(np.float64) - out64) / np.maximum(out64, 1e-300)
+    assert rel.max() < 1e-6
+    assert np.all(np.diag(out) == 0)
+
+
+def test_deposit_fixed_point_is_exact_sum(orc):
+    # sum_k q_k 2^-S equals sum_k dtau_k up to m * 2^-S, and q never overflows.
+    rng = np.random.default_rng(11)
+    lens = rng.integers(3, 10**7, size=3000).astype(np.int64)
+    S = orc.deposit_scale(lens)
+    m = len(lens)
+    dts = [Fraction(float(np.float32(1.0 / float(c)))) for c in lens]
+    qs = [math.floor(x * 2**S) for x in dts]
+    assert max(qs) * m < 2**63
+    assert abs(Fraction(sum(qs), 2**S) - sum(dts)) <= Fraction(m, 2**S)
+    assert max(qs) >= 2 ** (62 - orc.ceil_log2(m) - 1)
+
+
+# --------------------------------------------------------------------------
+# Whole runs: brute force, FP64 agreement, determinism
+# --------------------------------------------------------------------------
+
+def test_brute_force_on_convex_polygon(orc):
+    # Points on a circle, shuffled: the optimum visits them in angular order.
+    n = 9
+    ang = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    pts = np.rint(np.stack([5000 + 4000 * np.cos(ang), 5000 + 4000 * np.sin(ang)], 1))
+    perm = np.random.default_rng(2).permutation(n)
+    d = I.distance_matrix(pts[perm])
+    hull = I.distance_matrix(pts)
+    perimeter = int(sum(hull[i, (i + 1) % n] for i in range(n)))
+    best, tour = orc.brute_force(d)
+    assert best == perimeter
+    assert int(d[tour[:-1], tour[1:]].sum()) == best
+
+
+@pytest.mark.parametrize("n,seed", [(8, 21), (9, 22), (10, 23)])
+def test_ant_system_reaches_brute_force_optimum(orc, n, seed):
+    inst = I.uniform_instance(n, 1000, seed=seed)
+    opt, _ = orc.brute_force(inst.dist)
+    res = orc.run(inst.dist, m=n, iterations=100, seed=seed)
+    assert np.all(res["iter_best"] >= opt)
+    assert res["best_len"] == opt
+    t = res["best_tour"]
+    assert int(inst.dist[t[:-1], t[1:]].sum()) == opt
+
+
+def test_run_fp32_mirror_tracks_fp64(orc):
+    w = I.workload_n48()
+    res = orc.run(w["inst"].dist, w["m"], 100, w["seed"])
+    r64, r32 = res["tau64"], res["tau32"].astype(np.float64)
+    assert np.all(np.abs(r32 - r64) <= 1e-5 * np.abs(r64) + 2.0 ** -126)
+    assert res["best_len"] == res["iter_best"].min()
+    again = orc.run(w["inst"].dist, w["m"], 100, w["seed"])
+    assert np.array_equal(again["tau32"], res["tau32"]) and again["best_len"] == res["best_len"]
