@@ -1,0 +1,387 @@
+"""Benchmark of the GB300 Ant System (one JSON line on stdout).
+
+A step is one full Ant System iteration of the workload (tour construction,
+iteration best, deposit, evaporation and choice_info), replayed from a CUDA
+graph through the C ABI with all state resident in HBM.  Between timed steps
+L2 is flushed by writing a 256 MB buffer (outside the timed region); each step
+is timed with CUDA events on the stream the library launches on.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n1002]
+                  [--deposit gather|u64|f32] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the slow, plain restatement of the
+method used by the tests) on a bounded sample of the same workload.
+With N > 1 (torchrun) every rank runs an independent replica of the workload
+(no data-path collective: the instances are independent); the reported value
+is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ant-steps/s (tour constr.) & edges/s (pheromone) vs roofline; batched solves/s, p99"
+WORKLOADS = {
+    "n48": "workload_n48",
+    "n1002": "workload_n1002",
+    "n2392": "workload_n2392",
+}
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="n1002", choices=sorted(WORKLOADS))
+    ap.add_argument("--deposit", default="gather", choices=["gather", "u64", "f32"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, ants: int):
+    """Time the oracle on `ants` ants of iteration 0 plus one full update.
+
+    Returns (ant_steps_per_s, seconds, description)."""
+    import numpy as np
+    from oracle import oracle as orc
+    d = w["inst"].dist
+    n, m = d.shape[0], w["m"]
+    t0 = time.perf_counter()
+    h = orc.heta(d, w["beta"])
+    tau = np.full((n, n), orc.tau0(d, m), np.float32)
+    np.fill_diagonal(tau, 0)
+    ch = orc.choice(tau, h, w["alpha"])
+    t_setup = time.perf_counter() - t0
+    ants = max(1, min(ants, m))
+    t0 = time.perf_counter()
+    tours = np.zeros((m, n + 1), np.int32)
+    lens = np.zeros(m, np.int64)
+    for k in range(ants):
+        tours[k], lens[k] = orc.construct_ant(ch, d, w["seed"], 0, k)
+    t_con = time.perf_counter() - t0
+    # the other ants' tours are copies for the update (same work per edge)
+    for k in range(ants, m):
+        tours[k], lens[k] = tours[k % ants], lens[k % ants]
+    t0 = time.perf_counter()
+    tau = orc.update_mirror(tau, tours, lens, w["rho"])
+    ch = orc.choice(tau, h, w["alpha"])
+    t_upd = time.perf_counter() - t0
+    per_iter = t_con / ants * m + t_upd
+    value = m * (n - 1) / per_iter
+    desc = (f"oracle (C, 1 thread): {ants} of {m} ants of iteration 0 constructed plus one "
+            f"full pheromone update and choice_info; iteration time extrapolated as "
+            f"t_ant*m + t_update (setup {t_setup:.2f}s not counted)")
+    return value, t_con + t_upd, desc
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    from oracle import oracle as orc
+    orc.build()
+    d = w["inst"].dist
+    n, m = d.shape[0], w["m"]
+    ants = max(1, min(m, int(2.0 / max(_oracle_ant_seconds(w), 1e-6))))
+    for _ in range(args.warmup):
+        oracle_sample(w, max(1, ants // 4))
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        v, s, desc = oracle_sample(w, ants)
+        vals.append(v)
+        secs += s
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ant-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": m * (n - 1) / value * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "n": n, "m": m, "iterations": w["iterations"],
+                   "parallelism": "cpu-1-thread", "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "ant-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_ant_seconds(w):
+    import numpy as np
+    from oracle import oracle as orc
+    d = w["inst"].dist
+    n, m = d.shape[0], w["m"]
+    h = orc.heta(d, w["beta"])
+    tau = np.full((n, n), orc.tau0(d, m), np.float32)
+    ch = orc.choice(tau, h, w["alpha"])
+    t0 = time.perf_counter()
+    orc.construct_ant(ch, d, w["seed"], 0, 0)
+    return time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, w, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_1101_2678_gb300 import aco
+
+    torch.cuda.set_device(local)
+    aco.load()
+    d = w["inst"].dist
+    n, m = d.shape[0], w["m"]
+    dep = {"gather": aco.ACO_DEPOSIT_GATHER, "u64": aco.ACO_DEPOSIT_ATOMIC_U64,
+           "f32": aco.ACO_DEPOSIT_ATOMIC_F32}[args.deposit]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    col = aco.Colony(d, m, seed=w["seed"] + rank, alpha=w["alpha"], beta=w["beta"], rho=w["rho"])
+    h = col.h
+    aco.aco_set_option(h, aco.ACO_OPT_STREAM, stream.cuda_stream)
+    aco.aco_set_option(h, aco.ACO_OPT_DEPOSIT, dep)
+    aco.aco_set_option(h, aco.ACO_OPT_PROFILE, 1)
+    launches = aco.aco_kernel_launches_per_iteration(h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            aco.aco_iterate(h, 1)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local) if rank == 0 else None
+        if clocks:
+            clocks.start()
+        step_ms, phase_ms = [], np.zeros(aco.ACO_NUM_PHASES)
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            aco.aco_iterate(h, 1)
+            e1.record(stream)
+            phase_ms += aco.aco_get_kernel_times(h)  # synchronises the stream
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+    aco.aco_synchronize(h)
+    best_tour, best_len = aco.aco_best_tour(h, n)
+    col.close()
+
+    total_ms = max_over_ranks(sum(step_ms), world)
+    steps = args.steps
+    ant_steps = m * (n - 1) * steps * world
+    value = ant_steps / (total_ms / 1e3)
+    con_ms = phase_ms[aco.ACO_PHASE_CONSTRUCT] / steps
+    upd_ms = (phase_ms[aco.ACO_PHASE_DEPOSIT] + phase_ms[aco.ACO_PHASE_UPDATE]) / steps
+    best_ms = phase_ms[aco.ACO_PHASE_BEST] / steps
+
+    # e2e: a whole solve through the public API from host memory.
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_solve(aco, w, rank)
+
+    if rank != 0:
+        return
+    peaks, peak_kind = measured_peaks()
+    roof = construct_roofline(n, m, con_ms, peaks, peak_kind)
+    line = {
+        "metric": METRIC, "value": value, "unit": "ant-steps/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "n": n, "m": m, "alpha": w["alpha"],
+                   "beta": w["beta"], "rho": w["rho"], "deposit": args.deposit,
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "flushed between steps (256 MB write)"},
+        "construct_ant_steps_per_s": m * (n - 1) / (con_ms / 1e3),
+        "pheromone_edges_per_s": m * n / (upd_ms / 1e3),
+        "phase_ms": {"construct": con_ms, "best": best_ms, "pheromone": upd_ms},
+        "best_len": best_len,
+        "roofline": roof,
+        "gpu_launches": launches * steps,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        v, s, desc = oracle_sample(w, max(1, int(10.0 / max(_oracle_ant_seconds(w), 1e-6))))
+        line["cpu_baseline"] = {"value": v, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+def construct_roofline(n, m, con_ms, peaks, peak_kind):
+    """Roofline entry for the construction kernel (the dominant kernel).
+
+    Algorithmic bytes per launch: every ant reads, at each of its n-1 steps,
+    the 4-byte choice_info entries of the cities it has not visited yet:
+    4 * m * sum_{s=1}^{n-1} (n - s) = 4 m n (n-1) / 2."""
+    algo = 4.0 * m * n * (n - 1) / 2.0
+    achieved = algo / (con_ms / 1e3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "kernel": "construct_kernel", "algorithmic_bytes_per_launch": algo,
+            "avg_launch_ms": con_ms}
+
+
+def e2e_solve(aco, w, rank):
+    """create (uploads dist) + iterate + best tour to the host, wall-clock timed."""
+    import numpy as np
+    import torch
+    d = np.ascontiguousarray(w["inst"].dist, dtype=np.int32)
+    n, m, iters = d.shape[0], w["m"], w["iterations"]
+    pinned = torch.from_numpy(d).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = aco.aco_create(pinned, w["alpha"], w["beta"], w["rho"], m, w["seed"] + rank)
+    aco.aco_iterate(h, iters)
+    tour, length = aco.aco_best_tour(h, n)
+    t1 = time.perf_counter()
+    aco.aco_destroy(h)
+    h2d = d.nbytes
+    d2h = tour.nbytes + 8
+    return {"value": m * (n - 1) * iters / (t1 - t0), "unit": "ant-steps/s",
+            "h2d_bytes_per_step": h2d / iters, "d2h_bytes_per_step": d2h / iters,
+            "what": f"aco_create from pinned host dist + aco_iterate({iters}) + aco_best_tour "
+                    f"to host, wall clock; bytes amortised over the {iters} iterations",
+            "seconds": t1 - t0}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    from paper_1101_2678_gb300 import instances
+    w = getattr(instances, WORKLOADS[args.workload])()
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+    else:
+        run_ours(args, w, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

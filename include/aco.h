@@ -1,0 +1,199 @@
+/*
+ * aco.h - C ABI of the GB300 (sm_103a) Ant System for the symmetric TSP.
+ *
+ * The method is the Ant System of Cecilia, Garcia, Ujaldon, Nisbet and Amos,
+ * "Parallelization Strategies for Ant Colony Optimisation on GPUs": m ants
+ * build tours by the random proportional rule (Section II, Eq. 1) over
+ * choice_info = tau^alpha * eta^beta (Section III-A), then the pheromone is
+ * evaporated (Eq. 2) and every ant deposits 1/C^k on its tour's edges
+ * (Eqs. 3-4).  Everything runs in CUDA kernels on one GPU; there is no CPU
+ * fallback.  If the library cannot reach a GPU every call fails with
+ * ACO_ECUDA.
+ *
+ * Conventions for every entry point:
+ *  - Return value: ACO_OK (0) or a negative ACO_E* code; no exception or
+ *    abort crosses the ABI.  aco_strerror() names the code and
+ *    aco_last_error_message() gives the detail of the last failure on the
+ *    calling thread.
+ *  - Host pointers are plain C arrays owned by the caller; the library copies
+ *    what it needs and never keeps a caller pointer after the call returns.
+ *  - Matrices are row-major, n x n, without padding.  Tours are arrays of
+ *    n+1 city indices with tour[n] == tour[0] (a closed tour, Section II).
+ *  - A handle is not thread-safe: calls on one handle must not overlap.
+ *    Work on a handle is ordered on its CUDA stream; calls that return data
+ *    to the host synchronise that stream.
+ *
+ * Readings of points the paper leaves open (the same in the CPU oracle):
+ *  - eta_ij^beta = 1/d_ij^beta in double rounded to float; d_ij >= 1 is
+ *    required for i != j (eta = 1/d is undefined at d = 0).
+ *  - tau0 = m / C_nn, C_nn the nearest-neighbour tour from city 0 (ties to
+ *    the lower index); tau_ii = 0.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
+ *    counter = (step, ant, iteration, 0); an ant starts at
+ *    floor(x0 * n / 2^32) ("ants are randomly placed", Section II).
+ *  - Eq. 1 is sampled exactly by an integer roulette: with M the largest
+ *    unvisited weight and B = 62 - ceil(log2 n), q_j = floor(w_j *
+ *    2^(B-1-ilogb M)) for unvisited j, T = floor(r Q / 2^64) with
+ *    r = x1 * 2^32 + x0 and Q = sum q_j, and the chosen city is the first j
+ *    (ascending) whose prefix sum exceeds T; if M == 0 the lowest unvisited
+ *    city.  The result does not depend on how the kernel tiles the row.
+ *  - Deposit (Eqs. 3-4): dtau^k = (float)(1/(double)C^k) on both (a,b) and
+ *    (b,a).  The deterministic variants sum q_k = floor(dtau^k * 2^S),
+ *    S = 62 - ceil(log2 m) - ilogb(max_k dtau^k), exactly in 64-bit
+ *    integers, round the sum to float once and scale it by 2^-S;
+ *    tau' = fl(fl((1-rho) tau) + dep).
+ *  - choice = tau * eta^beta for alpha == 1, eta^beta for alpha == 0, and
+ *    powf(tau, alpha) * eta^beta otherwise.
+ *  - The best-so-far tour changes only to a strictly shorter tour; within an
+ *    iteration the lowest ant index wins ties.
+ */
+#ifndef ACO_GB300_H
+#define ACO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define ACO_OK 0
+#define ACO_EINVAL (-1)   /* an argument is out of range or inconsistent     */
+#define ACO_ENOMEM (-2)   /* a device or host allocation failed              */
+#define ACO_ECUDA (-3)    /* a CUDA call failed (no GPU, bad launch, ...)    */
+#define ACO_ESTATE (-4)   /* the call is not valid in the handle's state     */
+#define ACO_ETIMEOUT (-5) /* a bounded device-side wait gave up              */
+#define ACO_EBUSY (-6)    /* no free slot or not enough memory budget left   */
+
+/* ---- limits ------------------------------------------------------------- */
+#define ACO_MAX_N 4096    /* cities per instance                             */
+#define ACO_MAX_M 16384   /* ants per instance                               */
+
+/* ---- options (aco_set_option / aco_get_option) --------------------------- */
+#define ACO_OPT_DEPOSIT 1      /* ACO_DEPOSIT_* below; default GATHER           */
+#define ACO_OPT_STREAM 2       /* cudaStream_t as int64; 0 = the handle's own   */
+#define ACO_OPT_USE_GRAPH 3    /* 1 (default): aco_iterate replays a CUDA graph */
+#define ACO_OPT_PROFILE 4      /* 1: record CUDA events around every kernel     */
+#define ACO_OPT_WARPS_PER_ANT 5 /* 0 (default) = automatic, else 1, 2 or 4      */
+#define ACO_OPT_ANTS_PER_CTA 6 /* 0 (default) = automatic, else 1..8            */
+
+#define ACO_DEPOSIT_GATHER 0   /* atomic-free: edges bucketed per city by the
+                                  construction kernel, one warp reduces a row  */
+#define ACO_DEPOSIT_ATOMIC_U64 1 /* red.global.add.u64 of the fixed-point q_k  */
+#define ACO_DEPOSIT_ATOMIC_F32 2 /* red.global.add.f32 of dtau^k into tau after
+                                  evaporation (the paper's atomic kernel; the
+                                  order of additions, hence the last bits of
+                                  tau, is not deterministic)                   */
+
+/* ---- phases reported by aco_get_kernel_times ------------------------------ */
+#define ACO_PHASE_CONSTRUCT 0  /* tour construction kernel                      */
+#define ACO_PHASE_BEST 1       /* iteration-best / best-so-far kernel          */
+#define ACO_PHASE_DEPOSIT 2    /* deposit kernel(s) (0 for the gather variant)  */
+#define ACO_PHASE_UPDATE 3     /* evaporation + deposit apply + choice_info     */
+#define ACO_NUM_PHASES 4
+
+typedef struct aco_colony *aco_handle;
+
+/* Name of an error code (static string). */
+const char *aco_strerror(int code);
+
+/* Detail of the last failure on the calling thread (static per-thread buffer). */
+const char *aco_last_error_message(void);
+
+/*
+ * aco_create - set up one Ant System instance (Section II; Section III-A for
+ * the choice_info table).
+ *   n      number of cities, 3 <= n <= ACO_MAX_N
+ *   dist   host array, n*n int32, row-major: symmetric, d_ii = 0 and
+ *          d_ij >= 1 for i != j.  Copied; the caller keeps ownership.
+ *   alpha  pheromone exponent (finite, >= 0)
+ *   beta   heuristic exponent (finite, >= 0)
+ *   rho    evaporation rate, 0 < rho <= 1 (Eq. 2)
+ *   m      number of ants, 1 <= m <= ACO_MAX_M
+ *   seed   Philox key
+ *   out    receives the handle (owned by the library until aco_destroy)
+ * Computes eta^beta, the nearest-neighbour tour, tau0 and the first
+ * choice_info on the device.  Errors: ACO_EINVAL (bad argument, dist not
+ * symmetric / zero diagonal / positive off-diagonal), ACO_ENOMEM, ACO_ECUDA.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+int aco_create(int32_t n, const int32_t *dist, float alpha, float beta, float rho, int32_t m,
+               uint64_t seed, aco_handle *out);
+
+/* aco_destroy - free everything the handle owns; NULL is accepted. */
+int aco_destroy(aco_handle h);
+
+/*
+ * aco_choice_info - recompute choice_info = tau^alpha * eta^beta from the
+ * current tau (Section III-A; idempotent).  If out != NULL, copy it to the
+ * host as n*n float (row-major).
+ */
+int aco_choice_info(aco_handle h, float *out);
+
+/*
+ * aco_construct_tours - every ant builds a tour for the current iteration
+ * (Section II, Eq. 1), then the iteration-best and best-so-far tours are
+ * updated.  The iteration counter does not advance, so calling it twice
+ * gives the same tours.  tours (m*(n+1) int32) and lens (m int64, C^k) are
+ * host outputs; either may be NULL.
+ */
+int aco_construct_tours(aco_handle h, int32_t *tours, int64_t *lens);
+
+/*
+ * aco_update_pheromone - evaporation (Eq. 2) and deposit (Eqs. 3-4) from the
+ * tours of the last aco_construct_tours, then choice_info is recomputed and
+ * the iteration counter advances.  ACO_ESTATE if no tours were constructed
+ * since the last update.
+ */
+int aco_update_pheromone(aco_handle h);
+
+/*
+ * aco_iterate - `iterations` full Ant System iterations (construct, best,
+ * update).  With ACO_OPT_USE_GRAPH the iteration is captured once as a CUDA
+ * graph and replayed.  Asynchronous: returns once the work is enqueued.
+ */
+int aco_iterate(aco_handle h, int32_t iterations);
+
+/*
+ * aco_best_tour - best-so-far tour (n+1 int32) and its length; either output
+ * may be NULL.  ACO_ESTATE before the first construction.
+ */
+int aco_best_tour(aco_handle h, int32_t *tour, int64_t *len);
+
+/* aco_get_pheromone - copy tau (n*n float, row-major) to the host. */
+int aco_get_pheromone(aco_handle h, float *tau);
+
+/* aco_get_heuristic - copy eta^beta (n*n float, row-major) to the host. */
+int aco_get_heuristic(aco_handle h, float *heta);
+
+/* aco_get_iteration - number of completed pheromone updates. */
+int aco_get_iteration(aco_handle h, int64_t *iteration);
+
+/* aco_get_tau0 - the initial pheromone m / C_nn and C_nn; either may be NULL. */
+int aco_get_tau0(aco_handle h, float *tau0, int64_t *nn_len);
+
+/* aco_set_option / aco_get_option - ACO_OPT_* keys above. */
+int aco_set_option(aco_handle h, int32_t key, int64_t value);
+int aco_get_option(aco_handle h, int32_t key, int64_t *value);
+
+/*
+ * aco_get_kernel_times - with ACO_OPT_PROFILE on, the device time in ms of
+ * each ACO_PHASE_* in the most recent iteration (synchronises the stream).
+ * ms must hold ACO_NUM_PHASES floats.
+ */
+int aco_get_kernel_times(aco_handle h, float *ms);
+
+/* aco_synchronize - wait for the handle's stream and report device-side errors. */
+int aco_synchronize(aco_handle h);
+
+/*
+ * aco_kernel_launches_per_iteration - how many kernels one iteration launches
+ * with the handle's current options.
+ */
+int aco_kernel_launches_per_iteration(aco_handle h, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACO_GB300_H */

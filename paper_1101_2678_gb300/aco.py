@@ -1,0 +1,238 @@
+"""ctypes binding of libaco_gb300.so (include/aco.h), same names as the C ABI.
+
+This module only marshals arguments: every step of the Ant System runs in the
+CUDA kernels of the library.  There is no CPU fallback; if the library or a
+GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libaco_gb300.so")
+
+ACO_OK = 0
+ACO_EINVAL = -1
+ACO_ENOMEM = -2
+ACO_ECUDA = -3
+ACO_ESTATE = -4
+ACO_ETIMEOUT = -5
+ACO_EBUSY = -6
+ACO_MAX_N = 4096
+ACO_MAX_M = 16384
+
+ACO_OPT_DEPOSIT = 1
+ACO_OPT_STREAM = 2
+ACO_OPT_USE_GRAPH = 3
+ACO_OPT_PROFILE = 4
+ACO_OPT_WARPS_PER_ANT = 5
+ACO_OPT_ANTS_PER_CTA = 6
+
+ACO_DEPOSIT_GATHER = 0
+ACO_DEPOSIT_ATOMIC_U64 = 1
+ACO_DEPOSIT_ATOMIC_F32 = 2
+
+ACO_PHASE_CONSTRUCT = 0
+ACO_PHASE_BEST = 1
+ACO_PHASE_DEPOSIT = 2
+ACO_PHASE_UPDATE = 3
+ACO_NUM_PHASES = 4
+
+# (name, restype, argtypes) of every exported entry point.
+_vp = C.c_void_p
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+_f32p = C.POINTER(C.c_float)
+SIGNATURES = [
+    ("aco_strerror", C.c_char_p, [C.c_int]),
+    ("aco_last_error_message", C.c_char_p, []),
+    ("aco_create", C.c_int, [C.c_int32, _vp, C.c_float, C.c_float, C.c_float, C.c_int32,
+                             C.c_uint64, C.POINTER(_vp)]),
+    ("aco_destroy", C.c_int, [_vp]),
+    ("aco_choice_info", C.c_int, [_vp, _vp]),
+    ("aco_construct_tours", C.c_int, [_vp, _vp, _vp]),
+    ("aco_update_pheromone", C.c_int, [_vp]),
+    ("aco_iterate", C.c_int, [_vp, C.c_int32]),
+    ("aco_best_tour", C.c_int, [_vp, _vp, _vp]),
+    ("aco_get_pheromone", C.c_int, [_vp, _vp]),
+    ("aco_get_heuristic", C.c_int, [_vp, _vp]),
+    ("aco_get_iteration", C.c_int, [_vp, _i64p]),
+    ("aco_get_tau0", C.c_int, [_vp, _f32p, _i64p]),
+    ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
+    ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
+    ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
+    ("aco_synchronize", C.c_int, [_vp]),
+    ("aco_kernel_launches_per_iteration", C.c_int, [_vp, _i32p]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AcoError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail} (code {code})")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build() "
+                                   "(the Ant System has no CPU fallback)")
+            L = C.CDLL(p)
+            for name, res, args in SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != ACO_OK:
+        L = load()
+        detail = L.aco_last_error_message().decode() or L.aco_strerror(rc).decode()
+        raise AcoError(rc, where, detail)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def aco_strerror(code: int) -> str:
+    return load().aco_strerror(code).decode()
+
+
+def aco_create(dist, alpha: float, beta: float, rho: float, m: int, seed: int):
+    """Create an instance from an n x n int32 distance matrix; returns the handle."""
+    d = np.ascontiguousarray(dist, dtype=np.int32)
+    if d.ndim != 2 or d.shape[0] != d.shape[1]:
+        raise ValueError("dist must be a square matrix")
+    h = C.c_void_p()
+    _check(load().aco_create(d.shape[0], _ptr(d), alpha, beta, rho, m, seed, C.byref(h)),
+           "aco_create")
+    return h
+
+
+def aco_destroy(h) -> None:
+    _check(load().aco_destroy(h), "aco_destroy")
+
+
+def aco_choice_info(h, n: int | None = None):
+    """Recompute choice_info; with n given, return it as an n x n float32 array."""
+    out = None if n is None else np.empty((n, n), np.float32)
+    _check(load().aco_choice_info(h, _ptr(out)), "aco_choice_info")
+    return out
+
+
+def aco_construct_tours(h, n: int | None = None, m: int | None = None):
+    """Construct tours; with n and m given, return (tours (m, n+1), lens (m,))."""
+    tours = lens = None
+    if n is not None and m is not None:
+        tours = np.empty((m, n + 1), np.int32)
+        lens = np.empty(m, np.int64)
+    _check(load().aco_construct_tours(h, _ptr(tours), _ptr(lens)), "aco_construct_tours")
+    return tours, lens
+
+
+def aco_update_pheromone(h) -> None:
+    _check(load().aco_update_pheromone(h), "aco_update_pheromone")
+
+
+def aco_iterate(h, iterations: int) -> None:
+    _check(load().aco_iterate(h, iterations), "aco_iterate")
+
+
+def aco_best_tour(h, n: int):
+    tour = np.empty(n + 1, np.int32)
+    length = np.zeros(1, np.int64)
+    _check(load().aco_best_tour(h, _ptr(tour), _ptr(length)), "aco_best_tour")
+    return tour, int(length[0])
+
+
+def aco_get_pheromone(h, n: int) -> np.ndarray:
+    out = np.empty((n, n), np.float32)
+    _check(load().aco_get_pheromone(h, _ptr(out)), "aco_get_pheromone")
+    return out
+
+
+def aco_get_heuristic(h, n: int) -> np.ndarray:
+    out = np.empty((n, n), np.float32)
+    _check(load().aco_get_heuristic(h, _ptr(out)), "aco_get_heuristic")
+    return out
+
+
+def aco_get_iteration(h) -> int:
+    v = C.c_int64()
+    _check(load().aco_get_iteration(h, C.byref(v)), "aco_get_iteration")
+    return v.value
+
+
+def aco_get_tau0(h):
+    t = C.c_float()
+    nn = C.c_int64()
+    _check(load().aco_get_tau0(h, C.byref(t), C.byref(nn)), "aco_get_tau0")
+    return float(np.float32(t.value)), nn.value
+
+
+def aco_set_option(h, key: int, value: int) -> None:
+    _check(load().aco_set_option(h, key, value), "aco_set_option")
+
+
+def aco_get_option(h, key: int) -> int:
+    v = C.c_int64()
+    _check(load().aco_get_option(h, key, C.byref(v)), "aco_get_option")
+    return v.value
+
+
+def aco_get_kernel_times(h) -> np.ndarray:
+    out = np.zeros(ACO_NUM_PHASES, np.float32)
+    _check(load().aco_get_kernel_times(h, _ptr(out)), "aco_get_kernel_times")
+    return out
+
+
+def aco_synchronize(h) -> None:
+    _check(load().aco_synchronize(h), "aco_synchronize")
+
+
+def aco_kernel_launches_per_iteration(h) -> int:
+    v = C.c_int32()
+    _check(load().aco_kernel_launches_per_iteration(h, C.byref(v)),
+           "aco_kernel_launches_per_iteration")
+    return v.value
+
+
+class Colony:
+    """Thin owner of one handle (destroys it on close / garbage collection)."""
+
+    def __init__(self, dist, m: int, seed: int, alpha=1.0, beta=2.0, rho=0.5):
+        d = np.ascontiguousarray(dist, dtype=np.int32)
+        self.n = int(d.shape[0])
+        self.m = int(m)
+        self.h = aco_create(d, alpha, beta, rho, m, seed)
+
+    def close(self):
+        if self.h is not None:
+            aco_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,125 @@
+// Device-side building blocks shared by the Ant System kernels (sm_103a).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace aco {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Per-instance iteration state, resident on the device.
+struct IterState {
+  unsigned long long iteration;  // completed pheromone updates (Philox counter word 2)
+  long long best_len;            // best-so-far tour length (INT64_MAX before the first)
+  long long iter_best_len;       // shortest C^k of the last construction
+  long long nn_len;              // nearest-neighbour tour length C_nn
+  int iter_best_ant;
+  int deposit_shift;             // S of the fixed-point deposit
+  float tau0;
+  int status;                    // device error bits (kStatus*)
+};
+
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusBadTour = 2;
+
+// Everything a kernel needs to know about one instance.  Matrices are n rows
+// of `ld` elements (ld = n rounded up to a multiple of 4, padding zero).
+struct Instance {
+  int n, m, ld;
+  int ldt;   // tour row stride (>= n + 1, multiple of 4)
+  int ldm;   // nbr row stride (>= m, multiple of 32)
+  float alpha, beta, rho;
+  unsigned long long seed;
+  const int32_t* dist;          // [n][ld]
+  float* heta;                  // [n][ld]  eta^beta
+  float* tau;                   // [n][ld]
+  float* choice;                // [n][ld]  choice_info
+  int32_t* tours;               // [m][ldt]
+  long long* lens;              // [m]
+  uint32_t* nbr;                // [n][ldm]  (pred << 16 | succ) of city i in tour k
+  unsigned long long* q;        // [m]   fixed-point deposit per ant
+  float* delta;                 // [m]   dtau^k as float
+  unsigned long long* acc;      // [n][ld] fixed-point accumulator (atomic u64 variant)
+  int32_t* best_tour;           // [n + 1]
+  IterState* st;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32
+// S-box, multipliers 0xD2511F53 / 0xCD9E8D57, key bumped by 0x9E3779B9 /
+// 0xBB67AE85 between rounds.
+// ---------------------------------------------------------------------------
+struct Philox4 {
+  uint32_t x0, x1, x2, x3;
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return Philox4{c0, c1, c2, c3};
+}
+
+// The draw of one construction step: counter (step, ant, iteration, 0).
+__device__ __forceinline__ Philox4 step_draw(unsigned long long seed, uint32_t step, uint32_t ant,
+                                             uint32_t iteration) {
+  return philox4x32_10(step, ant, iteration, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// ceil(log2 v) for v >= 1.
+__host__ __device__ __forceinline__ int ceil_log2_u32(uint32_t v) {
+#ifdef __CUDA_ARCH__
+  return v <= 1 ? 0 : 32 - __clz(v - 1);
+#else
+  int c = 0;
+  while ((1ull << c) < v) ++c;
+  return c;
+#endif
+}
+
+// Unbiased exponent floor(log2 x) of a positive finite float given its bits
+// (subnormals included: 2^-149 has exponent -149).
+__device__ __forceinline__ int exponent_of_bits(uint32_t b) {
+  return b >= 0x00800000u ? (int)(b >> 23) - 127 : -118 - __clz(b);
+}
+
+// 2^e as a float, for -126 <= e <= 127.
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// 2^e as a double, for -1022 <= e <= 1023.
+__device__ __forceinline__ double pow2d(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int src) {
+  return __shfl_sync(FULL, v, src);
+}
+
+// choice_info = tau^alpha * eta^beta (alpha == 1: one rounding).
+__device__ __forceinline__ float choice_of(float tau, float heta, float alpha) {
+  if (alpha == 1.0f) return __fmul_rn(tau, heta);
+  if (alpha == 0.0f) return heta;
+  return __fmul_rn(powf(tau, alpha), heta);
+}
+
+// Bounded spin helper: every device-side wait in this library gives up after
+// this many polls and reports kStatusTimeout.
+constexpr long long kSpinLimit = 1ll << 26;
+
+}  // namespace aco

@@ -1,0 +1,565 @@
+// C ABI of the single-instance Ant System (include/aco.h).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/aco.h"
+#include "aco_device.cuh"
+#include "kernels.h"
+#include "runtime.h"
+
+namespace aco {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? ACO_ENOMEM : ACO_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// Construction tilings
+// ---------------------------------------------------------------------------
+static const int kCg1[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80};
+static const int kCg2[] = {8, 12, 16, 20, 24, 32, 40, 48, 64};
+static const int kCg4[] = {4, 8, 12, 16, 20, 24, 32};
+
+bool construct_supported(int C, int G) {
+  const int* set = G == 1 ? kCg1 : G == 2 ? kCg2 : G == 4 ? kCg4 : nullptr;
+  const int cnt = G == 1 ? 11 : G == 2 ? 9 : G == 4 ? 7 : 0;
+  for (int i = 0; i < cnt; ++i)
+    if (set && set[i] == C) return true;
+  return false;
+}
+
+ConstructTiling construct_tiling(int n, int G, int A) {
+  const int* set = G == 1 ? kCg1 : G == 2 ? kCg2 : G == 4 ? kCg4 : nullptr;
+  const int cnt = G == 1 ? 11 : G == 2 ? 9 : G == 4 ? 7 : 0;
+  for (int i = 0; i < cnt; ++i)
+    if (32 * G * set[i] >= n) return ConstructTiling{set[i], G, A};
+  return ConstructTiling{0, G, A};
+}
+
+ConstructTiling default_construct_tiling(int n) {
+  if (n <= 32 * 80) return construct_tiling(n, 1, 4);
+  return construct_tiling(n, 2, 2);
+}
+
+cudaError_t launch_construct(const Instance& I, ConstructTiling t, cudaStream_t st) {
+  if (t.G * t.A > 8) return cudaErrorInvalidValue;
+  switch (t.G) {
+    case 1:
+      return launch_construct_g1(I, t.C, t.A, st);
+    case 2:
+      return launch_construct_g2(I, t.C, t.A, st);
+    case 4:
+      return launch_construct_g4(I, t.C, t.A, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+  return sms;
+}
+
+int validate_instance(int32_t n, const int32_t* dist, float alpha, float beta, float rho,
+                      int32_t m) {
+  if (n < 3 || n > ACO_MAX_N) return fail(ACO_EINVAL, "n=%d outside [3, %d]", n, ACO_MAX_N);
+  if (m < 1 || m > ACO_MAX_M) return fail(ACO_EINVAL, "m=%d outside [1, %d]", m, ACO_MAX_M);
+  if (!dist) return fail(ACO_EINVAL, "dist is NULL");
+  if (!std::isfinite(alpha) || alpha < 0.0f) return fail(ACO_EINVAL, "alpha must be finite and >= 0");
+  if (!std::isfinite(beta) || beta < 0.0f) return fail(ACO_EINVAL, "beta must be finite and >= 0");
+  if (!(rho > 0.0f && rho <= 1.0f)) return fail(ACO_EINVAL, "rho must lie in (0, 1]");
+  for (int i = 0; i < n; ++i) {
+    if (dist[(size_t)i * n + i] != 0) return fail(ACO_EINVAL, "dist[%d][%d] != 0", i, i);
+    for (int j = i + 1; j < n; ++j) {
+      const int32_t a = dist[(size_t)i * n + j], b = dist[(size_t)j * n + i];
+      if (a != b) return fail(ACO_EINVAL, "dist not symmetric at (%d,%d)", i, j);
+      if (a < 1) return fail(ACO_EINVAL, "dist[%d][%d]=%d, must be >= 1", i, j, a);
+    }
+  }
+  return ACO_OK;
+}
+
+}  // namespace aco
+
+using namespace aco;
+
+// ---------------------------------------------------------------------------
+// The handle
+// ---------------------------------------------------------------------------
+struct aco_colony {
+  Instance I{};
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  int sms = 148;
+  int deposit = kDepositGather;
+  int use_graph = 1;
+  int profile = 0;
+  int warps_per_ant = 0;
+  int ants_per_cta = 0;
+  bool tours_valid = false;
+  bool constructed = false;
+  long long host_iteration = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[ACO_NUM_PHASES + 1] = {};
+};
+
+static ConstructTiling tiling_of(const aco_colony* h) {
+  const int n = h->I.n;
+  if (h->warps_per_ant == 0) {
+    ConstructTiling t = default_construct_tiling(n);
+    if (h->ants_per_cta) t.A = h->ants_per_cta;
+    return t;
+  }
+  const int G = h->warps_per_ant;
+  int A = h->ants_per_cta ? h->ants_per_cta : (G == 1 ? 4 : G == 2 ? 2 : 1);
+  return construct_tiling(n, G, A);
+}
+
+// External records so that the events also become graph nodes under capture.
+static cudaError_t record_event(aco_colony* h, cudaEvent_t ev, cudaStream_t st) {
+  (void)h;
+  return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+}
+
+static void drop_graph(aco_colony* h) {
+  if (h->exec) {
+    cudaGraphExecDestroy(h->exec);
+    h->exec = nullptr;
+  }
+}
+
+static int enqueue_construct(aco_colony* h) {
+  const ConstructTiling t = tiling_of(h);
+  if (t.C == 0) return fail(ACO_EINVAL, "no construction tiling for n=%d", h->I.n);
+  cudaError_t e;
+  if (h->profile && (e = record_event(h, h->ev[0], h->stream)) != cudaSuccess)
+    return cuda_fail(e, "event");
+  if ((e = launch_construct(h->I, t, h->stream)) != cudaSuccess) return cuda_fail(e, "construct");
+  if (h->profile && (e = record_event(h, h->ev[1], h->stream)) != cudaSuccess)
+    return cuda_fail(e, "event");
+  if ((e = launch_best(h->I, h->stream)) != cudaSuccess) return cuda_fail(e, "best");
+  if (h->profile && (e = record_event(h, h->ev[2], h->stream)) != cudaSuccess)
+    return cuda_fail(e, "event");
+  return ACO_OK;
+}
+
+static int enqueue_update(aco_colony* h) {
+  cudaError_t e;
+  if ((e = launch_deposit(h->I, h->deposit, h->sms, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "deposit");
+  if (h->profile && (e = record_event(h, h->ev[3], h->stream)) != cudaSuccess)
+    return cuda_fail(e, "event");
+  if ((e = launch_update(h->I, h->deposit, h->sms, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "update");
+  if (h->profile && (e = record_event(h, h->ev[4], h->stream)) != cudaSuccess)
+    return cuda_fail(e, "event");
+  return ACO_OK;
+}
+
+static int check_status(aco_colony* h) {
+  int status = 0;
+  cudaError_t e = cudaMemcpyAsync(&status, &h->I.st->status, sizeof(int), cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  if (status & kStatusTimeout) return fail(ACO_ETIMEOUT, "a device-side wait gave up");
+  if (status) return fail(ACO_ECUDA, "device status 0x%x", status);
+  return ACO_OK;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+extern "C" {
+
+const char* aco_strerror(int code) {
+  switch (code) {
+    case ACO_OK:
+      return "ACO_OK";
+    case ACO_EINVAL:
+      return "ACO_EINVAL: invalid argument";
+    case ACO_ENOMEM:
+      return "ACO_ENOMEM: out of memory";
+    case ACO_ECUDA:
+      return "ACO_ECUDA: CUDA error";
+    case ACO_ESTATE:
+      return "ACO_ESTATE: call not valid in this state";
+    case ACO_ETIMEOUT:
+      return "ACO_ETIMEOUT: device-side wait gave up";
+    case ACO_EBUSY:
+      return "ACO_EBUSY: no free slot or memory budget";
+    default:
+      return "unknown ACO error code";
+  }
+}
+
+const char* aco_last_error_message(void) { return g_err; }
+
+int aco_create(int32_t n, const int32_t* dist, float alpha, float beta, float rho, int32_t m,
+               uint64_t seed, aco_handle* out) {
+  if (!out) return fail(ACO_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_instance(n, dist, alpha, beta, rho, m);
+  if (rc) return rc;
+  aco_colony* h = new (std::nothrow) aco_colony();
+  if (!h) return fail(ACO_ENOMEM, "host allocation");
+  Instance& I = h->I;
+  I.n = n;
+  I.m = m;
+  I.ld = (int)align_up((size_t)n, 4);
+  I.ldt = (int)align_up((size_t)n + 1, 4);
+  I.ldm = (int)align_up((size_t)m, 32);
+  I.alpha = alpha;
+  I.beta = beta;
+  I.rho = rho;
+  I.seed = seed;
+  const size_t mat = (size_t)n * I.ld;
+  // Arena layout (every block 256-byte aligned).
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_dist = take(mat * 4), o_heta = take(mat * 4), o_tau = take(mat * 4),
+               o_choice = take(mat * 4), o_tours = take((size_t)m * I.ldt * 4),
+               o_lens = take((size_t)m * 8), o_nbr = take((size_t)n * I.ldm * 4),
+               o_q = take((size_t)m * 8), o_delta = take((size_t)m * 4),
+               o_acc = take(mat * 8), o_best = take(((size_t)n + 1) * 4),
+               o_st = take(sizeof(IterState));
+  h->arena_bytes = off;
+  cudaError_t e = cudaMalloc(&h->arena, off);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  char* b = (char*)h->arena;
+  I.dist = (const int32_t*)(b + o_dist);
+  I.heta = (float*)(b + o_heta);
+  I.tau = (float*)(b + o_tau);
+  I.choice = (float*)(b + o_choice);
+  I.tours = (int32_t*)(b + o_tours);
+  I.lens = (long long*)(b + o_lens);
+  I.nbr = (uint32_t*)(b + o_nbr);
+  I.q = (unsigned long long*)(b + o_q);
+  I.delta = (float*)(b + o_delta);
+  I.acc = (unsigned long long*)(b + o_acc);
+  I.best_tour = (int32_t*)(b + o_best);
+  I.st = (IterState*)(b + o_st);
+  h->sms = device_sms();
+  rc = ACO_OK;
+  do {
+    if ((e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      rc = cuda_fail(e, "stream");
+      break;
+    }
+    h->stream = h->own_stream;
+    for (int i = 0; i <= ACO_NUM_PHASES; ++i)
+      if ((e = cudaEventCreate(&h->ev[i])) != cudaSuccess) break;
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "event");
+      break;
+    }
+    if ((e = cudaMemsetAsync(h->arena, 0, off, h->stream)) != cudaSuccess) {
+      rc = cuda_fail(e, "memset");
+      break;
+    }
+    IterState st0{};
+    st0.best_len = INT64_MAX;
+    if ((e = cudaMemcpyAsync(I.st, &st0, sizeof st0, cudaMemcpyHostToDevice, h->stream)) !=
+        cudaSuccess) {
+      rc = cuda_fail(e, "upload state");
+      break;
+    }
+    // dist: n rows of n int32 into rows of ld (padding stays zero).
+    if ((e = cudaMemcpy2DAsync((void*)I.dist, (size_t)I.ld * 4, dist, (size_t)n * 4, (size_t)n * 4,
+                               (size_t)n, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) {
+      rc = cuda_fail(e, "upload dist");
+      break;
+    }
+    if ((e = launch_setup(I, h->sms, h->stream)) != cudaSuccess) {
+      rc = cuda_fail(e, "setup");
+      break;
+    }
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+      rc = cuda_fail(e, "setup sync");
+      break;
+    }
+  } while (0);
+  if (rc) {
+    aco_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return ACO_OK;
+}
+
+int aco_destroy(aco_handle h) {
+  if (!h) return ACO_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  for (int i = 0; i <= ACO_NUM_PHASES; ++i)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  if (h->arena) cudaFree(h->arena);
+  delete h;
+  return ACO_OK;
+}
+
+int aco_choice_info(aco_handle h, float* out) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  cudaError_t e = launch_choice(h->I, h->sms, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "choice");
+  if (out) {
+    const int n = h->I.n;
+    e = cudaMemcpy2DAsync(out, (size_t)n * 4, h->I.choice, (size_t)h->I.ld * 4, (size_t)n * 4, n,
+                          cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy choice");
+    return check_status(h);
+  }
+  return ACO_OK;
+}
+
+int aco_construct_tours(aco_handle h, int32_t* tours, int64_t* lens) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  int rc = enqueue_construct(h);
+  if (rc) return rc;
+  h->tours_valid = true;
+  h->constructed = true;
+  cudaError_t e;
+  const int n = h->I.n, m = h->I.m;
+  if (tours &&
+      (e = cudaMemcpy2DAsync(tours, (size_t)(n + 1) * 4, h->I.tours, (size_t)h->I.ldt * 4,
+                             (size_t)(n + 1) * 4, m, cudaMemcpyDeviceToHost, h->stream)) !=
+          cudaSuccess)
+    return cuda_fail(e, "copy tours");
+  if (lens && (e = cudaMemcpyAsync(lens, h->I.lens, (size_t)m * 8, cudaMemcpyDeviceToHost,
+                                   h->stream)) != cudaSuccess)
+    return cuda_fail(e, "copy lens");
+  if (tours || lens) return check_status(h);
+  return ACO_OK;
+}
+
+int aco_update_pheromone(aco_handle h) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  if (!h->tours_valid) return fail(ACO_ESTATE, "no tours constructed since the last update");
+  int rc = enqueue_update(h);
+  if (rc) return rc;
+  h->tours_valid = false;
+  h->host_iteration += 1;
+  return ACO_OK;
+}
+
+int aco_iterate(aco_handle h, int32_t iterations) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  if (iterations < 0) return fail(ACO_EINVAL, "iterations < 0");
+  if (iterations == 0) return ACO_OK;
+  cudaError_t e;
+  if (h->use_graph) {
+    if (!h->exec) {
+      cudaGraph_t g = nullptr;
+      if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin capture");
+      int rc = enqueue_construct(h);
+      if (!rc) rc = enqueue_update(h);
+      e = cudaStreamEndCapture(h->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "end capture");
+      e = cudaGraphInstantiate(&h->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        h->exec = nullptr;
+        return cuda_fail(e, "instantiate");
+      }
+    }
+    for (int i = 0; i < iterations; ++i)
+      if ((e = cudaGraphLaunch(h->exec, h->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+  } else {
+    for (int i = 0; i < iterations; ++i) {
+      int rc = enqueue_construct(h);
+      if (!rc) rc = enqueue_update(h);
+      if (rc) return rc;
+    }
+  }
+  h->constructed = true;
+  h->tours_valid = false;
+  h->host_iteration += iterations;
+  return ACO_OK;
+}
+
+int aco_best_tour(aco_handle h, int32_t* tour, int64_t* len) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  if (!h->constructed) return fail(ACO_ESTATE, "no tour constructed yet");
+  cudaError_t e;
+  if (tour && (e = cudaMemcpyAsync(tour, h->I.best_tour, ((size_t)h->I.n + 1) * 4,
+                                   cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "copy best tour");
+  if (len && (e = cudaMemcpyAsync(len, &h->I.st->best_len, 8, cudaMemcpyDeviceToHost,
+                                  h->stream)) != cudaSuccess)
+    return cuda_fail(e, "copy best len");
+  return check_status(h);
+}
+
+int aco_get_pheromone(aco_handle h, float* tau) {
+  if (!h || !tau) return fail(ACO_EINVAL, "NULL argument");
+  const int n = h->I.n;
+  cudaError_t e = cudaMemcpy2DAsync(tau, (size_t)n * 4, h->I.tau, (size_t)h->I.ld * 4,
+                                    (size_t)n * 4, n, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy tau");
+  return check_status(h);
+}
+
+int aco_get_heuristic(aco_handle h, float* heta) {
+  if (!h || !heta) return fail(ACO_EINVAL, "NULL argument");
+  const int n = h->I.n;
+  cudaError_t e = cudaMemcpy2DAsync(heta, (size_t)n * 4, h->I.heta, (size_t)h->I.ld * 4,
+                                    (size_t)n * 4, n, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy heta");
+  return check_status(h);
+}
+
+int aco_get_iteration(aco_handle h, int64_t* iteration) {
+  if (!h || !iteration) return fail(ACO_EINVAL, "NULL argument");
+  unsigned long long it = 0;
+  cudaError_t e = cudaMemcpyAsync(&it, &h->I.st->iteration, 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy iteration");
+  int rc = check_status(h);
+  *iteration = (int64_t)it;
+  return rc;
+}
+
+int aco_get_tau0(aco_handle h, float* tau0, int64_t* nn_len) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  IterState st{};
+  cudaError_t e = cudaMemcpyAsync(&st, h->I.st, sizeof st, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy state");
+  int rc = check_status(h);
+  if (tau0) *tau0 = st.tau0;
+  if (nn_len) *nn_len = st.nn_len;
+  return rc;
+}
+
+int aco_set_option(aco_handle h, int32_t key, int64_t value) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  switch (key) {
+    case ACO_OPT_DEPOSIT:
+      if (value < 0 || value > 2) return fail(ACO_EINVAL, "deposit variant %lld", (long long)value);
+      h->deposit = (int)value;
+      break;
+    case ACO_OPT_STREAM:
+      h->stream = value ? (cudaStream_t)(intptr_t)value : h->own_stream;
+      break;
+    case ACO_OPT_USE_GRAPH:
+      h->use_graph = value != 0;
+      break;
+    case ACO_OPT_PROFILE:
+      h->profile = value != 0;
+      break;
+    case ACO_OPT_WARPS_PER_ANT: {
+      if (value != 0 && value != 1 && value != 2 && value != 4)
+        return fail(ACO_EINVAL, "warps per ant must be 0, 1, 2 or 4");
+      const int old = h->warps_per_ant;
+      h->warps_per_ant = (int)value;
+      if (tiling_of(h).C == 0) {
+        h->warps_per_ant = old;
+        return fail(ACO_EINVAL, "no tiling with %lld warps per ant for n=%d", (long long)value,
+                    h->I.n);
+      }
+      break;
+    }
+    case ACO_OPT_ANTS_PER_CTA:
+      if (value < 0 || value > 8) return fail(ACO_EINVAL, "ants per CTA must be in [0, 8]");
+      {
+        const int old = h->ants_per_cta;
+        h->ants_per_cta = (int)value;
+        const ConstructTiling t = tiling_of(h);
+        if (t.G * t.A > 8) {
+          h->ants_per_cta = old;
+          return fail(ACO_EINVAL, "more than 8 warps per CTA");
+        }
+      }
+      break;
+    default:
+      return fail(ACO_EINVAL, "unknown option %d", key);
+  }
+  drop_graph(h);
+  return ACO_OK;
+}
+
+int aco_get_option(aco_handle h, int32_t key, int64_t* value) {
+  if (!h || !value) return fail(ACO_EINVAL, "NULL argument");
+  switch (key) {
+    case ACO_OPT_DEPOSIT:
+      *value = h->deposit;
+      break;
+    case ACO_OPT_STREAM:
+      *value = (int64_t)(intptr_t)h->stream;
+      break;
+    case ACO_OPT_USE_GRAPH:
+      *value = h->use_graph;
+      break;
+    case ACO_OPT_PROFILE:
+      *value = h->profile;
+      break;
+    case ACO_OPT_WARPS_PER_ANT:
+      *value = tiling_of(h).G;
+      break;
+    case ACO_OPT_ANTS_PER_CTA:
+      *value = tiling_of(h).A;
+      break;
+    default:
+      return fail(ACO_EINVAL, "unknown option %d", key);
+  }
+  return ACO_OK;
+}
+
+int aco_get_kernel_times(aco_handle h, float* ms) {
+  if (!h || !ms) return fail(ACO_EINVAL, "NULL argument");
+  if (!h->profile) return fail(ACO_ESTATE, "profiling is off");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  for (int p = 0; p < ACO_NUM_PHASES; ++p) {
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, h->ev[p], h->ev[p + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "elapsed time");
+    ms[p] = t;
+  }
+  return ACO_OK;
+}
+
+int aco_synchronize(aco_handle h) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  return check_status(h);
+}
+
+int aco_kernel_launches_per_iteration(aco_handle h, int32_t* count) {
+  if (!h || !count) return fail(ACO_EINVAL, "NULL argument");
+  *count = launches_for_variant(h->deposit);
+  return ACO_OK;
+}
+
+}  // extern "C"

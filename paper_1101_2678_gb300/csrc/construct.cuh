@@ -1,0 +1,287 @@
+// Tour construction (Section II, Eq. 1; data-parallel design of Section III-A).
+//
+// One group of G warps builds one ant's tour.  Thread t of the group owns the
+// contiguous cities [t*C, t*C + C) of every row: it loads them with float4
+// loads into registers, keeps their tabu bits (the paper's "1 = unvisited"
+// integer per city, here one bit per city in registers) and takes part in the
+// selection.  Each step:
+//   1. load row choice[cur] (C floats per thread), zero visited cities;
+//   2. M = max over unvisited (REDUX on the float bit patterns, which order
+//      like the values for w >= 0), across warps through shared memory;
+//   3. q_j = floor(w_j * 2^(B-1-ilogb M)), per-thread u64 sums, warp
+//      inclusive scan, group totals -> Q;
+//   4. T = floor(r Q / 2^64) with r from Philox (one Philox call per lane per
+//      32 steps, broadcast by shuffle);
+//   5. the thread whose prefix range holds T is found by ballot; its chunk is
+//      rescanned by all 32 lanes of its warp (P = ceil(C/32) cities each),
+//      a second scan and ballot give the city.
+// Every operation is an exact max or an exact integer sum, so the chosen city
+// is the same for every (C, G) tiling and equals the CPU oracle's choice.
+// After the last step the group computes C^k = sum of d over the tour and
+// writes, for every city of the tour, its predecessor and successor into
+// nbr[city][ant] (the bucketing used by the gather deposit).
+#pragma once
+
+#include "aco_device.cuh"
+
+namespace aco {
+
+struct GroupSmem {
+  uint32_t wmax[4];
+  unsigned long long wsum[4];
+  long long wlen[4];
+  int wmin[4];
+  int next;
+};
+
+constexpr int kMaxGroupsPerCta = 8;
+
+__device__ __forceinline__ void group_sync(int bar_id, int nthreads) {
+  if (nthreads == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
+  }
+}
+
+// floor(v * 2^sc) for v >= 0 with the scale passed as one or two float powers
+// of two (the product is exact: scaling by a power of two never rounds unless
+// the result is below 2^-126, and then the floor is 0 either way).
+template <bool kTwo>
+__device__ __forceinline__ unsigned long long quantise(float v, float f1, float f2) {
+  float y = __fmul_rn(v, f1);
+  if (kTwo) y = __fmul_rn(y, f2);
+  return __float2ull_rz(y);
+}
+
+template <int C>
+__device__ __forceinline__ unsigned long long chunk_sum(const float (&v)[C], float f1, float f2,
+                                                        bool two) {
+  unsigned long long s = 0;
+  if (!two) {
+#pragma unroll
+    for (int i = 0; i < C; ++i) s += quantise<false>(v[i], f1, f2);
+  } else {
+#pragma unroll
+    for (int i = 0; i < C; ++i) s += quantise<true>(v[i], f1, f2);
+  }
+  return s;
+}
+
+__device__ __forceinline__ unsigned long long warp_inclusive_scan(unsigned long long x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += t;
+  }
+  return x;
+}
+
+template <int C, int G>
+__device__ __forceinline__ void construct_ant(const Instance& I, const int ant, const int tg,
+                                              GroupSmem* gs, const int bar_id) {
+  static_assert(C % 4 == 0 && C >= 4 && C <= 128, "C must be a multiple of 4 in [4,128]");
+  static_assert(G == 1 || G == 2 || G == 4, "G must be 1, 2 or 4");
+  constexpr int NW = (C + 31) / 32;  // tabu words per thread
+  constexpr int P = (C + 31) / 32;   // cities per lane in the rescan
+  constexpr int NT = 32 * G;
+  const int n = I.n, ld = I.ld;
+  const int lane = tg & 31, wg = tg >> 5;
+  const int base = tg * C;
+  const uint32_t iter = (uint32_t)I.st->iteration;
+  const int B = 62 - ceil_log2_u32((uint32_t)n);
+  const unsigned long long seed = I.seed;
+
+  // Tabu bits: 1 = visited.  Padding cities (index >= n) and bits beyond C
+  // start out visited.
+  uint32_t vis[NW];
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const int real = n - (base + 32 * w);  // local cities of word w below n
+    uint32_t word = real <= 0 ? FULL : (real >= 32 ? 0u : (FULL << real));
+    const int inchunk = C - 32 * w;
+    if (inchunk < 32) word |= FULL << inchunk;
+    vis[w] = word;
+  }
+
+  const Philox4 x0 = step_draw(seed, 0u, (uint32_t)ant, iter);
+  const int start = (int)__umulhi(x0.x0, (uint32_t)n);
+  {
+    const int li = start - base;
+    if (li >= 0 && li < C) {
+#pragma unroll
+      for (int w = 0; w < NW; ++w)
+        if (w == (li >> 5)) vis[w] |= 1u << (li & 31);
+    }
+  }
+  int32_t* tour = I.tours + (size_t)ant * I.ldt;
+  if (tg == 0) tour[0] = start;
+  int cur = start;
+  unsigned long long rwin = 0;
+
+  for (int s = 1; s < n; ++s) {
+    const int off = (s - 1) & 31;
+    if (off == 0) {
+      const Philox4 x = step_draw(seed, (uint32_t)(s + lane), (uint32_t)ant, iter);
+      rwin = ((unsigned long long)x.x1 << 32) | x.x0;
+    }
+    const unsigned long long r = shfl_u64(rwin, off);
+    const float* row = I.choice + (size_t)cur * ld;
+
+    float v[C];
+#pragma unroll
+    for (int i = 0; i < C; i += 4) {
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (base + i < ld) t = __ldg(reinterpret_cast<const float4*>(row + base + i));
+      v[i] = t.x;
+      v[i + 1] = t.y;
+      v[i + 2] = t.z;
+      v[i + 3] = t.w;
+    }
+    uint32_t mx = 0;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0.0f;
+      mx = max(mx, __float_as_uint(v[i]));
+    }
+    mx = __reduce_max_sync(FULL, mx);
+    if (G > 1) {
+      if (lane == 0) gs->wmax[wg] = mx;
+      group_sync(bar_id, NT);
+#pragma unroll
+      for (int w = 0; w < G; ++w) mx = max(mx, gs->wmax[w]);
+    }
+
+    int next;
+    if (mx == 0u) {
+      // Every unvisited weight is zero: the lowest-index unvisited city.
+      uint32_t cand = 0xffffffffu;
+#pragma unroll
+      for (int w = NW - 1; w >= 0; --w) {
+        const uint32_t fr = ~vis[w];
+        if (fr) cand = (uint32_t)(base + 32 * w + __ffs(fr) - 1);
+      }
+      cand = __reduce_min_sync(FULL, cand);
+      if (G > 1) {
+        if (lane == 0) gs->wmin[wg] = (int)cand;
+        group_sync(bar_id, NT);
+#pragma unroll
+        for (int w = 0; w < G; ++w) cand = min(cand, (uint32_t)gs->wmin[w]);
+      }
+      next = (int)cand;
+    } else {
+      const int sc = B - 1 - exponent_of_bits(mx);
+      const bool two = sc > 127;
+      const float f1 = two ? pow2f(127) : pow2f(sc);
+      const float f2 = two ? pow2f(sc - 127) : 1.0f;
+      const unsigned long long mine = chunk_sum<C>(v, f1, f2, two);
+      const unsigned long long incl = warp_inclusive_scan(mine, lane);
+      const unsigned long long wtot = shfl_u64(incl, 31);
+      unsigned long long woff = 0, Q = wtot;
+      if (G > 1) {
+        if (lane == 0) gs->wsum[wg] = wtot;
+        group_sync(bar_id, NT);
+        Q = 0;
+#pragma unroll
+        for (int w = 0; w < G; ++w) {
+          const unsigned long long u = gs->wsum[w];
+          if (w < wg) woff += u;
+          Q += u;
+        }
+      }
+      const unsigned long long T = __umul64hi(r, Q);
+      next = 0;
+      if (G == 1 || (T >= woff && T - woff < wtot)) {
+        const unsigned long long t1 = T - woff;
+        const int L = max(__ffs(__ballot_sync(FULL, incl > t1)) - 1, 0);
+        const unsigned long long t2 = t1 - shfl_u64(incl - mine, L);
+        const int baseL = (wg * 32 + L) * C;
+        uint32_t visL[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) visL[w] = __shfl_sync(FULL, vis[w], L);
+        unsigned long long qv[P];
+        unsigned long long ps = 0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const int li = lane * P + p;
+          uint32_t word = FULL;
+#pragma unroll
+          for (int w = 0; w < NW; ++w)
+            if (w == (li >> 5)) word = visL[w];
+          float w8 = 0.0f;
+          if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u)) w8 = row[baseL + li];
+          qv[p] = two ? quantise<true>(w8, f1, f2) : quantise<false>(w8, f1, f2);
+          ps += qv[p];
+        }
+        const unsigned long long incl2 = warp_inclusive_scan(ps, lane);
+        const int L2 = max(__ffs(__ballot_sync(FULL, incl2 > t2)) - 1, 0);
+        int pick = 0;
+        if (lane == L2) {
+          unsigned long long c = incl2 - ps;
+          pick = -1;
+#pragma unroll
+          for (int p = 0; p < P; ++p) {
+            c += qv[p];
+            if (pick < 0 && c > t2) pick = p;
+          }
+        }
+        pick = max(__shfl_sync(FULL, pick, L2), 0);
+        next = baseL + L2 * P + pick;
+        if (G > 1 && lane == 0) gs->next = next;
+      }
+      if (G > 1) {
+        group_sync(bar_id, NT);
+        next = gs->next;
+      }
+    }
+
+    // A city outside [0, n) can only come from a defect; record it and stay
+    // in bounds instead of reading past the matrix.
+    if ((unsigned)next >= (unsigned)n) {
+      if (tg == 0) atomicOr(&I.st->status, kStatusBadTour);
+      next = start;
+    }
+    const int li = next - base;
+    if (li >= 0 && li < C) {
+#pragma unroll
+      for (int w = 0; w < NW; ++w)
+        if (w == (li >> 5)) vis[w] |= 1u << (li & 31);
+    }
+    if (tg == 0) tour[s] = next;
+    cur = next;
+  }
+  if (tg == 0) tour[n] = start;
+  group_sync(bar_id, NT);
+
+  // C^k (Section II) and the per-city neighbour buckets.
+  long long len = 0;
+  for (int s = tg; s < n; s += NT) {
+    const int a = tour[s], b = tour[s + 1];
+    const int p = tour[s == 0 ? n - 1 : s - 1];
+    len += I.dist[(size_t)a * ld + b];
+    I.nbr[(size_t)a * I.ldm + ant] = ((uint32_t)p << 16) | (uint32_t)b;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
+  if (G > 1) {
+    if (lane == 0) gs->wlen[wg] = len;
+    group_sync(bar_id, NT);
+    len = 0;
+#pragma unroll
+    for (int w = 0; w < G; ++w) len += gs->wlen[w];
+  }
+  if (tg == 0) I.lens[ant] = len;
+}
+
+// One CTA holds blockDim.x / (32 G) ant groups.
+template <int C, int G>
+__global__ void __launch_bounds__(256) construct_kernel(Instance I) {
+  __shared__ GroupSmem gs[kMaxGroupsPerCta];
+  const int grp = threadIdx.x / (32 * G);
+  const int tg = threadIdx.x % (32 * G);
+  const int ant = blockIdx.x * (blockDim.x / (32 * G)) + grp;
+  if (ant >= I.m) return;
+  construct_ant<C, G>(I, ant, tg, &gs[grp], 1 + grp);
+}
+
+}  // namespace aco

@@ -1,0 +1,44 @@
+// Construction kernel instantiations with 2 warp(s) per ant.
+#include "construct.cuh"
+#include "kernels.h"
+
+namespace aco {
+
+cudaError_t launch_construct_g2(const Instance& I, int C, int A, cudaStream_t st) {
+  const int threads = 32 * 2 * A;
+  const int grid = (I.m + A - 1) / A;
+  switch (C) {
+    case 8:
+      construct_kernel<8, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 12:
+      construct_kernel<12, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 16:
+      construct_kernel<16, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 20:
+      construct_kernel<20, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 24:
+      construct_kernel<24, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 32:
+      construct_kernel<32, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 40:
+      construct_kernel<40, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 48:
+      construct_kernel<48, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    case 64:
+      construct_kernel<64, 2><<<grid, threads, 0, st>>>(I);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace aco

@@ -1,0 +1,20 @@
+// Host-side helpers shared by the C ABI translation units.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace aco {
+
+// Record a message for aco_last_error_message() and return `code`.
+int fail(int code, const char* fmt, ...);
+// Map a CUDA error to ACO_ENOMEM / ACO_ECUDA with a message.
+int cuda_fail(cudaError_t e, const char* what);
+// Streaming multiprocessors of the current device.
+int device_sms();
+// Argument checks shared by aco_create and the batch/pool admission.
+int validate_instance(int32_t n, const int32_t* dist, float alpha, float beta, float rho,
+                      int32_t m);
+
+}  // namespace aco

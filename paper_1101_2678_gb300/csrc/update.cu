@@ -1,0 +1,421 @@
+// Setup, iteration-best and pheromone-update kernels (Section II, Eqs. 2-4;
+// Section III-B for the atomic and scatter-to-gather designs).
+#include <climits>
+
+#include "aco_device.cuh"
+#include "kernels.h"
+
+namespace aco {
+
+// ---------------------------------------------------------------------------
+// Setup
+// ---------------------------------------------------------------------------
+
+// Nearest-neighbour tour from city 0 (ties to the lower index), C_nn and
+// tau0 = m / C_nn.  One CTA; the cities of a row are strided over its threads.
+__global__ void nn_tour_kernel(Instance I) {
+  extern __shared__ uint32_t seen[];
+  __shared__ long long red_d[32];
+  __shared__ int red_j[32];
+  __shared__ int s_next;
+  const int n = I.n, ld = I.ld;
+  const int words = (n + 31) / 32;
+  for (int w = threadIdx.x; w < words; w += blockDim.x) seen[w] = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) seen[0] = 1u;
+  __syncthreads();
+  int cur = 0;
+  long long len = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int s = 1; s < n; ++s) {
+    long long bd = LLONG_MAX;
+    int bj = INT_MAX;
+    const int32_t* row = I.dist + (size_t)cur * ld;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      if ((seen[j >> 5] >> (j & 31)) & 1u) continue;
+      const long long dj = row[j];
+      if (dj < bd) {
+        bd = dj;
+        bj = j;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long od = __shfl_xor_sync(FULL, bd, o);
+      const int oj = __shfl_xor_sync(FULL, bj, o);
+      if (od < bd || (od == bd && oj < bj)) {
+        bd = od;
+        bj = oj;
+      }
+    }
+    if (lane == 0) {
+      red_d[warp] = bd;
+      red_j[warp] = bj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long d0 = red_d[0];
+      int j0 = red_j[0];
+      for (int w = 1; w < nwarps; ++w)
+        if (red_d[w] < d0 || (red_d[w] == d0 && red_j[w] < j0)) {
+          d0 = red_d[w];
+          j0 = red_j[w];
+        }
+      if ((unsigned)j0 >= (unsigned)n) {  // cannot happen while a city is unvisited
+        atomicOr(&I.st->status, kStatusBadTour);
+        j0 = 0;
+      }
+      s_next = j0;
+      seen[j0 >> 5] |= 1u << (j0 & 31);
+    }
+    __syncthreads();
+    const int nx = s_next;
+    len += row[nx];
+    cur = nx;
+  }
+  len += I.dist[(size_t)cur * ld];
+  if (threadIdx.x == 0) {
+    I.st->nn_len = len;
+    I.st->tau0 = (float)((double)I.m / (double)len);
+  }
+}
+
+// eta^beta (double, rounded once to float), tau = tau0 off the diagonal, and
+// the first choice_info.  Padding columns stay zero.
+__global__ void init_matrices_kernel(Instance I) {
+  const int n = I.n, ld = I.ld;
+  const size_t total = (size_t)n * ld;
+  const float tau0 = I.st->tau0;
+  const double beta = (double)I.beta;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    float h = 0.0f, t = 0.0f;
+    if (j < n && j != i) {
+      const double d = (double)I.dist[e];
+      double v;
+      if (beta == 0.0) v = 1.0;
+      else if (beta == 1.0) v = 1.0 / d;
+      else if (beta == 2.0) v = 1.0 / (d * d);
+      else if (beta == 3.0) v = 1.0 / (d * d * d);
+      else v = pow(d, -beta);
+      h = (float)v;
+      t = tau0;
+    }
+    I.heta[e] = h;
+    I.tau[e] = t;
+    I.choice[e] = (j < n && j != i) ? choice_of(t, h, I.alpha) : 0.0f;
+  }
+}
+
+// choice_info from the current tau (no state change).
+__global__ void choice_kernel(Instance I, int bump_iteration) {
+  const size_t total = (size_t)I.n * I.ld;
+  const float alpha = I.alpha;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    I.choice[e] = choice_of(I.tau[e], I.heta[e], alpha);
+  if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Iteration best, best-so-far and the per-ant deposits dtau^k, q_k.
+// ---------------------------------------------------------------------------
+__global__ void best_kernel(Instance I) {
+  __shared__ long long red_l[32];
+  __shared__ int red_k[32];
+  __shared__ int s_best, s_shift, s_improved;
+  const int m = I.m, n = I.n;
+  long long bl = LLONG_MAX;
+  int bk = INT_MAX;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const long long L = I.lens[k];
+    if (L < bl) {
+      bl = L;
+      bk = k;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ol = __shfl_xor_sync(FULL, bl, o);
+    const int ok = __shfl_xor_sync(FULL, bk, o);
+    if (ol < bl || (ol == bl && ok < bk)) {
+      bl = ol;
+      bk = ok;
+    }
+  }
+  if (lane == 0) {
+    red_l[warp] = bl;
+    red_k[warp] = bk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (red_l[w] < bl || (red_l[w] == bl && red_k[w] < bk)) {
+        bl = red_l[w];
+        bk = red_k[w];
+      }
+    const float dmax = (float)(1.0 / (double)bl);
+    const int S = 62 - ceil_log2_u32((uint32_t)m) - exponent_of_bits(__float_as_uint(dmax));
+    IterState* st = I.st;
+    st->iter_best_len = bl;
+    st->iter_best_ant = bk;
+    st->deposit_shift = S;
+    s_improved = bl < st->best_len;
+    if (s_improved) st->best_len = bl;
+    s_best = bk;
+    s_shift = S;
+  }
+  __syncthreads();
+  const double scale = pow2d(s_shift);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const float dk = (float)(1.0 / (double)I.lens[k]);
+    I.delta[k] = dk;
+    I.q[k] = __double2ull_rz((double)dk * scale);
+  }
+  if (s_improved) {
+    const int32_t* src = I.tours + (size_t)s_best * I.ldt;
+    for (int s = threadIdx.x; s <= n; s += blockDim.x) I.best_tour[s] = src[s];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pheromone update
+// ---------------------------------------------------------------------------
+
+// tau' = fl(fl((1-rho) tau) + dep), dep = fl(acc) * 2^-S (Eqs. 2-4).
+__device__ __forceinline__ float apply_deposit(float tau, unsigned long long acc, float keep,
+                                               float inv_scale) {
+  const float dep = __fmul_rn(__ull2float_rn(acc), inv_scale);
+  return __fadd_rn(__fmul_rn(keep, tau), dep);
+}
+
+__device__ __forceinline__ float inv_scale_of(int S) {
+  // 2^-S.  3 <= C^k < 2^44 (n <= 4096, int32 distances) and m <= 16384 put S
+  // in [50, 106], inside the normal float range.
+  return pow2f(-S);
+}
+
+// Atomic-free "scatter to gather" deposit fused with evaporation and
+// choice_info.  One warp per row i: the construction kernel bucketed every
+// tour edge under both of its cities (nbr[i][k] = predecessor and successor of
+// i in tour k), so row i's deposit is a segmented reduction of 2m (column,
+// q_k) pairs.  Lanes holding the same column are grouped with match.any and
+// summed by shuffles; the group leader adds the group sum to the warp's
+// private u64 row in shared memory.  No atomics, exact, deterministic.
+__global__ void update_gather_kernel(Instance I, int bump_iteration) {
+  extern __shared__ unsigned long long acc_rows[];
+  const int warps = blockDim.x >> 5;
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * warps + wi;
+  const int n = I.n, ld = I.ld, m = I.m;
+  if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
+  if (i >= n) return;
+  unsigned long long* acc = acc_rows + (size_t)wi * ld;
+  for (int j = lane; j < ld; j += 32) acc[j] = 0ull;
+  __syncwarp();
+  const uint32_t* nb = I.nbr + (size_t)i * I.ldm;
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    const int k = k0 + lane;
+    const bool valid = k < m;
+    const uint32_t ps = valid ? nb[k] : 0u;
+    const unsigned long long qk = valid ? I.q[k] : 0ull;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const uint32_t col = valid ? (half ? (ps & 0xffffu) : (ps >> 16)) : 0xffffffffu;
+      const uint32_t grp = __match_any_sync(FULL, col);
+      const int rounds = (int)__reduce_max_sync(FULL, (uint32_t)__popc(grp));
+      uint32_t rem = grp;
+      unsigned long long sum = 0;
+      for (int r = 0; r < rounds; ++r) {
+        const int src = rem ? __ffs(rem) - 1 : lane;
+        const unsigned long long val = shfl_u64(qk, src);
+        if (rem) {
+          sum += val;
+          rem &= rem - 1;
+        }
+      }
+      if (valid && lane == __ffs(grp) - 1) acc[col] += sum;
+      __syncwarp();
+    }
+  }
+  const float keep = __fsub_rn(1.0f, I.rho);
+  const float inv = inv_scale_of(I.st->deposit_shift);
+  const float alpha = I.alpha;
+  float* tau = I.tau + (size_t)i * ld;
+  const float* heta = I.heta + (size_t)i * ld;
+  float* ch = I.choice + (size_t)i * ld;
+  for (int j = lane * 4; j < ld; j += 128) {
+    const float4 t4 = *reinterpret_cast<const float4*>(tau + j);
+    const float4 h4 = *reinterpret_cast<const float4*>(heta + j);
+    float4 o, c;
+    o.x = apply_deposit(t4.x, acc[j + 0], keep, inv);
+    o.y = apply_deposit(t4.y, acc[j + 1], keep, inv);
+    o.z = apply_deposit(t4.z, acc[j + 2], keep, inv);
+    o.w = apply_deposit(t4.w, acc[j + 3], keep, inv);
+    c.x = choice_of(o.x, h4.x, alpha);
+    c.y = choice_of(o.y, h4.y, alpha);
+    c.z = choice_of(o.z, h4.z, alpha);
+    c.w = choice_of(o.w, h4.w, alpha);
+    *reinterpret_cast<float4*>(tau + j) = o;
+    *reinterpret_cast<float4*>(ch + j) = c;
+  }
+}
+
+// Atomic deposit in 64-bit fixed point: one thread per tour edge (k, s) adds
+// q_k to acc[a][b] and acc[b][a] with red.global.add.u64 (Fig. 2's design;
+// integer addition commutes, so the result is deterministic).
+__global__ void deposit_atomic_u64_kernel(Instance I) {
+  const int n = I.n, ld = I.ld;
+  const size_t total = (size_t)I.m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / n), s = (int)(e % n);
+    const int32_t* t = I.tours + (size_t)k * I.ldt;
+    const int a = t[s], b = t[s + 1];
+    const unsigned long long qk = I.q[k];
+    atomicAdd(I.acc + (size_t)a * ld + b, qk);
+    atomicAdd(I.acc + (size_t)b * ld + a, qk);
+  }
+}
+
+// Evaporation + fixed-point deposit + choice_info, elementwise; clears acc.
+__global__ void apply_acc_kernel(Instance I, int bump_iteration) {
+  const size_t total4 = (size_t)I.n * I.ld / 4;
+  const float keep = __fsub_rn(1.0f, I.rho);
+  const float inv = inv_scale_of(I.st->deposit_shift);
+  const float alpha = I.alpha;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total4;
+       e += (size_t)gridDim.x * blockDim.x) {
+    float4 t4 = reinterpret_cast<const float4*>(I.tau)[e];
+    const float4 h4 = reinterpret_cast<const float4*>(I.heta)[e];
+    ulonglong2* a2 = reinterpret_cast<ulonglong2*>(I.acc) + 2 * e;
+    const ulonglong2 a01 = a2[0], a23 = a2[1];
+    float4 c;
+    t4.x = apply_deposit(t4.x, a01.x, keep, inv);
+    t4.y = apply_deposit(t4.y, a01.y, keep, inv);
+    t4.z = apply_deposit(t4.z, a23.x, keep, inv);
+    t4.w = apply_deposit(t4.w, a23.y, keep, inv);
+    c.x = choice_of(t4.x, h4.x, alpha);
+    c.y = choice_of(t4.y, h4.y, alpha);
+    c.z = choice_of(t4.z, h4.z, alpha);
+    c.w = choice_of(t4.w, h4.w, alpha);
+    reinterpret_cast<float4*>(I.tau)[e] = t4;
+    reinterpret_cast<float4*>(I.choice)[e] = c;
+    a2[0] = make_ulonglong2(0ull, 0ull);
+    a2[1] = make_ulonglong2(0ull, 0ull);
+  }
+  if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
+}
+
+// The paper's atomic kernel: evaporation first (Eq. 2) ...
+__global__ void evaporate_kernel(Instance I) {
+  const size_t total4 = (size_t)I.n * I.ld / 4;
+  const float keep = __fsub_rn(1.0f, I.rho);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total4;
+       e += (size_t)gridDim.x * blockDim.x) {
+    float4 t4 = reinterpret_cast<const float4*>(I.tau)[e];
+    t4.x = __fmul_rn(keep, t4.x);
+    t4.y = __fmul_rn(keep, t4.y);
+    t4.z = __fmul_rn(keep, t4.z);
+    t4.w = __fmul_rn(keep, t4.w);
+    reinterpret_cast<float4*>(I.tau)[e] = t4;
+  }
+}
+
+// ... then red.global.add.f32 of dtau^k on both directions of every tour edge
+// (Eqs. 3-4; the order of the float additions is not deterministic).
+__global__ void deposit_atomic_f32_kernel(Instance I) {
+  const int n = I.n, ld = I.ld;
+  const size_t total = (size_t)I.m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / n), s = (int)(e % n);
+    const int32_t* t = I.tours + (size_t)k * I.ldt;
+    const int a = t[s], b = t[s + 1];
+    const float dk = I.delta[k];
+    atomicAdd(I.tau + (size_t)a * ld + b, dk);
+    atomicAdd(I.tau + (size_t)b * ld + a, dk);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers
+// ---------------------------------------------------------------------------
+static int grid_for(size_t work, int threads, int sms) {
+  size_t blocks = (work + threads - 1) / threads;
+  const size_t cap = (size_t)sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+cudaError_t launch_setup(const Instance& I, int sms, cudaStream_t st) {
+  int threads = 32 * ((I.n + 31) / 32);
+  if (threads > 1024) threads = 1024;
+  const size_t smem = sizeof(uint32_t) * ((I.n + 31) / 32);
+  nn_tour_kernel<<<1, threads, smem, st>>>(I);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  init_matrices_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_choice(const Instance& I, int sms, cudaStream_t st) {
+  choice_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best(const Instance& I, cudaStream_t st) {
+  best_kernel<<<1, 1024, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+int gather_warps_per_cta(int ld) {
+  // Shared memory per warp: one u64 row.  Keep a CTA at or below 96 KB.
+  int w = (96 * 1024) / (8 * ld);
+  if (w > 8) w = 8;
+  if (w < 1) w = 1;
+  return w;
+}
+
+cudaError_t launch_deposit(const Instance& I, int variant, int sms, cudaStream_t st) {
+  if (variant == kDepositAtomicU64) {
+    deposit_atomic_u64_kernel<<<grid_for((size_t)I.m * I.n, 256, sms), 256, 0, st>>>(I);
+  } else if (variant == kDepositAtomicF32) {
+    evaporate_kernel<<<grid_for((size_t)I.n * I.ld / 4, 256, sms), 256, 0, st>>>(I);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    deposit_atomic_f32_kernel<<<grid_for((size_t)I.m * I.n, 256, sms), 256, 0, st>>>(I);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t st) {
+  if (variant == kDepositGather) {
+    const int w = gather_warps_per_cta(I.ld);
+    const size_t smem = (size_t)w * I.ld * sizeof(unsigned long long);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(update_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           100 * 1024);
+      attr_set = true;
+    }
+    update_gather_kernel<<<(I.n + w - 1) / w, 32 * w, smem, st>>>(I, 1);
+  } else if (variant == kDepositAtomicU64) {
+    apply_acc_kernel<<<grid_for((size_t)I.n * I.ld / 4, 256, sms), 256, 0, st>>>(I, 1);
+  } else {
+    choice_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I, 1);
+  }
+  return cudaGetLastError();
+}
+
+int launches_for_variant(int variant) {
+  // construct + best + deposit kernels + update kernel
+  if (variant == kDepositGather) return 3;
+  if (variant == kDepositAtomicU64) return 4;
+  return 5;
+}
+
+}  // namespace aco

@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tours, lengths, eta^beta, tau0 and (for the deterministic deposits) tau must
+match the oracle bit for bit: every step is either integer arithmetic or a
+fixed sequence of IEEE-rounded float operations (readings R1-R7 of the
+oracle).  The non-deterministic float-atomic deposit is held to the error
+bound of m float additions.  The FP32 state is also held to 1e-5 relative of
+the FP64 recurrence (plus an absolute floor of 2^-126 for underflow).
+"""
+import numpy as np
+import pytest
+
+from paper_1101_2678_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aco():
+    from paper_1101_2678_gb300 import build
+    build.build()
+    from paper_1101_2678_gb300 import aco as a
+    a.load()
+    return a
+
+
+def oracle_initial_choice(orc, dist, m, alpha=1.0, beta=2.0):
+    n = dist.shape[0]
+    h = orc.heta(dist, beta)
+    tau = np.full((n, n), orc.tau0(dist, m), np.float32)
+    np.fill_diagonal(tau, 0)
+    return orc.choice(tau, h, alpha)
+
+
+def check_tours(t, lens, dist):
+    n = dist.shape[0]
+    for k in range(t.shape[0]):
+        assert t[k, n] == t[k, 0]
+        assert np.array_equal(np.sort(t[k, :n]), np.arange(n))
+        assert lens[k] == int(dist[t[k, :n], t[k, 1:]].astype(np.int64).sum())
+
+
+# ---------------------------------------------------------------------------
+# Setup
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,beta", [(3, 2.0), (48, 2.0), (97, 1.0), (130, 3.0), (300, 0.0)])
+def test_setup_matches_oracle(aco, orc, n, beta):
+    inst = I.uniform_instance(n, 1000, seed=n)
+    m = max(3, n // 2)
+    with aco.Colony(inst.dist, m, seed=1, beta=beta) as c:
+        assert np.array_equal(aco.aco_get_heuristic(c.h, n), orc.heta(inst.dist, beta))
+        tau0, nn = aco.aco_get_tau0(c.h)
+        assert nn == orc.nn_tour_length(inst.dist)
+        assert tau0 == orc.tau0(inst.dist, m)
+        ch = aco.aco_choice_info(c.h, n)
+        assert np.array_equal(ch, oracle_initial_choice(orc, inst.dist, m, beta=beta))
+        assert aco.aco_get_iteration(c.h) == 0
+
+
+# ---------------------------------------------------------------------------
+# Tour construction (Eq. 1)
+# ---------------------------------------------------------------------------
+
+TILINGS = [(0, 0), (1, 1), (1, 4), (2, 2), (4, 1), (4, 2)]
+
+
+@pytest.mark.parametrize("n", [3, 5, 31, 48, 97, 129, 300, 517])
+def test_first_iteration_tours_match_oracle(aco, orc, n):
+    inst = I.uniform_instance(n, 1000, seed=100 + n)
+    m = n + 3
+    ch = oracle_initial_choice(orc, inst.dist, m)
+    otours, olens = orc.construct(ch, inst.dist, m, seed=7, iteration=0)
+    with aco.Colony(inst.dist, m, seed=7) as c:
+        for G, A in TILINGS:
+            if G:
+                try:
+                    aco.aco_set_option(c.h, aco.ACO_OPT_WARPS_PER_ANT, G)
+                except aco.AcoError:
+                    continue  # no tiling for this n and G
+                aco.aco_set_option(c.h, aco.ACO_OPT_ANTS_PER_CTA, A)
+            tours, lens = aco.aco_construct_tours(c.h, n, m)
+            assert np.array_equal(tours, otours), (G, A)
+            assert np.array_equal(lens, olens), (G, A)
+
+
+@pytest.mark.parametrize("wl,ants", [("n1002", 12), ("n2392", 6)])
+def test_full_size_first_iteration_sampled(aco, orc, wl, ants):
+    w = getattr(I, "workload_" + wl)()
+    d, m = w["inst"].dist, w["m"]
+    n = d.shape[0]
+    ch = oracle_initial_choice(orc, d, m)
+    with aco.Colony(d, m, seed=w["seed"]) as c:
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+        check_tours(tours, lens, d)
+        for k in np.linspace(0, m - 1, ants).astype(int):
+            t, L = orc.construct_ant(ch, d, w["seed"], 0, int(k))
+            assert np.array_equal(tours[k], t), k
+            assert lens[k] == L
+
+
+def test_max_n_sampled(aco, orc):
+    n = 4096
+    inst = I.uniform_instance(n, 1000, seed=4096)
+    m = 64
+    ch = oracle_initial_choice(orc, inst.dist, m)
+    with aco.Colony(inst.dist, m, seed=3) as c:
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+        check_tours(tours, lens, inst.dist)
+        for k in [0, 63]:
+            t, L = orc.construct_ant(ch, inst.dist, 3, 0, k)
+            assert np.array_equal(tours[k], t) and lens[k] == L
+
+
+def test_construct_is_idempotent_and_graph_equals_eager(aco):
+    inst = I.uniform_instance(200, 1000, seed=5)
+    with aco.Colony(inst.dist, 64, seed=11) as a, aco.Colony(inst.dist, 64, seed=11) as b:
+        t1, _ = aco.aco_construct_tours(a.h, 200, 64)
+        t2, _ = aco.aco_construct_tours(a.h, 200, 64)
+        assert np.array_equal(t1, t2)
+        aco.aco_set_option(b.h, aco.ACO_OPT_USE_GRAPH, 0)
+        aco.aco_iterate(a.h, 5)
+        aco.aco_iterate(b.h, 5)
+        assert np.array_equal(aco.aco_get_pheromone(a.h, 200), aco.aco_get_pheromone(b.h, 200))
+        assert aco.aco_best_tour(a.h, 200)[1] == aco.aco_best_tour(b.h, 200)[1]
+        assert aco.aco_get_iteration(a.h) == 5
+
+
+def test_chi_squared_first_move_on_gpu(aco, orc):
+    # Frequencies of (start, second city) over many GPU ants against Eq. 1
+    # with the oracle's choice_info for iteration 0.
+    from scipy.stats import chisquare
+    inst = I.uniform_instance(6, 1000, seed=66)
+    m = 16384
+    ch = oracle_initial_choice(orc, inst.dist, m).astype(np.float64)
+    with aco.Colony(inst.dist, m, seed=5) as c:
+        tours, _ = aco.aco_construct_tours(c.h, 6, m)
+    counts = np.zeros((6, 6), np.int64)
+    np.add.at(counts, (tours[:, 0], tours[:, 1]), 1)
+    for i in range(6):
+        cand = [j for j in range(6) if j != i]
+        p = ch[i, cand] / ch[i, cand].sum()
+        assert counts[i, i] == 0
+        assert chisquare(counts[i, cand], p * counts[i].sum()).pvalue > 0.01
+
+
+# ---------------------------------------------------------------------------
+# Pheromone update (Eqs. 2-4) and whole runs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("deposit", ["GATHER", "ATOMIC_U64"])
+def test_n48_hundred_iterations_bit_exact(aco, orc, deposit):
+    w = I.workload_n48()
+    d = w["inst"].dist
+    ref = orc.run(d, w["m"], 100, w["seed"])
+    with aco.Colony(d, w["m"], seed=w["seed"]) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, getattr(aco, "ACO_DEPOSIT_" + deposit))
+        aco.aco_iterate(c.h, 99)
+        tours, lens = aco.aco_construct_tours(c.h, 48, 48)
+        aco.aco_update_pheromone(c.h)
+        tour, best = aco.aco_best_tour(c.h, 48)
+        tau = aco.aco_get_pheromone(c.h, 48)
+    assert np.array_equal(tours, ref["tours"]) and np.array_equal(lens, ref["lens"])
+    assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+    assert np.array_equal(tau, ref["tau32"])
+    r64 = ref["tau64"]
+    assert np.all(np.abs(tau - r64) <= 1e-5 * np.abs(r64) + 2.0 ** -126)
+
+
+@pytest.mark.parametrize("n,m,iters", [(130, 130, 12), (257, 100, 6), (400, 37, 4)])
+def test_multi_iteration_state_bit_exact(aco, orc, n, m, iters):
+    inst = I.clustered_instance(n, seed=n, clusters=8, sigma=300, side=5000)
+    ref = orc.run(inst.dist, m, iters, 77)
+    with aco.Colony(inst.dist, m, seed=77) as c:
+        aco.aco_iterate(c.h, iters)
+        tau = aco.aco_get_pheromone(c.h, n)
+        tour, best = aco.aco_best_tour(c.h, n)
+    assert np.array_equal(tau, ref["tau32"])
+    assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+    r64 = ref["tau64"]
+    assert np.all(np.abs(tau - r64) <= 1e-5 * np.abs(r64) + 2.0 ** -126)
+
+
+def test_float_atomic_deposit_within_rounding_bound(aco, orc):
+    # One update with red.global.add.f32 from the initial state: each cell is
+    # a sum of at most m float additions in some order, so the result lies
+    # within (m + 2) 2^-24 relative of the exact Eqs. 2-4 (oracle, fp64, on
+    # the oracle's own iteration-0 tours, which the GPU reproduces).
+    n, m = 300, 300
+    inst = I.uniform_instance(n, 1000, seed=31)
+    ch0 = oracle_initial_choice(orc, inst.dist, m)
+    otours, olens = orc.construct(ch0, inst.dist, m, seed=2, iteration=0)
+    tau0 = np.full((n, n), orc.tau0(inst.dist, m), np.float64)
+    np.fill_diagonal(tau0, 0)
+    exact = orc.update_fp64(tau0, otours, olens, 0.5)
+    with aco.Colony(inst.dist, m, seed=2) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, aco.ACO_DEPOSIT_ATOMIC_F32)
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+        aco.aco_update_pheromone(c.h)
+        tau = aco.aco_get_pheromone(c.h, n).astype(np.float64)
+        ch = aco.aco_choice_info(c.h, n)
+    assert np.array_equal(tours, otours) and np.array_equal(lens, olens)
+    assert np.all(np.abs(tau - exact) <= (m + 2) * 2.0 ** -24 * np.abs(exact) + 2.0 ** -126)
+    assert np.all(np.abs(tau - exact) <= 1e-5 * np.abs(exact) + 2.0 ** -126)
+    h = orc.heta(inst.dist, 2.0)
+    assert np.array_equal(ch, (tau.astype(np.float32) * h).astype(np.float32))
+
+
+def test_deposit_variants_agree(aco):
+    inst = I.uniform_instance(333, 1000, seed=8)
+    out = {}
+    for v in ["GATHER", "ATOMIC_U64"]:
+        with aco.Colony(inst.dist, 333, seed=9) as c:
+            aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, getattr(aco, "ACO_DEPOSIT_" + v))
+            aco.aco_iterate(c.h, 8)
+            out[v] = (aco.aco_get_pheromone(c.h, 333), aco.aco_best_tour(c.h, 333))
+    assert np.array_equal(out["GATHER"][0], out["ATOMIC_U64"][0])
+    assert out["GATHER"][1][1] == out["ATOMIC_U64"][1][1]
+
+
+def test_update_invariants_at_full_size(aco):
+    # n = 1002 after two iterations: tau symmetric, valid tours, and one
+    # update's deposit totals 2 n sum_k 1/C^k (Eqs. 3-4).
+    w = I.workload_n1002()
+    d, m = w["inst"].dist, w["m"]
+    n = d.shape[0]
+    with aco.Colony(d, m, seed=w["seed"]) as c:
+        aco.aco_iterate(c.h, 2)
+        before = aco.aco_get_pheromone(c.h, n)
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+        aco.aco_update_pheromone(c.h)
+        after = aco.aco_get_pheromone(c.h, n)
+    check_tours(tours, lens, d)
+    assert np.array_equal(after, after.T)
+    dep = after.astype(np.float64) - 0.5 * before.astype(np.float64)
+    assert abs(dep.sum() / (2 * n * (1.0 / lens).sum()) - 1) < 1e-5
+
+
+def test_single_ant_and_tiny_instances(aco, orc):
+    for n, m in [(3, 1), (4, 1), (5, 2), (7, 40)]:
+        inst = I.uniform_instance(n, 100, seed=n * 10 + m)
+        ref = orc.run(inst.dist, m, 5, 3)
+        with aco.Colony(inst.dist, m, seed=3) as c:
+            aco.aco_iterate(c.h, 5)
+            assert np.array_equal(aco.aco_get_pheromone(c.h, n), ref["tau32"])
+            assert aco.aco_best_tour(c.h, n)[1] == ref["best_len"]
+
+
+def test_long_run_underflow_and_zero_weights(aco, orc):
+    # 200 iterations at rho = 0.9: never-reinforced pheromone underflows to
+    # subnormals and zero, exercising the subnormal path of the roulette and
+    # the "all unvisited weights zero" rule.
+    inst = I.uniform_instance(40, 1000, seed=4)
+    ref = orc.run(inst.dist, 20, 200, 12, rho=0.9)
+    with aco.Colony(inst.dist, 20, seed=12, rho=0.9) as c:
+        aco.aco_iterate(c.h, 200)
+        tau = aco.aco_get_pheromone(c.h, 40)
+        best = aco.aco_best_tour(c.h, 40)
+    assert np.array_equal(tau, ref["tau32"])
+    assert best[1] == ref["best_len"]
+    assert (tau == 0).sum() > 40  # underflow really happened
+
+
+def test_state_errors(aco):
+    inst = I.uniform_instance(10, 100, seed=1)
+    with aco.Colony(inst.dist, 4, seed=1) as c:
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_best_tour(c.h, 10)
+        assert e.value.code == aco.ACO_ESTATE
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_update_pheromone(c.h)
+        assert e.value.code == aco.ACO_ESTATE
+        aco.aco_construct_tours(c.h)
+        aco.aco_update_pheromone(c.h)
+        with pytest.raises(aco.AcoError):
+            aco.aco_update_pheromone(c.h)
+        with pytest.raises(aco.AcoError):
+            aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, 7)
+
+
+def test_profiled_phase_times(aco):
+    inst = I.uniform_instance(500, 1000, seed=3)
+    with aco.Colony(inst.dist, 500, seed=1) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_PROFILE, 1)
+        aco.aco_iterate(c.h, 2)
+        t = aco.aco_get_kernel_times(c.h)
+        assert t[aco.ACO_PHASE_CONSTRUCT] > 0 and t[aco.ACO_PHASE_UPDATE] > 0
+        assert aco.aco_kernel_launches_per_iteration(c.h) == 3
