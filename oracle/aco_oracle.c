@@ -31,8 +31,9 @@
  *     start = floor(x0 * n / 2^32) ("ants are randomly placed", Section II).
  *     Step s >= 1 draws r = x1 * 2^32 + x0.
  *  R2 Eq. 1 is sampled by an exact integer roulette: with M the largest weight
- *     among unvisited cities and B = 62 - ceil(log2 n), each unvisited weight
- *     w_j becomes q_j = floor(w_j * 2^(B-1-ilogb M)); Q = sum q_j; the target is
+ *     among unvisited cities and B = 50, each unvisited weight w_j becomes
+ *     q_j = floor(w_j * 2^(B-1-ilogb M)) < 2^50; for n <= 4096 = 2^12 cities
+ *     Q = sum q_j < 2^62 fits 64 bits.  The target is
  *     T = floor(r * Q / 2^64); the chosen city is the first j (ascending index)
  *     whose inclusive prefix sum of q exceeds T.  P(j) = q_j / Q.  If M = 0
  *     the lowest-index unvisited city is taken.
@@ -115,10 +116,14 @@ static int exponent_of(float x)
 /* ------------------------------------------------------------------------- */
 /* Eq. 1 by the integer roulette of reading R2.                               */
 /* w: weights of row i (n entries), visited: 1 for cities in the tabu list.  */
-/* Returns the chosen city, or -1 if every city is visited.                  */
+/* Returns the chosen city, -1 if every city is visited, -2 if n > 4096.     */
 /* ------------------------------------------------------------------------- */
+#define ROULETTE_BITS 50
+#define ROULETTE_MAX_N 4096
+
 int orc_roulette(int n, const float *w, const uint8_t *visited, uint64_t r)
 {
+    if (n > ROULETTE_MAX_N) return -2;
     float M = 0.0f;
     int first_unvisited = -1;
     for (int j = 0; j < n; ++j) {
@@ -129,8 +134,7 @@ int orc_roulette(int n, const float *w, const uint8_t *visited, uint64_t r)
     if (first_unvisited < 0) return -1;
     if (M == 0.0f) return first_unvisited;
 
-    int B = 62 - orc_ceil_log2(n);
-    int scale = B - 1 - exponent_of(M);
+    int scale = ROULETTE_BITS - 1 - exponent_of(M);
     uint64_t *q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
     uint64_t Q = 0;
     for (int j = 0; j < n; ++j) {
@@ -159,7 +163,7 @@ uint64_t orc_roulette_weights(int n, const float *w, const uint8_t *visited, uin
         for (int j = 0; j < n; ++j) q[j] = 0;
         return 0;
     }
-    int scale = 62 - orc_ceil_log2(n) - 1 - exponent_of(M);
+    int scale = ROULETTE_BITS - 1 - exponent_of(M);
     for (int j = 0; j < n; ++j) {
         q[j] = visited[j] ? 0u : (uint64_t)floor(ldexp((double)w[j], scale));
         Q += q[j];
