@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--warps-per-ant", type=int, default=0, help="0 = library default")
+    ap.add_argument("--ants-per-cta", type=int, default=0, help="0 = library default")
     return ap.parse_args()
 
 
@@ -142,6 +144,31 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measure_l2_copy_gbs(reps: int = 200, mib: int = 16) -> float:
+    """L2 copy bandwidth: torch copy between two L2-resident buffers.
+
+    Same method as the HBM figure of MEASURED_PEAKS.json (read + write bytes
+    of b.copy_(a), CUDA events) but on 2 x `mib` MiB, which stay in the
+    129 MB L2; best of `reps` back-to-back copies."""
+    import torch
+    a = torch.empty(mib << 18, dtype=torch.float32, device="cuda").normal_()
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    best = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        if ms > 0:
+            best = max(best, 2 * a.numel() * 4 / (ms / 1e3) / 1e9)
+    return best
 
 
 def measured_peaks():
@@ -258,6 +285,12 @@ def run_ours(args, w, rank, world, local):
     aco.aco_set_option(h, aco.ACO_OPT_STREAM, stream.cuda_stream)
     aco.aco_set_option(h, aco.ACO_OPT_DEPOSIT, dep)
     aco.aco_set_option(h, aco.ACO_OPT_PROFILE, 1)
+    if args.warps_per_ant:
+        aco.aco_set_option(h, aco.ACO_OPT_WARPS_PER_ANT, args.warps_per_ant)
+    if args.ants_per_cta:
+        aco.aco_set_option(h, aco.ACO_OPT_ANTS_PER_CTA, args.ants_per_cta)
+    tiling = (aco.aco_get_option(h, aco.ACO_OPT_WARPS_PER_ANT),
+              aco.aco_get_option(h, aco.ACO_OPT_ANTS_PER_CTA))
     launches = aco.aco_kernel_launches_per_iteration(h)
 
     with torch.cuda.stream(stream):
@@ -305,6 +338,15 @@ def run_ours(args, w, rank, world, local):
         return
     peaks, peak_kind = measured_peaks()
     roof = construct_roofline(n, m, con_ms, peaks, peak_kind)
+    l2_gbs = measure_l2_copy_gbs()
+    algo = roof["algorithmic_bytes_per_launch"]
+    dense = 4.0 * m * (n - 1) * n
+    roof_l2 = {"bound": "l2", "peak": l2_gbs, "unit": "GB/s",
+               "peak_kind": "L2 copy bandwidth measured in this run (2 x 16 MiB torch copy)",
+               "achieved_algorithmic": algo / (con_ms / 1e3) / 1e9,
+               "frac_algorithmic": algo / (con_ms / 1e3) / 1e9 / l2_gbs,
+               "achieved_dense_rows": dense / (con_ms / 1e3) / 1e9,
+               "frac_dense_rows": dense / (con_ms / 1e3) / 1e9 / l2_gbs}
     line = {
         "metric": METRIC, "value": value, "unit": "ant-steps/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
@@ -312,6 +354,7 @@ def run_ours(args, w, rank, world, local):
         "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "m": m, "alpha": w["alpha"],
                    "beta": w["beta"], "rho": w["rho"], "deposit": args.deposit,
+                   "warps_per_ant": tiling[0], "ants_per_cta": tiling[1],
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed between steps (256 MB write)"},
         "construct_ant_steps_per_s": m * (n - 1) / (con_ms / 1e3),
@@ -319,6 +362,7 @@ def run_ours(args, w, rank, world, local):
         "phase_ms": {"construct": con_ms, "best": best_ms, "pheromone": upd_ms},
         "best_len": best_len,
         "roofline": roof,
+        "roofline_l2": roof_l2,
         "gpu_launches": launches * steps,
         "clocks": clk,
         "e2e": e2e,

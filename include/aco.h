@@ -192,6 +192,107 @@ int aco_synchronize(aco_handle h);
  */
 int aco_kernel_launches_per_iteration(aco_handle h, int32_t *count);
 
+/*
+ * aco_create_coords - as aco_create, but the instance is given by integer
+ * city coordinates (xy: n pairs x, y, host, copied) and the distance matrix
+ * is built on the device with the TSPLIB EUC_2D rounding
+ * d = floor(sqrt(dx^2 + dy^2) + 0.5) in IEEE double.  Coordinates must lie in
+ * [-2^25, 2^25] and be pairwise distinct (ACO_EINVAL otherwise).
+ */
+int aco_create_coords(int32_t n, const int32_t *xy, float alpha, float beta, float rho,
+                      int32_t m, uint64_t seed, aco_handle *out);
+
+/* ======================================================================== *
+ * Batched and served instances: a pool of device-resident slots.
+ *
+ * A pool owns one HBM arena of `budget_bytes`; every admitted instance gets
+ * its own dist / eta^beta / tau / choice_info / tours / best-tour block from
+ * it and keeps it until released.  aco_pool_step() runs one Ant System
+ * iteration for every live slot: one construction launch per tiling class
+ * (instances of similar n), one best launch and one gather-update launch for
+ * all slots together, captured as a CUDA graph while the live set is
+ * unchanged.  Random numbers use each instance's own seed and iteration
+ * counter, so an instance's results are identical alone and in any mix.
+ * Pools use the deterministic gather deposit.  A pool is not thread-safe.
+ * ======================================================================== */
+typedef struct aco_pool *aco_pool_handle;
+
+/* Device bytes one instance of n cities and m ants takes from a pool. */
+int aco_pool_bytes_needed(int32_t n, int32_t m, uint64_t *bytes);
+
+/* aco_pool_create - max_slots >= 1 concurrent instances within budget_bytes of HBM. */
+int aco_pool_create(int32_t max_slots, uint64_t budget_bytes, aco_pool_handle *out);
+
+/* aco_pool_destroy - free the arena and every slot; NULL is accepted. */
+int aco_pool_destroy(aco_pool_handle p);
+
+/*
+ * aco_pool_admit / aco_pool_admit_coords - add an instance that will run
+ * `iterations` iterations (>= 1) in subsequent aco_pool_step calls.  Same
+ * argument rules as aco_create / aco_create_coords.  The upload and setup
+ * (eta^beta, nearest-neighbour tour, tau0, choice_info) run on a side stream
+ * and overlap with steps already in flight.  A pageable dist / xy buffer may
+ * be reused as soon as the call returns; a pinned one must stay unchanged
+ * until the next aco_pool_step or aco_pool_synchronize.  *slot receives the
+ * slot index.
+ * ACO_EBUSY if no slot is free or the arena has no block large enough.
+ */
+int aco_pool_admit(aco_pool_handle p, int32_t n, const int32_t *dist, float alpha, float beta,
+                   float rho, int32_t m, uint64_t seed, int32_t iterations, int32_t *slot);
+int aco_pool_admit_coords(aco_pool_handle p, int32_t n, const int32_t *xy, float alpha,
+                          float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
+                          int32_t *slot);
+
+/*
+ * aco_pool_step - one iteration for every live slot (asynchronous).  A slot
+ * whose iteration budget is used up becomes finished and leaves the live set.
+ * *live_after (may be NULL) receives the number of slots still live.
+ */
+int aco_pool_step(aco_pool_handle p, int32_t *live_after);
+
+/*
+ * aco_pool_finished - slots that are finished but not yet released, in
+ * completion order; writes at most `capacity` of them and the total count.
+ */
+int aco_pool_finished(aco_pool_handle p, int32_t *slots, int32_t capacity, int32_t *count);
+
+/*
+ * aco_pool_result - best-so-far tour (n+1 int32) and length of a slot (live
+ * or finished; synchronises the pool).  Either output may be NULL.
+ */
+int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t *tour, int64_t *len);
+
+/* aco_pool_pheromone - copy a slot's tau (n*n float) to the host. */
+int aco_pool_pheromone(aco_pool_handle p, int32_t slot, float *tau);
+
+/* aco_pool_release - return a finished (or live) slot and its memory. */
+int aco_pool_release(aco_pool_handle p, int32_t slot);
+
+/*
+ * aco_pool_stats - live and finished slot counts, arena bytes in use, and
+ * kernel launches of the last step.  Any output may be NULL.
+ */
+int aco_pool_stats(aco_pool_handle p, int32_t *live, int32_t *finished, uint64_t *bytes_in_use,
+                   int32_t *launches_last_step);
+
+/* aco_pool_synchronize - wait for all pool work and report device-side errors. */
+int aco_pool_synchronize(aco_pool_handle p);
+
+/*
+ * Static batches (a pool with one slot per instance and no iteration limit).
+ *   aco_batch_create: count instances; ns[i] cities, dists[i] (host, n*n,
+ *   copied), alpha/beta/rho/ms/seeds per instance.
+ *   aco_batch_iterate: `iterations` steps of every instance.
+ *   aco_batch_best: best-so-far tour and length of instance idx.
+ */
+typedef struct aco_pool *aco_batch;
+int aco_batch_create(int32_t count, const int32_t *ns, const int32_t *const *dists,
+                     const float *alpha, const float *beta, const float *rho, const int32_t *ms,
+                     const uint64_t *seeds, aco_batch *out);
+int aco_batch_iterate(aco_batch b, int32_t iterations);
+int aco_batch_best(aco_batch b, int32_t idx, int32_t *tour, int64_t *len);
+int aco_batch_destroy(aco_batch b);
+
 #ifdef __cplusplus
 }
 #endif

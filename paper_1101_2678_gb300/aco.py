@@ -67,6 +67,26 @@ SIGNATURES = [
     ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
     ("aco_synchronize", C.c_int, [_vp]),
     ("aco_kernel_launches_per_iteration", C.c_int, [_vp, _i32p]),
+    ("aco_create_coords", C.c_int, [C.c_int32, _vp, C.c_float, C.c_float, C.c_float, C.c_int32,
+                                    C.c_uint64, C.POINTER(_vp)]),
+    ("aco_pool_bytes_needed", C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_uint64)]),
+    ("aco_pool_create", C.c_int, [C.c_int32, C.c_uint64, C.POINTER(_vp)]),
+    ("aco_pool_destroy", C.c_int, [_vp]),
+    ("aco_pool_admit", C.c_int, [_vp, C.c_int32, _vp, C.c_float, C.c_float, C.c_float, C.c_int32,
+                                 C.c_uint64, C.c_int32, _i32p]),
+    ("aco_pool_admit_coords", C.c_int, [_vp, C.c_int32, _vp, C.c_float, C.c_float, C.c_float,
+                                        C.c_int32, C.c_uint64, C.c_int32, _i32p]),
+    ("aco_pool_step", C.c_int, [_vp, _i32p]),
+    ("aco_pool_finished", C.c_int, [_vp, _vp, C.c_int32, _i32p]),
+    ("aco_pool_result", C.c_int, [_vp, C.c_int32, _vp, _vp]),
+    ("aco_pool_pheromone", C.c_int, [_vp, C.c_int32, _vp]),
+    ("aco_pool_release", C.c_int, [_vp, C.c_int32]),
+    ("aco_pool_stats", C.c_int, [_vp, _i32p, _i32p, C.POINTER(C.c_uint64), _i32p]),
+    ("aco_pool_synchronize", C.c_int, [_vp]),
+    ("aco_batch_create", C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    ("aco_batch_iterate", C.c_int, [_vp, C.c_int32]),
+    ("aco_batch_best", C.c_int, [_vp, C.c_int32, _vp, _vp]),
+    ("aco_batch_destroy", C.c_int, [_vp]),
 ]
 
 _lock = threading.Lock()
@@ -209,6 +229,130 @@ def aco_kernel_launches_per_iteration(h) -> int:
     _check(load().aco_kernel_launches_per_iteration(h, C.byref(v)),
            "aco_kernel_launches_per_iteration")
     return v.value
+
+
+def aco_create_coords(xy, alpha: float, beta: float, rho: float, m: int, seed: int):
+    """Create an instance from (n, 2) integer coordinates (EUC_2D distances on device)."""
+    c = np.ascontiguousarray(xy, dtype=np.int32)
+    h = C.c_void_p()
+    _check(load().aco_create_coords(c.shape[0], _ptr(c), alpha, beta, rho, m, seed, C.byref(h)),
+           "aco_create_coords")
+    return h
+
+
+# ---- pools (batched / served instances) ---------------------------------------------------
+
+def aco_pool_bytes_needed(n: int, m: int) -> int:
+    v = C.c_uint64()
+    _check(load().aco_pool_bytes_needed(n, m, C.byref(v)), "aco_pool_bytes_needed")
+    return v.value
+
+
+def aco_pool_create(max_slots: int, budget_bytes: int):
+    p = C.c_void_p()
+    _check(load().aco_pool_create(max_slots, budget_bytes, C.byref(p)), "aco_pool_create")
+    return p
+
+
+def aco_pool_destroy(p) -> None:
+    _check(load().aco_pool_destroy(p), "aco_pool_destroy")
+
+
+def aco_pool_admit(p, dist, alpha, beta, rho, m, seed, iterations):
+    """Admit an instance given by its distance matrix; returns the slot (raises AcoError)."""
+    d = np.ascontiguousarray(dist, dtype=np.int32)
+    slot = C.c_int32()
+    _check(load().aco_pool_admit(p, d.shape[0], _ptr(d), alpha, beta, rho, m, seed, iterations,
+                                 C.byref(slot)), "aco_pool_admit")
+    return slot.value
+
+
+def aco_pool_admit_coords(p, xy, alpha, beta, rho, m, seed, iterations):
+    """Admit an instance given by integer coordinates; returns the slot or None if busy."""
+    c = np.ascontiguousarray(xy, dtype=np.int32)
+    slot = C.c_int32()
+    rc = load().aco_pool_admit_coords(p, c.shape[0], _ptr(c), alpha, beta, rho, m, seed,
+                                      iterations, C.byref(slot))
+    if rc == ACO_EBUSY:
+        return None
+    _check(rc, "aco_pool_admit_coords")
+    return slot.value
+
+
+def aco_pool_step(p) -> int:
+    live = C.c_int32()
+    _check(load().aco_pool_step(p, C.byref(live)), "aco_pool_step")
+    return live.value
+
+
+def aco_pool_finished(p):
+    cnt = C.c_int32()
+    _check(load().aco_pool_finished(p, None, 0, C.byref(cnt)), "aco_pool_finished")
+    out = np.zeros(max(cnt.value, 1), np.int32)
+    _check(load().aco_pool_finished(p, _ptr(out), len(out), C.byref(cnt)), "aco_pool_finished")
+    return out[:cnt.value].tolist()
+
+
+def aco_pool_result(p, slot: int, n: int):
+    tour = np.empty(n + 1, np.int32)
+    length = np.zeros(1, np.int64)
+    _check(load().aco_pool_result(p, slot, _ptr(tour), _ptr(length)), "aco_pool_result")
+    return tour, int(length[0])
+
+
+def aco_pool_pheromone(p, slot: int, n: int) -> np.ndarray:
+    out = np.empty((n, n), np.float32)
+    _check(load().aco_pool_pheromone(p, slot, _ptr(out)), "aco_pool_pheromone")
+    return out
+
+
+def aco_pool_release(p, slot: int) -> None:
+    _check(load().aco_pool_release(p, slot), "aco_pool_release")
+
+
+def aco_pool_stats(p) -> dict:
+    live, fin, launches = C.c_int32(), C.c_int32(), C.c_int32()
+    used = C.c_uint64()
+    _check(load().aco_pool_stats(p, C.byref(live), C.byref(fin), C.byref(used), C.byref(launches)),
+           "aco_pool_stats")
+    return dict(live=live.value, finished=fin.value, bytes_in_use=used.value,
+                launches_last_step=launches.value)
+
+
+def aco_pool_synchronize(p) -> None:
+    _check(load().aco_pool_synchronize(p), "aco_pool_synchronize")
+
+
+def aco_batch_create(dists, ms, seeds, alpha=1.0, beta=2.0, rho=0.5):
+    """A static batch: one slot per instance (lists of distance matrices, ant counts, seeds)."""
+    count = len(dists)
+    ds = [np.ascontiguousarray(d, dtype=np.int32) for d in dists]
+    ns = np.array([d.shape[0] for d in ds], np.int32)
+    ptrs = (C.c_void_p * count)(*[d.ctypes.data for d in ds])
+    al = np.full(count, alpha, np.float32)
+    be = np.full(count, beta, np.float32)
+    rh = np.full(count, rho, np.float32)
+    mm = np.ascontiguousarray(ms, np.int32)
+    sd = np.ascontiguousarray(seeds, np.uint64)
+    b = C.c_void_p()
+    _check(load().aco_batch_create(count, _ptr(ns), ptrs, _ptr(al), _ptr(be), _ptr(rh), _ptr(mm),
+                                   _ptr(sd), C.byref(b)), "aco_batch_create")
+    return b
+
+
+def aco_batch_iterate(b, iterations: int) -> None:
+    _check(load().aco_batch_iterate(b, iterations), "aco_batch_iterate")
+
+
+def aco_batch_best(b, idx: int, n: int):
+    tour = np.empty(n + 1, np.int32)
+    length = np.zeros(1, np.int64)
+    _check(load().aco_batch_best(b, idx, _ptr(tour), _ptr(length)), "aco_batch_best")
+    return tour, int(length[0])
+
+
+def aco_batch_destroy(b) -> None:
+    _check(load().aco_batch_destroy(b), "aco_batch_destroy")
 
 
 class Colony:

@@ -73,6 +73,21 @@ cudaError_t launch_construct(const Instance& I, ConstructTiling t, cudaStream_t 
   }
 }
 
+cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
+                                   ConstructTiling t, cudaStream_t st) {
+  if (t.G * t.A > 8) return cudaErrorInvalidValue;
+  switch (t.G) {
+    case 1:
+      return launch_construct_items_g1(insts, items, count, t.C, t.A, st);
+    case 2:
+      return launch_construct_items_g2(insts, items, count, t.C, t.A, st);
+    case 4:
+      return launch_construct_items_g4(insts, items, count, t.C, t.A, st);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -216,12 +231,34 @@ const char* aco_strerror(int code) {
 
 const char* aco_last_error_message(void) { return g_err; }
 
+static int create_common(int32_t n, const int32_t* dist, const int32_t* xy, float alpha,
+                         float beta, float rho, int32_t m, uint64_t seed, aco_handle* out);
+
 int aco_create(int32_t n, const int32_t* dist, float alpha, float beta, float rho, int32_t m,
                uint64_t seed, aco_handle* out) {
   if (!out) return fail(ACO_EINVAL, "out is NULL");
   *out = nullptr;
   int rc = validate_instance(n, dist, alpha, beta, rho, m);
   if (rc) return rc;
+  return create_common(n, dist, nullptr, alpha, beta, rho, m, seed, out);
+}
+
+int aco_create_coords(int32_t n, const int32_t* xy, float alpha, float beta, float rho, int32_t m,
+                      uint64_t seed, aco_handle* out) {
+  if (!out) return fail(ACO_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate_coords_public(n, xy);
+  if (rc) return rc;
+  if (m < 1 || m > ACO_MAX_M) return fail(ACO_EINVAL, "m=%d outside [1, %d]", m, ACO_MAX_M);
+  if (!std::isfinite(alpha) || alpha < 0.0f || !std::isfinite(beta) || beta < 0.0f)
+    return fail(ACO_EINVAL, "alpha and beta must be finite and >= 0");
+  if (!(rho > 0.0f && rho <= 1.0f)) return fail(ACO_EINVAL, "rho must lie in (0, 1]");
+  return create_common(n, nullptr, xy, alpha, beta, rho, m, seed, out);
+}
+
+static int create_common(int32_t n, const int32_t* dist, const int32_t* xy, float alpha,
+                         float beta, float rho, int32_t m, uint64_t seed, aco_handle* out) {
+  int rc;
   aco_colony* h = new (std::nothrow) aco_colony();
   if (!h) return fail(ACO_ENOMEM, "host allocation");
   Instance& I = h->I;
@@ -292,10 +329,17 @@ int aco_create(int32_t n, const int32_t* dist, float alpha, float beta, float rh
       rc = cuda_fail(e, "upload state");
       break;
     }
-    // dist: n rows of n int32 into rows of ld (padding stays zero).
-    if ((e = cudaMemcpy2DAsync((void*)I.dist, (size_t)I.ld * 4, dist, (size_t)n * 4, (size_t)n * 4,
-                               (size_t)n, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) {
-      rc = cuda_fail(e, "upload dist");
+    if (dist) {
+      // dist: n rows of n int32 into rows of ld (padding stays zero).
+      e = cudaMemcpy2DAsync((void*)I.dist, (size_t)I.ld * 4, dist, (size_t)n * 4, (size_t)n * 4,
+                            (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    } else {
+      // coordinates staged in the choice_info block, distances built on the device
+      e = cudaMemcpyAsync(I.choice, xy, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = launch_dist_from_coords(I, (const int32_t*)I.choice, h->stream);
+    }
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "upload instance");
       break;
     }
     if ((e = launch_setup(I, h->sms, h->stream)) != cudaSuccess) {

@@ -8,8 +8,10 @@
 //   1. load row choice[cur] (C floats per thread), zero visited cities;
 //   2. M = max over unvisited (REDUX on the float bit patterns, which order
 //      like the values for w >= 0), across warps through shared memory;
-//   3. q_j = floor(w_j * 2^(B-1-ilogb M)), per-thread u64 sums, warp
-//      inclusive scan, group totals -> Q;
+//   3. q_j = floor(w_j * 2^(49-ilogb M)) from the float's exponent and
+//      significand fields with 32-bit integer shifts and IMAD.WIDE (no
+//      float-to-int conversion), per-thread u64 sums, warp inclusive scan,
+//      group totals -> Q;
 //   4. T = floor(r Q / 2^64) with r from Philox (one Philox call per lane per
 //      32 steps, broadcast by shuffle);
 //   5. the thread whose prefix range holds T is found by ballot; its chunk is
@@ -44,26 +46,47 @@ __device__ __forceinline__ void group_sync(int bar_id, int nthreads) {
   }
 }
 
-// floor(v * 2^sc) for v >= 0 with the scale passed as one or two float powers
-// of two (the product is exact: scaling by a power of two never rounds unless
-// the result is below 2^-126, and then the floor is 0 either way).
-template <bool kTwo>
-__device__ __forceinline__ unsigned long long quantise(float v, float f1, float f2) {
-  float y = __fmul_rn(v, f1);
-  if (kTwo) y = __fmul_rn(y, f2);
-  return __float2ull_rz(y);
+// Roulette weight bits: q_j = floor(w_j * 2^(kBits-1-ilogb M)) < 2^kBits.
+constexpr int kRouletteBits = 50;
+
+// acc + floor(w * 2^sc) for a float w >= 0 given by its bits b, with
+// k = 150 - sc and sc <= 126.  w = mant * 2^(E-150) for a normal w (E the
+// biased exponent field, mant the 24-bit significand), so the product is
+// mant << (E - k) or mant >> (k - E).  A subnormal or zero w has E = 0 and,
+// because k >= 24, contributes 0, which is its exact floor (w * 2^sc < 1).
+// Only 32-bit integer operations and one IMAD.WIDE.U32: no float-to-64-bit
+// conversion, which is slow on this part.  The result needs E - k <= 31,
+// which kRouletteBits = 50 guarantees (E - k <= 26).
+__device__ __forceinline__ unsigned long long add_floor_scaled(unsigned long long acc, uint32_t b,
+                                                               int k) {
+  const int e = (int)(b >> 23);
+  const uint32_t mant = (b & 0x7fffffu) | 0x800000u;
+  const uint32_t dn = (uint32_t)max(k - e, 0);
+  const uint32_t up = (uint32_t)max(e - k, 0);
+  return acc + (unsigned long long)__funnelshift_rc(mant, 0u, dn) * (1u << up);
+}
+
+// Same for sc > 126 (only when the largest unvisited weight is below
+// 2^-77): scale exactly in float first (two power-of-two products, exact
+// since the result is normal or below 1), then the integer step with sc = 0.
+__device__ __forceinline__ unsigned long long add_floor_scaled_tiny(unsigned long long acc,
+                                                                    uint32_t b, float f1,
+                                                                    float f2) {
+  const float y = __fmul_rn(__fmul_rn(__uint_as_float(b), f1), f2);
+  return add_floor_scaled(acc, __float_as_uint(y), 150);
 }
 
 template <int C>
-__device__ __forceinline__ unsigned long long chunk_sum(const float (&v)[C], float f1, float f2,
-                                                        bool two) {
+__device__ __forceinline__ unsigned long long chunk_sum(const uint32_t (&v)[C], int sc) {
   unsigned long long s = 0;
-  if (!two) {
+  if (sc <= 126) {
+    const int k = 150 - sc;
 #pragma unroll
-    for (int i = 0; i < C; ++i) s += quantise<false>(v[i], f1, f2);
+    for (int i = 0; i < C; ++i) s = add_floor_scaled(s, v[i], k);
   } else {
+    const float f1 = pow2f(127), f2 = pow2f(sc - 127);
 #pragma unroll
-    for (int i = 0; i < C; ++i) s += quantise<true>(v[i], f1, f2);
+    for (int i = 0; i < C; ++i) s = add_floor_scaled_tiny(s, v[i], f1, f2);
   }
   return s;
 }
@@ -89,7 +112,6 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   const int lane = tg & 31, wg = tg >> 5;
   const int base = tg * C;
   const uint32_t iter = (uint32_t)I.st->iteration;
-  const int B = 62 - ceil_log2_u32((uint32_t)n);
   const unsigned long long seed = I.seed;
 
   // Tabu bits: 1 = visited.  Padding cities (index >= n) and bits beyond C
@@ -128,11 +150,11 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     const unsigned long long r = shfl_u64(rwin, off);
     const float* row = I.choice + (size_t)cur * ld;
 
-    float v[C];
+    uint32_t v[C];  // weight bits; w >= 0 orders like its bit pattern
 #pragma unroll
     for (int i = 0; i < C; i += 4) {
-      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (base + i < ld) t = __ldg(reinterpret_cast<const float4*>(row + base + i));
+      uint4 t = make_uint4(0u, 0u, 0u, 0u);
+      if (base + i < ld) t = __ldg(reinterpret_cast<const uint4*>(row + base + i));
       v[i] = t.x;
       v[i + 1] = t.y;
       v[i + 2] = t.z;
@@ -141,8 +163,8 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     uint32_t mx = 0;
 #pragma unroll
     for (int i = 0; i < C; ++i) {
-      if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0.0f;
-      mx = max(mx, __float_as_uint(v[i]));
+      if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+      mx = max(mx, v[i]);
     }
     mx = __reduce_max_sync(FULL, mx);
     if (G > 1) {
@@ -170,11 +192,8 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       }
       next = (int)cand;
     } else {
-      const int sc = B - 1 - exponent_of_bits(mx);
-      const bool two = sc > 127;
-      const float f1 = two ? pow2f(127) : pow2f(sc);
-      const float f2 = two ? pow2f(sc - 127) : 1.0f;
-      const unsigned long long mine = chunk_sum<C>(v, f1, f2, two);
+      const int sc = kRouletteBits - 1 - exponent_of_bits(mx);
+      const unsigned long long mine = chunk_sum<C>(v, sc);
       const unsigned long long incl = warp_inclusive_scan(mine, lane);
       const unsigned long long wtot = shfl_u64(incl, 31);
       unsigned long long woff = 0, Q = wtot;
@@ -208,9 +227,11 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
 #pragma unroll
           for (int w = 0; w < NW; ++w)
             if (w == (li >> 5)) word = visL[w];
-          float w8 = 0.0f;
-          if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u)) w8 = row[baseL + li];
-          qv[p] = two ? quantise<true>(w8, f1, f2) : quantise<false>(w8, f1, f2);
+          uint32_t w8 = 0u;
+          if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u))
+            w8 = __float_as_uint(row[baseL + li]);
+          qv[p] = sc <= 126 ? add_floor_scaled(0ull, w8, 150 - sc)
+                            : add_floor_scaled_tiny(0ull, w8, pow2f(127), pow2f(sc - 127));
           ps += qv[p];
         }
         const unsigned long long incl2 = warp_inclusive_scan(ps, lane);
@@ -282,6 +303,22 @@ __global__ void __launch_bounds__(256) construct_kernel(Instance I) {
   const int ant = blockIdx.x * (blockDim.x / (32 * G)) + grp;
   if (ant >= I.m) return;
   construct_ant<C, G>(I, ant, tg, &gs[grp], 1 + grp);
+}
+
+// Batched form: group g of block b builds ant items[b*A + g].y of instance
+// insts[items[b*A + g].x].  Items are listed longest instance first.
+template <int C, int G>
+__global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __restrict__ insts,
+                                                              const int2* __restrict__ items,
+                                                              int count) {
+  __shared__ GroupSmem gs[kMaxGroupsPerCta];
+  const int grp = threadIdx.x / (32 * G);
+  const int tg = threadIdx.x % (32 * G);
+  const int idx = blockIdx.x * (blockDim.x / (32 * G)) + grp;
+  if (idx >= count) return;
+  const int2 it = items[idx];
+  const Instance I = insts[it.x];
+  construct_ant<C, G>(I, it.y, tg, &gs[grp], 1 + grp);
 }
 
 }  // namespace aco

@@ -36,5 +36,20 @@ cudaError_t launch_construct_g1(const Instance& I, int C, int A, cudaStream_t st
 cudaError_t launch_construct_g2(const Instance& I, int C, int A, cudaStream_t st);
 cudaError_t launch_construct_g4(const Instance& I, int C, int A, cudaStream_t st);
 bool construct_supported(int C, int G);
+cudaError_t launch_construct_items_g1(const Instance* insts, const int2* items, int count, int C,
+                                      int A, cudaStream_t st);
+cudaError_t launch_construct_items_g2(const Instance* insts, const int2* items, int count, int C,
+                                      int A, cudaStream_t st);
+cudaError_t launch_construct_items_g4(const Instance* insts, const int2* items, int count, int C,
+                                      int A, cudaStream_t st);
+cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
+                                   ConstructTiling t, cudaStream_t st);
+
+// Batched best / gather update over device-side lists.
+cudaError_t launch_best_slots(const Instance* insts, const int* slots, int count, cudaStream_t st);
+cudaError_t launch_update_rows(const Instance* insts, const int2* rows, int count, int max_ld,
+                               cudaStream_t st);
+// Device-side setup of one instance from city coordinates (TSPLIB EUC_2D).
+cudaError_t launch_dist_from_coords(const Instance& I, const int32_t* xy, cudaStream_t st);
 
 }  // namespace aco

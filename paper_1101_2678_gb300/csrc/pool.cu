@@ -1,0 +1,615 @@
+// Batched and served Ant System instances: a pool of device-resident slots
+// (include/aco.h, aco_pool_* and aco_batch_*).
+//
+// Memory: one cudaMalloc'ed arena of the caller's HBM budget, carved by a
+// first-fit free list (host side) into one block per instance.  Each step
+// runs, for every live slot, the same three phases as a single instance:
+//   construct  one launch per tiling class (C cities per lane, G warps per
+//              ant), items (slot, ant) listed longest instance first;
+//   best       one CTA per live slot;
+//   update     one warp per (slot, row): gather deposit + evaporation +
+//              choice_info, fused.
+// The device-side lists are rebuilt and the step re-captured as a CUDA graph
+// only when the live set changes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/aco.h"
+#include "aco_device.cuh"
+#include "kernels.h"
+#include "runtime.h"
+
+namespace aco {
+
+static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct Layout {
+  size_t dist, heta, tau, choice, tours, lens, nbr, q, delta, best, st, total;
+};
+
+static Layout layout_of(int n, int m) {
+  const size_t ld = (size_t)((n + 3) / 4 * 4), ldt = (size_t)((n + 1 + 3) / 4 * 4),
+               ldm = (size_t)((m + 31) / 32 * 32);
+  const size_t mat = (size_t)n * ld;
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L.dist = take(mat * 4);
+  L.heta = take(mat * 4);
+  L.tau = take(mat * 4);
+  L.choice = take(mat * 4);
+  L.tours = take((size_t)m * ldt * 4);
+  L.lens = take((size_t)m * 8);
+  L.nbr = take((size_t)n * ldm * 4);
+  L.q = take((size_t)m * 8);
+  L.delta = take((size_t)m * 4);
+  L.best = take(((size_t)n + 1) * 4);
+  L.st = take(sizeof(IterState));
+  L.total = off;
+  return L;
+}
+
+static int validate_coords(int32_t n, const int32_t* xy) {
+  if (n < 3 || n > ACO_MAX_N) return fail(ACO_EINVAL, "n=%d outside [3, %d]", n, ACO_MAX_N);
+  if (!xy) return fail(ACO_EINVAL, "xy is NULL");
+  const int32_t lim = 1 << 25;
+  std::vector<std::pair<int32_t, int32_t>> pts((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const int32_t x = xy[2 * i], y = xy[2 * i + 1];
+    if (x < -lim || x > lim || y < -lim || y > lim)
+      return fail(ACO_EINVAL, "coordinate of city %d outside [-2^25, 2^25]", i);
+    pts[(size_t)i] = {x, y};
+  }
+  std::sort(pts.begin(), pts.end());
+  for (int i = 1; i < n; ++i)
+    if (pts[(size_t)i] == pts[(size_t)i - 1])
+      return fail(ACO_EINVAL, "duplicate city coordinates: eta = 1/d is undefined at d = 0");
+  return ACO_OK;
+}
+
+int validate_coords_public(int32_t n, const int32_t* xy) { return validate_coords(n, xy); }
+
+}  // namespace aco
+
+using namespace aco;
+
+struct PoolSlot {
+  bool used = false;
+  bool live = false;
+  bool finished = false;
+  int n = 0, m = 0;
+  long long iters_left = 0;
+  size_t off = 0, bytes = 0;
+  Instance I{};
+  cudaEvent_t ready = nullptr;  // setup done on the side stream
+  bool wait_ready = false;
+};
+
+struct aco_pool {
+  int max_slots = 0;
+  size_t budget = 0;
+  void* arena = nullptr;
+  std::map<size_t, size_t> free_blocks;  // offset -> size
+  size_t in_use = 0;
+  std::vector<PoolSlot> slots;
+  std::vector<int> finished_order;
+  cudaStream_t stream = nullptr, side = nullptr;
+  int sms = 148;
+  // device tables
+  Instance* d_inst = nullptr;
+  int* d_live = nullptr;
+  int2* d_items = nullptr;
+  int2* d_rows = nullptr;
+  int* d_coords = nullptr;  // staging for aco_pool_admit_coords (n pairs)
+  size_t items_cap = 0, rows_cap = 0;
+  // host mirrors of the lists
+  std::vector<int> h_live;
+  std::vector<int2> h_items, h_rows;
+  struct Class {
+    ConstructTiling t;
+    int begin, count;
+  };
+  std::vector<Class> classes;
+  int max_ld = 4;
+  bool dirty = true;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+  bool unlimited = false;  // static batch: no iteration budget
+};
+
+static void pool_drop_graph(aco_pool* p) {
+  if (p->exec) {
+    cudaGraphExecDestroy(p->exec);
+    p->exec = nullptr;
+  }
+}
+
+static bool pool_alloc(aco_pool* p, size_t bytes, size_t* off) {
+  for (auto it = p->free_blocks.begin(); it != p->free_blocks.end(); ++it) {
+    if (it->second >= bytes) {
+      *off = it->first;
+      const size_t rest = it->second - bytes;
+      const size_t noff = it->first + bytes;
+      p->free_blocks.erase(it);
+      if (rest) p->free_blocks[noff] = rest;
+      p->in_use += bytes;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void pool_free(aco_pool* p, size_t off, size_t bytes) {
+  p->in_use -= bytes;
+  auto it = p->free_blocks.emplace(off, bytes).first;
+  auto nx = std::next(it);
+  if (nx != p->free_blocks.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    p->free_blocks.erase(nx);
+  }
+  if (it != p->free_blocks.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      p->free_blocks.erase(it);
+    }
+  }
+}
+
+static int ensure_capacity(void** ptr, size_t* cap, size_t need, size_t elem) {
+  if (need <= *cap) return ACO_OK;
+  size_t ncap = std::max(need, *cap * 2 + 64);
+  void* np = nullptr;
+  cudaError_t e = cudaMalloc(&np, ncap * elem);
+  if (e != cudaSuccess) return cuda_fail(e, "pool list");
+  if (*ptr) cudaFree(*ptr);
+  *ptr = np;
+  *cap = ncap;
+  return ACO_OK;
+}
+
+// Rebuild the device work lists for the current live set.
+static int pool_rebuild(aco_pool* p) {
+  p->h_live.clear();
+  p->h_items.clear();
+  p->h_rows.clear();
+  p->classes.clear();
+  p->max_ld = 4;
+  std::vector<int> live;
+  for (int s = 0; s < p->max_slots; ++s)
+    if (p->slots[(size_t)s].live) live.push_back(s);
+  // longest instance first
+  std::sort(live.begin(), live.end(), [&](int a, int b) {
+    const int na = p->slots[(size_t)a].n, nb = p->slots[(size_t)b].n;
+    return na != nb ? na > nb : a < b;
+  });
+  p->h_live = live;
+  // group by tiling class, keeping the longest-first order inside a class
+  std::map<std::pair<int, int>, std::vector<int>> by_class;
+  std::vector<std::pair<int, int>> class_order;
+  for (int s : live) {
+    const ConstructTiling t = default_construct_tiling(p->slots[(size_t)s].n);
+    const auto key = std::make_pair(t.G, t.C);
+    if (!by_class.count(key)) class_order.push_back(key);
+    by_class[key].push_back(s);
+  }
+  for (const auto& key : class_order) {
+    aco_pool::Class c;
+    c.t = default_construct_tiling(p->slots[(size_t)by_class[key][0]].n);
+    c.begin = (int)p->h_items.size();
+    for (int s : by_class[key])
+      for (int k = 0; k < p->slots[(size_t)s].m; ++k) p->h_items.push_back(make_int2(s, k));
+    c.count = (int)p->h_items.size() - c.begin;
+    p->classes.push_back(c);
+  }
+  for (int s : live) {
+    const PoolSlot& sl = p->slots[(size_t)s];
+    p->max_ld = std::max(p->max_ld, sl.I.ld);
+    for (int i = 0; i < sl.n; ++i) p->h_rows.push_back(make_int2(s, i));
+  }
+  int rc = ensure_capacity((void**)&p->d_items, &p->items_cap, p->h_items.size(), sizeof(int2));
+  if (!rc) rc = ensure_capacity((void**)&p->d_rows, &p->rows_cap, p->h_rows.size(), sizeof(int2));
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!p->h_items.empty())
+    e = cudaMemcpyAsync(p->d_items, p->h_items.data(), p->h_items.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && !p->h_rows.empty())
+    e = cudaMemcpyAsync(p->d_rows, p->h_rows.data(), p->h_rows.size() * sizeof(int2),
+                        cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && !p->h_live.empty())
+    e = cudaMemcpyAsync(p->d_live, p->h_live.data(), p->h_live.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, p->stream);
+  // The host vectors must outlive the copies: synchronise before they change.
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pool lists");
+  pool_drop_graph(p);
+  p->dirty = false;
+  return ACO_OK;
+}
+
+static int pool_enqueue_step(aco_pool* p) {
+  cudaError_t e;
+  int launches = 0;
+  for (const auto& c : p->classes) {
+    e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pool construct");
+    ++launches;
+  }
+  if ((e = launch_best_slots(p->d_inst, p->d_live, (int)p->h_live.size(), p->stream)) !=
+      cudaSuccess)
+    return cuda_fail(e, "pool best");
+  if ((e = launch_update_rows(p->d_inst, p->d_rows, (int)p->h_rows.size(), p->max_ld,
+                              p->stream)) != cudaSuccess)
+    return cuda_fail(e, "pool update");
+  p->launches = launches + 2;
+  return ACO_OK;
+}
+
+static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const int32_t* xy,
+                             float alpha, float beta, float rho, int32_t m, uint64_t seed,
+                             int32_t iterations, int32_t* slot) {
+  if (!p || !slot) return fail(ACO_EINVAL, "NULL argument");
+  if (!p->unlimited && iterations < 1) return fail(ACO_EINVAL, "iterations must be >= 1");
+  int rc = dist ? validate_instance(n, dist, alpha, beta, rho, m)
+                : validate_coords_public(n, xy);
+  if (rc) return rc;
+  if (!dist) {
+    if (m < 1 || m > ACO_MAX_M) return fail(ACO_EINVAL, "m=%d outside [1, %d]", m, ACO_MAX_M);
+    if (!std::isfinite(alpha) || alpha < 0.0f || !std::isfinite(beta) || beta < 0.0f)
+      return fail(ACO_EINVAL, "alpha and beta must be finite and >= 0");
+    if (!(rho > 0.0f && rho <= 1.0f)) return fail(ACO_EINVAL, "rho must lie in (0, 1]");
+  }
+  int s = -1;
+  for (int i = 0; i < p->max_slots; ++i)
+    if (!p->slots[(size_t)i].used) {
+      s = i;
+      break;
+    }
+  if (s < 0) return fail(ACO_EBUSY, "no free slot");
+  const Layout L = layout_of(n, m);
+  size_t off = 0;
+  if (!pool_alloc(p, L.total, &off)) return fail(ACO_EBUSY, "HBM budget exhausted");
+  PoolSlot& sl = p->slots[(size_t)s];
+  const cudaEvent_t ev = sl.ready;
+  sl = PoolSlot{};
+  sl.ready = ev;
+  sl.used = true;
+  sl.n = n;
+  sl.m = m;
+  sl.iters_left = p->unlimited ? -1 : iterations;
+  sl.off = off;
+  sl.bytes = L.total;
+  Instance& I = sl.I;
+  I.n = n;
+  I.m = m;
+  I.ld = (n + 3) / 4 * 4;
+  I.ldt = (n + 1 + 3) / 4 * 4;
+  I.ldm = (m + 31) / 32 * 32;
+  I.alpha = alpha;
+  I.beta = beta;
+  I.rho = rho;
+  I.seed = seed;
+  char* b = (char*)p->arena + off;
+  I.dist = (const int32_t*)(b + L.dist);
+  I.heta = (float*)(b + L.heta);
+  I.tau = (float*)(b + L.tau);
+  I.choice = (float*)(b + L.choice);
+  I.tours = (int32_t*)(b + L.tours);
+  I.lens = (long long*)(b + L.lens);
+  I.nbr = (uint32_t*)(b + L.nbr);
+  I.q = (unsigned long long*)(b + L.q);
+  I.delta = (float*)(b + L.delta);
+  I.acc = nullptr;
+  I.best_tour = (int32_t*)(b + L.best);
+  I.st = (IterState*)(b + L.st);
+  cudaError_t e = cudaSuccess;
+  // Sources of the asynchronous copies below must outlive this call: the
+  // initial state is a static constant and the descriptor lives in the slot.
+  static const IterState st0 = [] {
+    IterState z{};
+    z.best_len = INT64_MAX;
+    return z;
+  }();
+  do {
+    if (!sl.ready && (e = cudaEventCreateWithFlags(&sl.ready, cudaEventDisableTiming)) != cudaSuccess)
+      break;
+    if ((e = cudaMemsetAsync(b, 0, L.total, p->side)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(I.st, &st0, sizeof st0, cudaMemcpyHostToDevice, p->side)) !=
+        cudaSuccess)
+      break;
+    if (dist) {
+      e = cudaMemcpy2DAsync((void*)I.dist, (size_t)I.ld * 4, dist, (size_t)n * 4, (size_t)n * 4,
+                            (size_t)n, cudaMemcpyHostToDevice, p->side);
+    } else {
+      // stage the coordinates in the (not yet used) choice_info block
+      e = cudaMemcpyAsync(I.choice, xy, (size_t)n * 8, cudaMemcpyHostToDevice, p->side);
+      if (e == cudaSuccess) e = launch_dist_from_coords(I, (const int32_t*)I.choice, p->side);
+    }
+    if (e != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(p->d_inst + s, &sl.I, sizeof sl.I, cudaMemcpyHostToDevice,
+                             p->side)) != cudaSuccess)
+      break;
+    if ((e = launch_setup(I, p->sms, p->side)) != cudaSuccess) break;
+    e = cudaEventRecord(sl.ready, p->side);
+  } while (0);
+  if (e != cudaSuccess) {
+    pool_free(p, off, L.total);
+    sl.used = false;
+    return cuda_fail(e, "pool admit");
+  }
+  sl.live = true;
+  sl.wait_ready = true;
+  p->dirty = true;
+  *slot = s;
+  return ACO_OK;
+}
+
+static int pool_check_status(aco_pool* p, int slot) {
+  int status = 0;
+  cudaError_t e = cudaMemcpyAsync(&status, &p->slots[(size_t)slot].I.st->status, sizeof(int),
+                                  cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pool synchronize");
+  if (status & kStatusTimeout) return fail(ACO_ETIMEOUT, "a device-side wait gave up");
+  if (status) return fail(ACO_ECUDA, "device status 0x%x in slot %d", status, slot);
+  return ACO_OK;
+}
+
+extern "C" {
+
+int aco_pool_bytes_needed(int32_t n, int32_t m, uint64_t* bytes) {
+  if (!bytes) return fail(ACO_EINVAL, "NULL argument");
+  if (n < 3 || n > ACO_MAX_N || m < 1 || m > ACO_MAX_M) return fail(ACO_EINVAL, "n or m out of range");
+  *bytes = layout_of(n, m).total;
+  return ACO_OK;
+}
+
+int aco_pool_create(int32_t max_slots, uint64_t budget_bytes, aco_pool_handle* out) {
+  if (!out) return fail(ACO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_slots < 1 || max_slots > (1 << 20)) return fail(ACO_EINVAL, "max_slots out of range");
+  if (budget_bytes < 4096) return fail(ACO_EINVAL, "budget too small");
+  aco_pool* p = new (std::nothrow) aco_pool();
+  if (!p) return fail(ACO_ENOMEM, "host allocation");
+  p->max_slots = max_slots;
+  p->budget = align256(budget_bytes);
+  p->slots.resize((size_t)max_slots);
+  p->sms = device_sms();
+  cudaError_t e;
+  do {
+    if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&p->arena, p->budget)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&p->d_inst, sizeof(Instance) * (size_t)max_slots)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&p->d_live, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
+  } while (0);
+  if (e != cudaSuccess) {
+    const int rc = cuda_fail(e, "pool create");
+    aco_pool_destroy(p);
+    return rc;
+  }
+  p->free_blocks[0] = p->budget;
+  *out = p;
+  return ACO_OK;
+}
+
+int aco_pool_destroy(aco_pool_handle p) {
+  if (!p) return ACO_OK;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  if (p->side) cudaStreamSynchronize(p->side);
+  pool_drop_graph(p);
+  for (auto& s : p->slots)
+    if (s.ready) cudaEventDestroy(s.ready);
+  if (p->arena) cudaFree(p->arena);
+  if (p->d_inst) cudaFree(p->d_inst);
+  if (p->d_live) cudaFree(p->d_live);
+  if (p->d_items) cudaFree(p->d_items);
+  if (p->d_rows) cudaFree(p->d_rows);
+  if (p->stream) cudaStreamDestroy(p->stream);
+  if (p->side) cudaStreamDestroy(p->side);
+  delete p;
+  return ACO_OK;
+}
+
+int aco_pool_admit(aco_pool_handle p, int32_t n, const int32_t* dist, float alpha, float beta,
+                   float rho, int32_t m, uint64_t seed, int32_t iterations, int32_t* slot) {
+  if (!dist) return fail(ACO_EINVAL, "dist is NULL");
+  return pool_admit_common(p, n, dist, nullptr, alpha, beta, rho, m, seed, iterations, slot);
+}
+
+int aco_pool_admit_coords(aco_pool_handle p, int32_t n, const int32_t* xy, float alpha,
+                          float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
+                          int32_t* slot) {
+  if (!xy) return fail(ACO_EINVAL, "xy is NULL");
+  return pool_admit_common(p, n, nullptr, xy, alpha, beta, rho, m, seed, iterations, slot);
+}
+
+int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  int rc;
+  if (p->dirty && (rc = pool_rebuild(p)) != ACO_OK) return rc;
+  cudaError_t e;
+  if (!p->h_live.empty()) {
+    for (int s : p->h_live) {
+      PoolSlot& sl = p->slots[(size_t)s];
+      if (sl.wait_ready) {
+        if ((e = cudaStreamWaitEvent(p->stream, sl.ready, 0)) != cudaSuccess)
+          return cuda_fail(e, "wait setup");
+        sl.wait_ready = false;
+      }
+    }
+    if (!p->exec) {
+      cudaGraph_t g = nullptr;
+      if ((e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "pool capture");
+      rc = pool_enqueue_step(p);
+      e = cudaStreamEndCapture(p->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "pool end capture");
+      e = cudaGraphInstantiate(&p->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        p->exec = nullptr;
+        return cuda_fail(e, "pool instantiate");
+      }
+    }
+    if ((e = cudaGraphLaunch(p->exec, p->stream)) != cudaSuccess) return cuda_fail(e, "pool launch");
+    for (int s : p->h_live) {
+      PoolSlot& sl = p->slots[(size_t)s];
+      if (sl.iters_left > 0 && --sl.iters_left == 0) {
+        sl.live = false;
+        sl.finished = true;
+        p->finished_order.push_back(s);
+        p->dirty = true;
+      }
+    }
+  } else {
+    p->launches = 0;
+  }
+  if (live_after) {
+    int live = 0;
+    for (const auto& sl : p->slots) live += sl.live ? 1 : 0;
+    *live_after = live;
+  }
+  return ACO_OK;
+}
+
+int aco_pool_finished(aco_pool_handle p, int32_t* slots, int32_t capacity, int32_t* count) {
+  if (!p || !count) return fail(ACO_EINVAL, "NULL argument");
+  const int total = (int)p->finished_order.size();
+  for (int i = 0; i < total && i < capacity && slots; ++i) slots[i] = p->finished_order[(size_t)i];
+  *count = total;
+  return ACO_OK;
+}
+
+int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t* tour, int64_t* len) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].used)
+    return fail(ACO_EINVAL, "slot %d is not in use", slot);
+  const PoolSlot& sl = p->slots[(size_t)slot];
+  cudaError_t e = cudaStreamSynchronize(p->side);
+  if (e == cudaSuccess && tour)
+    e = cudaMemcpyAsync(tour, sl.I.best_tour, ((size_t)sl.n + 1) * 4, cudaMemcpyDeviceToHost,
+                        p->stream);
+  if (e == cudaSuccess && len)
+    e = cudaMemcpyAsync(len, &sl.I.st->best_len, 8, cudaMemcpyDeviceToHost, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pool result");
+  return pool_check_status(p, slot);
+}
+
+int aco_pool_pheromone(aco_pool_handle p, int32_t slot, float* tau) {
+  if (!p || !tau) return fail(ACO_EINVAL, "NULL argument");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].used)
+    return fail(ACO_EINVAL, "slot %d is not in use", slot);
+  const PoolSlot& sl = p->slots[(size_t)slot];
+  cudaError_t e = cudaStreamSynchronize(p->side);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(tau, (size_t)sl.n * 4, sl.I.tau, (size_t)sl.I.ld * 4, (size_t)sl.n * 4,
+                          (size_t)sl.n, cudaMemcpyDeviceToHost, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pool pheromone");
+  return pool_check_status(p, slot);
+}
+
+int aco_pool_release(aco_pool_handle p, int32_t slot) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].used)
+    return fail(ACO_EINVAL, "slot %d is not in use", slot);
+  // Work that still reads the slot must finish before its memory is reused.
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->side);
+  if (e != cudaSuccess) return cuda_fail(e, "pool release");
+  PoolSlot& sl = p->slots[(size_t)slot];
+  if (sl.live) p->dirty = true;
+  pool_free(p, sl.off, sl.bytes);
+  cudaEvent_t ev = sl.ready;
+  sl = PoolSlot{};
+  sl.ready = ev;
+  auto& fo = p->finished_order;
+  fo.erase(std::remove(fo.begin(), fo.end(), slot), fo.end());
+  return ACO_OK;
+}
+
+int aco_pool_stats(aco_pool_handle p, int32_t* live, int32_t* finished, uint64_t* bytes_in_use,
+                   int32_t* launches_last_step) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  int l = 0;
+  for (const auto& sl : p->slots) l += sl.live ? 1 : 0;
+  if (live) *live = l;
+  if (finished) *finished = (int32_t)p->finished_order.size();
+  if (bytes_in_use) *bytes_in_use = p->in_use;
+  if (launches_last_step) *launches_last_step = p->launches;
+  return ACO_OK;
+}
+
+int aco_pool_synchronize(aco_pool_handle p) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  cudaError_t e = cudaStreamSynchronize(p->side);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pool synchronize");
+  for (int s = 0; s < p->max_slots; ++s)
+    if (p->slots[(size_t)s].used) {
+      const int rc = pool_check_status(p, s);
+      if (rc) return rc;
+    }
+  return ACO_OK;
+}
+
+int aco_batch_create(int32_t count, const int32_t* ns, const int32_t* const* dists,
+                     const float* alpha, const float* beta, const float* rho, const int32_t* ms,
+                     const uint64_t* seeds, aco_batch* out) {
+  if (!out) return fail(ACO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !ns || !dists || !alpha || !beta || !rho || !ms || !seeds)
+    return fail(ACO_EINVAL, "bad batch arguments");
+  uint64_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    uint64_t b = 0;
+    const int rc = aco_pool_bytes_needed(ns[i], ms[i], &b);
+    if (rc) return rc;
+    total += b;
+  }
+  aco_pool* p = nullptr;
+  int rc = aco_pool_create(count, total, &p);
+  if (rc) return rc;
+  p->unlimited = true;
+  for (int i = 0; i < count; ++i) {
+    int32_t slot = -1;
+    rc = aco_pool_admit(p, ns[i], dists[i], alpha[i], beta[i], rho[i], ms[i], seeds[i], 1, &slot);
+    if (rc) {
+      aco_pool_destroy(p);
+      return rc;
+    }
+  }
+  *out = p;
+  return ACO_OK;
+}
+
+int aco_batch_iterate(aco_batch b, int32_t iterations) {
+  if (!b) return fail(ACO_EINVAL, "NULL batch");
+  if (iterations < 0) return fail(ACO_EINVAL, "iterations < 0");
+  for (int i = 0; i < iterations; ++i) {
+    const int rc = aco_pool_step(b, nullptr);
+    if (rc) return rc;
+  }
+  return ACO_OK;
+}
+
+int aco_batch_best(aco_batch b, int32_t idx, int32_t* tour, int64_t* len) {
+  return aco_pool_result(b, idx, tour, len);
+}
+
+int aco_batch_destroy(aco_batch b) { return aco_pool_destroy(b); }
+
+}  // extern "C"

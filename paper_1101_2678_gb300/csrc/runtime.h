@@ -17,4 +17,8 @@ int device_sms();
 int validate_instance(int32_t n, const int32_t* dist, float alpha, float beta, float rho,
                       int32_t m);
 
+// Coordinates for aco_create_coords / aco_pool_admit_coords: range and
+// pairwise distinctness.
+int validate_coords_public(int32_t n, const int32_t* xy);
+
 }  // namespace aco

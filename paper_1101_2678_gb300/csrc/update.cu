@@ -4,6 +4,7 @@
 
 #include "aco_device.cuh"
 #include "kernels.h"
+#include "update.cuh"
 
 namespace aco {
 
@@ -118,149 +119,23 @@ __global__ void choice_kernel(Instance I, int bump_iteration) {
   if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
 }
 
-// ---------------------------------------------------------------------------
-// Iteration best, best-so-far and the per-ant deposits dtau^k, q_k.
-// ---------------------------------------------------------------------------
-__global__ void best_kernel(Instance I) {
-  __shared__ long long red_l[32];
-  __shared__ int red_k[32];
-  __shared__ int s_best, s_shift, s_improved;
-  const int m = I.m, n = I.n;
-  long long bl = LLONG_MAX;
-  int bk = INT_MAX;
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    const long long L = I.lens[k];
-    if (L < bl) {
-      bl = L;
-      bk = k;
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long ol = __shfl_xor_sync(FULL, bl, o);
-    const int ok = __shfl_xor_sync(FULL, bk, o);
-    if (ol < bl || (ol == bl && ok < bk)) {
-      bl = ol;
-      bk = ok;
-    }
-  }
-  if (lane == 0) {
-    red_l[warp] = bl;
-    red_k[warp] = bk;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-      if (red_l[w] < bl || (red_l[w] == bl && red_k[w] < bk)) {
-        bl = red_l[w];
-        bk = red_k[w];
-      }
-    const float dmax = (float)(1.0 / (double)bl);
-    const int S = 62 - ceil_log2_u32((uint32_t)m) - exponent_of_bits(__float_as_uint(dmax));
-    IterState* st = I.st;
-    st->iter_best_len = bl;
-    st->iter_best_ant = bk;
-    st->deposit_shift = S;
-    s_improved = bl < st->best_len;
-    if (s_improved) st->best_len = bl;
-    s_best = bk;
-    s_shift = S;
-  }
-  __syncthreads();
-  const double scale = pow2d(s_shift);
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    const float dk = (float)(1.0 / (double)I.lens[k]);
-    I.delta[k] = dk;
-    I.q[k] = __double2ull_rz((double)dk * scale);
-  }
-  if (s_improved) {
-    const int32_t* src = I.tours + (size_t)s_best * I.ldt;
-    for (int s = threadIdx.x; s <= n; s += blockDim.x) I.best_tour[s] = src[s];
-  }
-}
+// Iteration best, best-so-far and per-ant deposits: best_body() in update.cuh.
+__global__ void best_kernel(Instance I) { best_body(I); }
 
 // ---------------------------------------------------------------------------
 // Pheromone update
 // ---------------------------------------------------------------------------
 
-// tau' = fl(fl((1-rho) tau) + dep), dep = fl(acc) * 2^-S (Eqs. 2-4).
-__device__ __forceinline__ float apply_deposit(float tau, unsigned long long acc, float keep,
-                                               float inv_scale) {
-  const float dep = __fmul_rn(__ull2float_rn(acc), inv_scale);
-  return __fadd_rn(__fmul_rn(keep, tau), dep);
-}
-
-__device__ __forceinline__ float inv_scale_of(int S) {
-  // 2^-S.  3 <= C^k < 2^44 (n <= 4096, int32 distances) and m <= 16384 put S
-  // in [50, 106], inside the normal float range.
-  return pow2f(-S);
-}
-
-// Atomic-free "scatter to gather" deposit fused with evaporation and
-// choice_info.  One warp per row i: the construction kernel bucketed every
-// tour edge under both of its cities (nbr[i][k] = predecessor and successor of
-// i in tour k), so row i's deposit is a segmented reduction of 2m (column,
-// q_k) pairs.  Lanes holding the same column are grouped with match.any and
-// summed by shuffles; the group leader adds the group sum to the warp's
-// private u64 row in shared memory.  No atomics, exact, deterministic.
+// Gather deposit fused with evaporation and choice_info (gather_row() in
+// update.cuh): one warp per row.
 __global__ void update_gather_kernel(Instance I, int bump_iteration) {
   extern __shared__ unsigned long long acc_rows[];
   const int warps = blockDim.x >> 5;
   const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * warps + wi;
-  const int n = I.n, ld = I.ld, m = I.m;
   if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
-  if (i >= n) return;
-  unsigned long long* acc = acc_rows + (size_t)wi * ld;
-  for (int j = lane; j < ld; j += 32) acc[j] = 0ull;
-  __syncwarp();
-  const uint32_t* nb = I.nbr + (size_t)i * I.ldm;
-  for (int k0 = 0; k0 < m; k0 += 32) {
-    const int k = k0 + lane;
-    const bool valid = k < m;
-    const uint32_t ps = valid ? nb[k] : 0u;
-    const unsigned long long qk = valid ? I.q[k] : 0ull;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const uint32_t col = valid ? (half ? (ps & 0xffffu) : (ps >> 16)) : 0xffffffffu;
-      const uint32_t grp = __match_any_sync(FULL, col);
-      const int rounds = (int)__reduce_max_sync(FULL, (uint32_t)__popc(grp));
-      uint32_t rem = grp;
-      unsigned long long sum = 0;
-      for (int r = 0; r < rounds; ++r) {
-        const int src = rem ? __ffs(rem) - 1 : lane;
-        const unsigned long long val = shfl_u64(qk, src);
-        if (rem) {
-          sum += val;
-          rem &= rem - 1;
-        }
-      }
-      if (valid && lane == __ffs(grp) - 1) acc[col] += sum;
-      __syncwarp();
-    }
-  }
-  const float keep = __fsub_rn(1.0f, I.rho);
-  const float inv = inv_scale_of(I.st->deposit_shift);
-  const float alpha = I.alpha;
-  float* tau = I.tau + (size_t)i * ld;
-  const float* heta = I.heta + (size_t)i * ld;
-  float* ch = I.choice + (size_t)i * ld;
-  for (int j = lane * 4; j < ld; j += 128) {
-    const float4 t4 = *reinterpret_cast<const float4*>(tau + j);
-    const float4 h4 = *reinterpret_cast<const float4*>(heta + j);
-    float4 o, c;
-    o.x = apply_deposit(t4.x, acc[j + 0], keep, inv);
-    o.y = apply_deposit(t4.y, acc[j + 1], keep, inv);
-    o.z = apply_deposit(t4.z, acc[j + 2], keep, inv);
-    o.w = apply_deposit(t4.w, acc[j + 3], keep, inv);
-    c.x = choice_of(o.x, h4.x, alpha);
-    c.y = choice_of(o.y, h4.y, alpha);
-    c.z = choice_of(o.z, h4.z, alpha);
-    c.w = choice_of(o.w, h4.w, alpha);
-    *reinterpret_cast<float4*>(tau + j) = o;
-    *reinterpret_cast<float4*>(ch + j) = c;
-  }
+  if (i >= I.n) return;
+  gather_row(I, i, acc_rows + (size_t)wi * I.ld, lane);
 }
 
 // Atomic deposit in 64-bit fixed point: one thread per tour edge (k, s) adds
@@ -341,6 +216,49 @@ __global__ void deposit_atomic_f32_kernel(Instance I) {
 }
 
 // ---------------------------------------------------------------------------
+// Batched forms: one CTA (best) or one warp (update row) per list entry.
+// ---------------------------------------------------------------------------
+__global__ void best_slots_kernel(const Instance* __restrict__ insts, const int* __restrict__ slots,
+                                  int count) {
+  if ((int)blockIdx.x >= count) return;
+  const Instance I = insts[slots[blockIdx.x]];
+  best_body(I);
+}
+
+__global__ void update_rows_kernel(const Instance* __restrict__ insts, const int2* __restrict__ rows,
+                                   int count, int max_ld) {
+  extern __shared__ unsigned long long acc_rows[];
+  const int warps = blockDim.x >> 5;
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * warps + wi;
+  if (idx >= count) return;
+  const int2 it = rows[idx];
+  const Instance I = insts[it.x];
+  if (it.y == 0 && lane == 0) I.st->iteration += 1;
+  gather_row(I, it.y, acc_rows + (size_t)wi * max_ld, lane);
+}
+
+// Rounded Euclidean distances (TSPLIB EUC_2D): d = floor(sqrt(dx^2 + dy^2) +
+// 0.5) in IEEE double (exact squares for |coordinates| <= 2^25), written into
+// the instance's padded distance matrix.
+__global__ void dist_from_coords_kernel(Instance I, const int32_t* __restrict__ xy) {
+  const int n = I.n, ld = I.ld;
+  const size_t total = (size_t)n * ld;
+  int32_t* dist = const_cast<int32_t*>(I.dist);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    int32_t d = 0;
+    if (j < n && j != i) {
+      const double dx = (double)xy[2 * i] - (double)xy[2 * j];
+      const double dy = (double)xy[2 * i + 1] - (double)xy[2 * j + 1];
+      d = (int32_t)floor(__dsqrt_rn(dx * dx + dy * dy) + 0.5);
+    }
+    dist[e] = d;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
 static int grid_for(size_t work, int threads, int sms) {
@@ -369,6 +287,35 @@ cudaError_t launch_choice(const Instance& I, int sms, cudaStream_t st) {
 
 cudaError_t launch_best(const Instance& I, cudaStream_t st) {
   best_kernel<<<1, 1024, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_best_slots(const Instance* insts, const int* slots, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  best_slots_kernel<<<count, 256, 0, st>>>(insts, slots, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_rows(const Instance* insts, const int2* rows, int count, int max_ld,
+                               cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int w = gather_warps_per_cta(max_ld);
+  const size_t smem = (size_t)w * max_ld * sizeof(unsigned long long);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(update_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         100 * 1024);
+    attr_set = true;
+  }
+  update_rows_kernel<<<(count + w - 1) / w, 32 * w, smem, st>>>(insts, rows, count, max_ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dist_from_coords(const Instance& I, const int32_t* xy, cudaStream_t st) {
+  const size_t total = (size_t)I.n * I.ld;
+  size_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  dist_from_coords_kernel<<<(int)blocks, 256, 0, st>>>(I, xy);
   return cudaGetLastError();
 }
 

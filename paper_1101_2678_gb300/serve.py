@@ -1,0 +1,126 @@
+"""Continuous-batching solve server over an aco pool.
+
+Requests (TSP instances given by integer coordinates) arrive over time.  The
+server admits them in arrival order whenever the pool has a free slot and
+enough of its HBM budget, keeps every admitted instance's state resident on
+the device, and runs one Ant System iteration for all live instances per
+step, so work from requests that arrived at different times overlaps on the
+GPU.  A request finishes after its own number of iterations; its latency is
+completion time minus arrival time (queueing included).
+
+All compute happens in the library's kernels (aco_pool_step); this module only
+decides which request enters which slot and when.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import aco
+
+
+@dataclass
+class Request:
+    coords: np.ndarray  # (n, 2) int
+    m: int
+    iterations: int
+    seed: int
+    alpha: float = 1.0
+    beta: float = 2.0
+    rho: float = 0.5
+
+    @property
+    def n(self) -> int:
+        return int(self.coords.shape[0])
+
+
+@dataclass
+class Outcome:
+    index: int
+    arrival: float
+    admitted: float
+    finished: float
+    best_len: int
+    best_tour: np.ndarray = field(repr=False)
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Server:
+    def __init__(self, budget_bytes: int = 64 << 30, max_slots: int = 2048):
+        self.pool = aco.aco_pool_create(max_slots, budget_bytes)
+        self.budget = budget_bytes
+        self.max_slots = max_slots
+
+    def close(self):
+        if self.pool is not None:
+            aco.aco_pool_destroy(self.pool)
+            self.pool = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def run(self, requests, arrivals, deadline: float | None = None, realtime: bool = True):
+        """Serve `requests` arriving at `arrivals` (seconds from start).
+
+        realtime=True follows the wall clock (a request is visible once its
+        arrival time has passed); realtime=False makes every request available
+        immediately in arrival order (a throughput run).  Stops when all
+        requests are done or, with `deadline`, at the first step boundary past
+        it.  Returns (outcomes, stats)."""
+        pool = self.pool
+        total = len(requests)
+        order = np.argsort(np.asarray(arrivals), kind="stable")
+        queue = collections.deque()
+        live = {}  # slot -> (request index, admit time)
+        outcomes = []
+        nxt = 0
+        steps = 0
+        max_live = 0
+        t0 = time.perf_counter()
+        while len(outcomes) < total:
+            now = time.perf_counter() - t0
+            if deadline is not None and now >= deadline:
+                break
+            while nxt < total and (not realtime or arrivals[order[nxt]] <= now):
+                queue.append(int(order[nxt]))
+                nxt += 1
+            while queue:
+                r = requests[queue[0]]
+                slot = aco.aco_pool_admit_coords(pool, r.coords, r.alpha, r.beta, r.rho, r.m,
+                                                 r.seed, r.iterations)
+                if slot is None:
+                    break
+                live[slot] = (queue.popleft(), time.perf_counter() - t0)
+            if not live:
+                if nxt < total:
+                    time.sleep(max(0.0, min(0.01, arrivals[order[nxt]] - now)))
+                continue
+            max_live = max(max_live, len(live))
+            aco.aco_pool_step(pool)
+            steps += 1
+            for slot in aco.aco_pool_finished(pool):
+                ri, tadm = live.pop(slot)
+                tour, length = aco.aco_pool_result(pool, slot, requests[ri].n)
+                tfin = time.perf_counter() - t0
+                outcomes.append(Outcome(ri, float(arrivals[ri]), tadm, tfin, length, tour))
+                aco.aco_pool_release(pool, slot)
+        aco.aco_pool_synchronize(pool)
+        elapsed = time.perf_counter() - t0
+        lat = np.array([o.latency for o in outcomes]) if outcomes else np.zeros(1)
+        stats = dict(
+            completed=len(outcomes), submitted=nxt, total=total,
+            backlog=total - len(outcomes), still_live=len(live), queued=len(queue),
+            elapsed_s=elapsed, steps=steps, max_live=max_live,
+            solves_per_s=len(outcomes) / elapsed if elapsed > 0 else 0.0,
+            p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+        )
+        return outcomes, stats

@@ -1,0 +1,143 @@
+"""Batched and served instances (aco_pool_* / aco_batch_*) on the GPU.
+
+Every instance in a pool keeps its own seed and iteration counter, and the
+pool uses the deterministic gather deposit, so an instance's pheromone and
+best tour must be identical bit for bit whether it runs alone, in a static
+batch, or admitted mid-stream next to other instances of different sizes.
+"""
+import numpy as np
+import pytest
+
+from paper_1101_2678_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aco():
+    from paper_1101_2678_gb300 import build
+    build.build()
+    from paper_1101_2678_gb300 import aco as a
+    a.load()
+    return a
+
+
+def alone(aco, dist, m, seed, iters):
+    n = dist.shape[0]
+    with aco.Colony(dist, m, seed=seed) as c:
+        aco.aco_iterate(c.h, iters)
+        return aco.aco_get_pheromone(c.h, n), aco.aco_best_tour(c.h, n)
+
+
+def test_static_batch_equals_alone(aco, orc):
+    ns = [48, 300, 97, 1024, 5, 130, 517]
+    insts = [I.uniform_instance(n, 1000, seed=500 + n) for n in ns]
+    ms = [n if n < 1000 else 200 for n in ns]
+    seeds = [900 + i for i in range(len(ns))]
+    b = aco.aco_batch_create([x.dist for x in insts], ms, seeds)
+    try:
+        aco.aco_batch_iterate(b, 6)
+        for i, x in enumerate(insts):
+            tau_a, (tour_a, len_a) = alone(aco, x.dist, ms[i], seeds[i], 6)
+            tour_b, len_b = aco.aco_batch_best(b, i, x.n)
+            assert len_b == len_a and np.array_equal(tour_b, tour_a), i
+            assert np.array_equal(aco.aco_pool_pheromone(b, i, x.n), tau_a), i
+    finally:
+        aco.aco_batch_destroy(b)
+    # and the oracle agrees for the small ones
+    for i in [0, 4]:
+        ref = orc.run(insts[i].dist, ms[i], 6, seeds[i])
+        tau_a, (_, len_a) = alone(aco, insts[i].dist, ms[i], seeds[i], 6)
+        assert np.array_equal(tau_a, ref["tau32"]) and len_a == ref["best_len"]
+
+
+def test_coordinates_build_the_same_instance(aco, orc):
+    inst = I.clustered_instance(333, seed=4)
+    h = aco.aco_create_coords(inst.coords, 1.0, 2.0, 0.5, 64, 3)
+    try:
+        assert np.array_equal(aco.aco_get_heuristic(h, 333), orc.heta(inst.dist, 2.0))
+        assert aco.aco_get_tau0(h)[1] == orc.nn_tour_length(inst.dist)
+        aco.aco_iterate(h, 3)
+        tau = aco.aco_get_pheromone(h, 333)
+    finally:
+        aco.aco_destroy(h)
+    assert np.array_equal(tau, orc.run(inst.dist, 64, 3, 3)["tau32"])
+    with pytest.raises(aco.AcoError) as e:
+        aco.aco_create_coords(np.array([[0, 0], [5, 5], [0, 0]]), 1.0, 2.0, 0.5, 3, 1)
+    assert e.value.code == aco.ACO_EINVAL
+
+
+def test_continuous_admission_equals_alone(aco):
+    a = I.uniform_instance(400, 1000, seed=41)
+    b = I.clustered_instance(150, seed=42, clusters=8, side=3000)
+    c = I.uniform_instance(64, 1000, seed=43)
+    budget = sum(aco.aco_pool_bytes_needed(x.n, x.n) for x in (a, b, c)) + (1 << 20)
+    p = aco.aco_pool_create(8, budget)
+    try:
+        sa = aco.aco_pool_admit_coords(p, a.coords, 1.0, 2.0, 0.5, a.n, 7, 10)
+        for _ in range(3):
+            aco.aco_pool_step(p)
+        sb = aco.aco_pool_admit_coords(p, b.coords, 1.0, 2.0, 0.5, b.n, 8, 5)
+        aco.aco_pool_step(p)
+        sc = aco.aco_pool_admit(p, c.dist, 1.0, 2.0, 0.5, c.n, 9, 4)
+        steps = 0
+        while aco.aco_pool_step(p) > 0:
+            steps += 1
+            assert steps < 50
+        fin = aco.aco_pool_finished(p)
+        assert sorted(fin) == sorted([sa, sb, sc])
+        for slot, x, seed, iters in [(sa, a, 7, 10), (sb, b, 8, 5), (sc, c, 9, 4)]:
+            tau_a, (tour_a, len_a) = alone(aco, x.dist, x.n, seed, iters)
+            tour_p, len_p = aco.aco_pool_result(p, slot, x.n)
+            assert len_p == len_a and np.array_equal(tour_p, tour_a)
+            assert np.array_equal(aco.aco_pool_pheromone(p, slot, x.n), tau_a)
+            aco.aco_pool_release(p, slot)
+        st = aco.aco_pool_stats(p)
+        assert st["live"] == 0 and st["finished"] == 0 and st["bytes_in_use"] == 0
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+def test_budget_and_slots_refuse_then_recover(aco):
+    x = I.uniform_instance(200, 1000, seed=5)
+    need = aco.aco_pool_bytes_needed(200, 200)
+    p = aco.aco_pool_create(4, need + need // 2)
+    try:
+        s0 = aco.aco_pool_admit_coords(p, x.coords, 1.0, 2.0, 0.5, 200, 1, 2)
+        assert s0 is not None
+        assert aco.aco_pool_admit_coords(p, x.coords, 1.0, 2.0, 0.5, 200, 2, 2) is None
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_admit(p, x.dist, 1.0, 2.0, 0.5, 200, 2, 2)
+        assert e.value.code == aco.ACO_EBUSY
+        aco.aco_pool_step(p)
+        aco.aco_pool_step(p)
+        assert aco.aco_pool_finished(p) == [s0]
+        aco.aco_pool_release(p, s0)
+        s1 = aco.aco_pool_admit_coords(p, x.coords, 1.0, 2.0, 0.5, 200, 2, 1)
+        assert s1 is not None
+        aco.aco_pool_step(p)
+        aco.aco_pool_synchronize(p)
+    finally:
+        aco.aco_pool_destroy(p)
+    p = aco.aco_pool_create(1, 1 << 30)
+    try:
+        aco.aco_pool_admit_coords(p, x.coords, 1.0, 2.0, 0.5, 10, 1, 1)
+        assert aco.aco_pool_admit_coords(p, x.coords, 1.0, 2.0, 0.5, 10, 1, 1) is None
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+def test_pool_rejects_bad_arguments(aco):
+    p = aco.aco_pool_create(2, 1 << 24)
+    try:
+        x = I.uniform_instance(10, 100, seed=1)
+        for kw in [dict(rho=0.0), dict(m=0), dict(iterations=0)]:
+            args = dict(alpha=1.0, beta=2.0, rho=0.5, m=5, seed=1, iterations=3)
+            args.update(kw)
+            with pytest.raises(aco.AcoError) as e:
+                aco.aco_pool_admit(p, x.dist, **args)
+            assert e.value.code == aco.ACO_EINVAL
+        with pytest.raises(aco.AcoError):
+            aco.aco_pool_result(p, 0, 10)
+    finally:
+        aco.aco_pool_destroy(p)
