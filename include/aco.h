@@ -32,8 +32,8 @@
  *    counter = (step, ant, iteration, 0); an ant starts at
  *    floor(x0 * n / 2^32) ("ants are randomly placed", Section II).
  *  - Eq. 1 is sampled exactly by an integer roulette: with M the largest
- *    unvisited weight and B = 50, q_j = floor(w_j * 2^(B-1-ilogb M)) for
- *    unvisited j (so Q < 2^62 for n <= 4096), T = floor(r Q / 2^64) with
+ *    unvisited weight and B = 46, q_j = floor(w_j * 2^(B-1-ilogb M)) for
+ *    unvisited j (so Q < 2^58 for n <= 4096), T = floor(r Q / 2^64) with
  *    r = x1 * 2^32 + x0 and Q = sum q_j, and the chosen city is the first j
  *    (ascending) whose prefix sum exceeds T; if M == 0 the lowest unvisited
  *    city.  The result does not depend on how the kernel tiles the row.

@@ -31,9 +31,9 @@
  *     start = floor(x0 * n / 2^32) ("ants are randomly placed", Section II).
  *     Step s >= 1 draws r = x1 * 2^32 + x0.
  *  R2 Eq. 1 is sampled by an exact integer roulette: with M the largest weight
- *     among unvisited cities and B = 50, each unvisited weight w_j becomes
- *     q_j = floor(w_j * 2^(B-1-ilogb M)) < 2^50; for n <= 4096 = 2^12 cities
- *     Q = sum q_j < 2^62 fits 64 bits.  The target is
+ *     among unvisited cities and B = 46, each unvisited weight w_j becomes
+ *     q_j = floor(w_j * 2^(B-1-ilogb M)) < 2^46; for n <= 4096 = 2^12 cities
+ *     Q = sum q_j < 2^58 fits 64 bits.  The target is
  *     T = floor(r * Q / 2^64); the chosen city is the first j (ascending index)
  *     whose inclusive prefix sum of q exceeds T.  P(j) = q_j / Q.  If M = 0
  *     the lowest-index unvisited city is taken.
@@ -118,7 +118,7 @@ static int exponent_of(float x)
 /* w: weights of row i (n entries), visited: 1 for cities in the tabu list.  */
 /* Returns the chosen city, -1 if every city is visited, -2 if n > 4096.     */
 /* ------------------------------------------------------------------------- */
-#define ROULETTE_BITS 50
+#define ROULETTE_BITS 46
 #define ROULETTE_MAX_N 4096
 
 int orc_roulette(int n, const float *w, const uint8_t *visited, uint64_t r)

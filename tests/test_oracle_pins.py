@@ -60,7 +60,7 @@ def test_ceil_log2(orc):
 
 def test_roulette_weights_are_proportional(orc):
     # q_j / Q must equal w_j / sum(w) (Eq. 1) up to the quantisation step,
-    # i.e. |q_j/Q - p_j| <= n / 2^(B-1) with B = 50 bits per weight.
+    # i.e. |q_j/Q - p_j| <= n / 2^(B-1) with B = 46 bits per weight.
     rng = np.random.default_rng(0)
     for n in [3, 6, 48, 1002, 4096]:
         w = rng.lognormal(0.0, 3.0, size=n).astype(np.float32)
@@ -69,7 +69,7 @@ def test_roulette_weights_are_proportional(orc):
         q, Q = orc.roulette_weights(w, vis)
         assert Q == int(q.sum()) and Q < 2**62
         W = sum(Fraction(float(x)) for x, v in zip(w, vis) if not v)
-        B = 50
+        B = 46
         assert int(q.max()) < 2**B <= 2 * int(q.max())
         for j in range(n):
             if vis[j]:
