@@ -34,13 +34,15 @@ int cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // Construction tilings
 // ---------------------------------------------------------------------------
-static const int kCg1[] = {4, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80};
-static const int kCg2[] = {8, 12, 16, 20, 24, 32, 40, 48, 64};
-static const int kCg4[] = {4, 8, 12, 16, 20, 24, 32};
+// Cities per thread: multiples of 4 with C/4 odd (conflict-free chunk reads
+// from the staged row).
+static const int kCg1[] = {4, 12, 20, 28, 36, 44, 52, 60, 68, 76};
+static const int kCg2[] = {12, 20, 28, 36, 44, 52, 60, 68};
+static const int kCg4[] = {4, 12, 20, 28, 36};
 
 bool construct_supported(int C, int G) {
   const int* set = G == 1 ? kCg1 : G == 2 ? kCg2 : G == 4 ? kCg4 : nullptr;
-  const int cnt = G == 1 ? 11 : G == 2 ? 9 : G == 4 ? 7 : 0;
+  const int cnt = G == 1 ? 10 : G == 2 ? 8 : G == 4 ? 5 : 0;
   for (int i = 0; i < cnt; ++i)
     if (set && set[i] == C) return true;
   return false;
@@ -48,15 +50,15 @@ bool construct_supported(int C, int G) {
 
 ConstructTiling construct_tiling(int n, int G, int A) {
   const int* set = G == 1 ? kCg1 : G == 2 ? kCg2 : G == 4 ? kCg4 : nullptr;
-  const int cnt = G == 1 ? 11 : G == 2 ? 9 : G == 4 ? 7 : 0;
+  const int cnt = G == 1 ? 10 : G == 2 ? 8 : G == 4 ? 5 : 0;
   for (int i = 0; i < cnt; ++i)
     if (32 * G * set[i] >= n) return ConstructTiling{set[i], G, A};
   return ConstructTiling{0, G, A};
 }
 
 ConstructTiling default_construct_tiling(int n) {
-  if (n <= 32 * 80) return construct_tiling(n, 1, 4);
-  return construct_tiling(n, 2, 2);
+  if (n <= 32 * 76) return construct_tiling(n, 1, 4);
+  return construct_tiling(n, 2, 4);
 }
 
 cudaError_t launch_construct(const Instance& I, ConstructTiling t, cudaStream_t st) {

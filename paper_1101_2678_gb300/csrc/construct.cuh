@@ -8,10 +8,10 @@
 //   1. load row choice[cur] (C floats per thread), zero visited cities;
 //   2. M = max over unvisited (REDUX on the float bit patterns, which order
 //      like the values for w >= 0), across warps through shared memory;
-//   3. q_j = floor(w_j * 2^(49-ilogb M)) from the float's exponent and
-//      significand fields with 32-bit integer shifts and IMAD.WIDE (no
-//      float-to-int conversion), per-thread u64 sums, warp inclusive scan,
-//      group totals -> Q;
+//   3. q_j = floor(w_j * 2^(45-ilogb M)) split exactly into two 23-bit halves
+//      by FP32 round-toward-zero additions (FP32 pipe only; no float-to-int
+//      conversion and few integer ops), per-thread u64 sums, warp inclusive
+//      scan, group totals -> Q;
 //   4. T = floor(r Q / 2^64) with r from Philox (one Philox call per lane per
 //      32 steps, broadcast by shuffle);
 //   5. the thread whose prefix range holds T is found by ballot; its chunk is
@@ -46,49 +46,68 @@ __device__ __forceinline__ void group_sync(int bar_id, int nthreads) {
   }
 }
 
-// Roulette weight bits: q_j = floor(w_j * 2^(kBits-1-ilogb M)) < 2^kBits.
-constexpr int kRouletteBits = 50;
+// Roulette weight bits: q_j = floor(w_j * 2^(kRouletteBits-1-ilogb M)).
+constexpr int kRouletteBits = 46;
+constexpr float kTwo23 = 8388608.0f;
+constexpr uint32_t kTwo23Bits = 0x4b000000u;
 
-// acc + floor(w * 2^sc) for a float w >= 0 given by its bits b, with
-// k = 150 - sc and sc <= 126.  w = mant * 2^(E-150) for a normal w (E the
-// biased exponent field, mant the 24-bit significand), so the product is
-// mant << (E - k) or mant >> (k - E).  A subnormal or zero w has E = 0 and,
-// because k >= 24, contributes 0, which is its exact floor (w * 2^sc < 1).
-// Only 32-bit integer operations and one IMAD.WIDE.U32: no float-to-64-bit
-// conversion, which is slow on this part.  The result needs E - k <= 31,
-// which kRouletteBits = 50 guarantees (E - k <= 26).
-__device__ __forceinline__ unsigned long long add_floor_scaled(unsigned long long acc, uint32_t b,
-                                                               int k) {
-  const int e = (int)(b >> 23);
-  const uint32_t mant = (b & 0x7fffffu) | 0x800000u;
-  const uint32_t dn = (uint32_t)max(k - e, 0);
-  const uint32_t up = (uint32_t)max(e - k, 0);
-  return acc + (unsigned long long)__funnelshift_rc(mant, 0u, dn) * (1u << up);
+// q = floor(w * 2^sc) < 2^46 as hi * 2^23 + lo, on the FP32 pipe only.
+// t = w * 2^(sc-23) < 2^23 is exact (a power-of-two scaling); adding 2^23
+// with round-toward-zero gives 2^23 + floor(t); t - floor(t) is exact
+// (Sterbenz); fma.rz(frac, 2^23, 2^23) gives 2^23 + floor(frac * 2^23).
+// The two results are floats in [2^23, 2^24) whose bit patterns are
+// 0x4b000000 + hi and 0x4b000000 + lo.  f2 != 1 only when 2^(sc-23) is not
+// a float (largest unvisited weight below 2^-105): both scalings are exact.
+struct QuantParts {
+  uint32_t hi_bits, lo_bits;
+};
+
+__device__ __forceinline__ QuantParts quant_parts(uint32_t b, float f1, float f2) {
+  float t = __fmul_rn(__uint_as_float(b), f1);
+  if (f2 != 1.0f) t = __fmul_rn(t, f2);
+  const float zh = __fadd_rz(t, kTwo23);
+  const float hf = __fsub_rn(zh, kTwo23);
+  const float fr = __fsub_rn(t, hf);
+  const float zl = __fmaf_rz(fr, kTwo23, kTwo23);
+  return QuantParts{__float_as_uint(zh), __float_as_uint(zl)};
 }
 
-// Same for sc > 126 (only when the largest unvisited weight is below
-// 2^-77): scale exactly in float first (two power-of-two products, exact
-// since the result is normal or below 1), then the integer step with sc = 0.
-__device__ __forceinline__ unsigned long long add_floor_scaled_tiny(unsigned long long acc,
-                                                                    uint32_t b, float f1,
-                                                                    float f2) {
-  const float y = __fmul_rn(__fmul_rn(__uint_as_float(b), f1), f2);
-  return add_floor_scaled(acc, __float_as_uint(y), 150);
+__device__ __forceinline__ unsigned long long quant_value(uint32_t b, float f1, float f2) {
+  const QuantParts q = quant_parts(b, f1, f2);
+  return ((unsigned long long)(q.hi_bits - kTwo23Bits) << 23) + (q.lo_bits - kTwo23Bits);
 }
 
-template <int C>
-__device__ __forceinline__ unsigned long long chunk_sum(const uint32_t (&v)[C], int sc) {
-  unsigned long long s = 0;
-  if (sc <= 126) {
-    const int k = 150 - sc;
-#pragma unroll
-    for (int i = 0; i < C; ++i) s = add_floor_scaled(s, v[i], k);
+// Scale factors 2^(sc-23) for the step: one float when it exists.
+__device__ __forceinline__ void quant_factors(int sc, float& f1, float& f2) {
+  const int e = sc - 23;
+  if (e <= 127) {
+    f1 = pow2f(e);
+    f2 = 1.0f;
   } else {
-    const float f1 = pow2f(127), f2 = pow2f(sc - 127);
-#pragma unroll
-    for (int i = 0; i < C; ++i) s = add_floor_scaled_tiny(s, v[i], f1, f2);
+    f1 = pow2f(127);
+    f2 = pow2f(e - 127);
   }
-  return s;
+}
+
+// Sum of q over the thread's C weights (already scaled by f2, see the
+// caller).  The float bit patterns are summed modulo 2^32 (two per IADD3)
+// and the C offsets of 0x4b000000 removed once; the true part sums are below
+// C * 2^23 <= 2^30, so the wrap-around is exact.
+template <int C>
+__device__ __forceinline__ unsigned long long chunk_sum(const uint32_t (&v)[C], float f1) {
+  uint32_t hi0 = 0, lo0 = 0, hi1 = 0, lo1 = 0;
+#pragma unroll
+  for (int i = 0; i < C; i += 4) {
+    const QuantParts a = quant_parts(v[i], f1, 1.0f), b = quant_parts(v[i + 1], f1, 1.0f);
+    const QuantParts c = quant_parts(v[i + 2], f1, 1.0f), d = quant_parts(v[i + 3], f1, 1.0f);
+    hi0 += a.hi_bits + b.hi_bits;
+    lo0 += a.lo_bits + b.lo_bits;
+    hi1 += c.hi_bits + d.hi_bits;
+    lo1 += c.lo_bits + d.lo_bits;
+  }
+  const uint32_t off = (uint32_t)C * kTwo23Bits;
+  const uint32_t hi = hi0 + hi1 - off, lo = lo0 + lo1 - off;
+  return ((unsigned long long)hi << 23) + lo;
 }
 
 __device__ __forceinline__ unsigned long long warp_inclusive_scan(unsigned long long x, int lane) {
@@ -100,10 +119,20 @@ __device__ __forceinline__ unsigned long long warp_inclusive_scan(unsigned long 
   return x;
 }
 
+// Shared memory of one ant group: the staged row (32*G*C floats, 16-byte
+// aligned) followed by its mbarrier.
+template <int C, int G>
+struct StageLayout {
+  static constexpr int kRowFloats = 32 * G * C;
+  static constexpr int kBytes = ((kRowFloats * 4 + 8) + 15) / 16 * 16;
+};
+
 template <int C, int G>
 __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, const int tg,
-                                              GroupSmem* gs, const int bar_id) {
+                                              GroupSmem* gs, const int bar_id, float* srow) {
   static_assert(C % 4 == 0 && C >= 4 && C <= 128, "C must be a multiple of 4 in [4,128]");
+  static_assert((C / 4) % 2 == 1, "C/4 must be odd: lanes then read their chunks from shared "
+                                  "memory without bank conflicts");
   static_assert(G == 1 || G == 2 || G == 4, "G must be 1, 2 or 4");
   constexpr int NW = (C + 31) / 32;  // tabu words per thread
   constexpr int P = (C + 31) / 32;   // cities per lane in the rescan
@@ -141,20 +170,44 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   int cur = start;
   unsigned long long rwin = 0;
 
+  // Row staging: one thread copies row `cur` (4*ld bytes) into shared memory
+  // with the bulk-copy engine; the group waits on the mbarrier and every
+  // thread reads its contiguous chunk with conflict-free 16-byte loads.
+  const uint32_t srow_a = smem_u32(srow);
+  const uint32_t bar = srow_a + (uint32_t)StageLayout<C, G>::kRowFloats * 4u;
+  const uint32_t row_bytes = (uint32_t)ld * 4u;
+  uint32_t phase = 0;
+  bool waits_ok = true;
+  if (tg == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  group_sync(bar_id, NT);
+
   for (int s = 1; s < n; ++s) {
+    // Everyone is done with the previous row (the group agreed on `cur`).
+    if (tg == 0) {
+      fence_proxy_async_smem();
+      bulk_load(srow_a, I.choice + (size_t)cur * ld, row_bytes, bar);
+    }
     const int off = (s - 1) & 31;
     if (off == 0) {
       const Philox4 x = step_draw(seed, (uint32_t)(s + lane), (uint32_t)ant, iter);
       rwin = ((unsigned long long)x.x1 << 32) | x.x0;
     }
     const unsigned long long r = shfl_u64(rwin, off);
-    const float* row = I.choice + (size_t)cur * ld;
+    if (waits_ok && !mbar_wait_bounded(bar, phase)) {
+      waits_ok = false;  // stale data from here on; the status word says so
+      if (tg == 0) atomicOr(&I.st->status, kStatusTimeout);
+    }
+    phase ^= 1u;
+    const float* row = srow;
 
     uint32_t v[C];  // weight bits; w >= 0 orders like its bit pattern
 #pragma unroll
     for (int i = 0; i < C; i += 4) {
-      uint4 t = make_uint4(0u, 0u, 0u, 0u);
-      if (base + i < ld) t = __ldg(reinterpret_cast<const uint4*>(row + base + i));
+      // Chunk entries at or beyond ld hold stale data; their tabu bits are set.
+      const uint4 t = *reinterpret_cast<const uint4*>(row + base + i);
       v[i] = t.x;
       v[i + 1] = t.y;
       v[i + 2] = t.z;
@@ -193,7 +246,16 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       next = (int)cand;
     } else {
       const int sc = kRouletteBits - 1 - exponent_of_bits(mx);
-      const unsigned long long mine = chunk_sum<C>(v, sc);
+      float f1, f2;
+      quant_factors(sc, f1, f2);
+      if (f2 != 1.0f) {
+        // Largest unvisited weight below 2^-105 (rare): scale the chunk up
+        // first, exactly; quant_value() below applies f1 then f2, the same
+        // two exact products in the other order.
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] = __float_as_uint(__fmul_rn(__uint_as_float(v[i]), f2));
+      }
+      const unsigned long long mine = chunk_sum<C>(v, f1);
       const unsigned long long incl = warp_inclusive_scan(mine, lane);
       const unsigned long long wtot = shfl_u64(incl, 31);
       unsigned long long woff = 0, Q = wtot;
@@ -214,7 +276,7 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
         const unsigned long long t1 = T - woff;
         const int L = max(__ffs(__ballot_sync(FULL, incl > t1)) - 1, 0);
         const unsigned long long t2 = t1 - shfl_u64(incl - mine, L);
-        const int baseL = (wg * 32 + L) * C;
+        const int baseL = (wg * 32 + L) * C;  // within the staged row
         uint32_t visL[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) visL[w] = __shfl_sync(FULL, vis[w], L);
@@ -230,8 +292,7 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
           uint32_t w8 = 0u;
           if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u))
             w8 = __float_as_uint(row[baseL + li]);
-          qv[p] = sc <= 126 ? add_floor_scaled(0ull, w8, 150 - sc)
-                            : add_floor_scaled_tiny(0ull, w8, pow2f(127), pow2f(sc - 127));
+          qv[p] = quant_value(w8, f1, f2);
           ps += qv[p];
         }
         const unsigned long long incl2 = warp_inclusive_scan(ps, lane);
@@ -270,6 +331,7 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     }
     if (tg == 0) tour[s] = next;
     cur = next;
+    group_sync(bar_id, NT);
   }
   if (tg == 0) tour[n] = start;
   group_sync(bar_id, NT);
@@ -294,15 +356,18 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   if (tg == 0) I.lens[ant] = len;
 }
 
-// One CTA holds blockDim.x / (32 G) ant groups.
+// One CTA holds blockDim.x / (32 G) ant groups; dynamic shared memory holds
+// one StageLayout<C, G> per group.
 template <int C, int G>
 __global__ void __launch_bounds__(256) construct_kernel(Instance I) {
   __shared__ GroupSmem gs[kMaxGroupsPerCta];
+  extern __shared__ __align__(16) unsigned char stage[];
   const int grp = threadIdx.x / (32 * G);
   const int tg = threadIdx.x % (32 * G);
   const int ant = blockIdx.x * (blockDim.x / (32 * G)) + grp;
   if (ant >= I.m) return;
-  construct_ant<C, G>(I, ant, tg, &gs[grp], 1 + grp);
+  construct_ant<C, G>(I, ant, tg, &gs[grp], 1 + grp,
+                      reinterpret_cast<float*>(stage + grp * StageLayout<C, G>::kBytes));
 }
 
 // Batched form: group g of block b builds ant items[b*A + g].y of instance
@@ -318,7 +383,26 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
   if (idx >= count) return;
   const int2 it = items[idx];
   const Instance I = insts[it.x];
-  construct_ant<C, G>(I, it.y, tg, &gs[grp], 1 + grp);
+  extern __shared__ __align__(16) unsigned char stage[];
+  construct_ant<C, G>(I, it.y, tg, &gs[grp], 1 + grp,
+                      reinterpret_cast<float*>(stage + grp * StageLayout<C, G>::kBytes));
+}
+
+// Dynamic shared memory for A groups, with the opt-in above 48 KB set once.
+template <int C, int G, bool kItems>
+inline size_t construct_smem_setup(int A) {
+  const size_t bytes = (size_t)A * StageLayout<C, G>::kBytes;
+  static bool done = false;
+  if (!done) {
+    if (kItems)
+      cudaFuncSetAttribute(construct_items_kernel<C, G>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * StageLayout<C, G>::kBytes);
+    else
+      cudaFuncSetAttribute(construct_kernel<C, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           8 * StageLayout<C, G>::kBytes);
+    done = true;
+  }
+  return bytes;
 }
 
 }  // namespace aco

@@ -8,39 +8,56 @@ cudaError_t launch_construct_g1(const Instance& I, int C, int A, cudaStream_t st
   const int threads = 32 * 1 * A;
   const int grid = (I.m + A - 1) / A;
   switch (C) {
-    case 4:
-      construct_kernel<4, 1><<<grid, threads, 0, st>>>(I);
+    case 4: {
+      const size_t smem = construct_smem_setup<4, 1, false>(A);
+      construct_kernel<4, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 8:
-      construct_kernel<8, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 12: {
+      const size_t smem = construct_smem_setup<12, 1, false>(A);
+      construct_kernel<12, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 12:
-      construct_kernel<12, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 20: {
+      const size_t smem = construct_smem_setup<20, 1, false>(A);
+      construct_kernel<20, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 16:
-      construct_kernel<16, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 28: {
+      const size_t smem = construct_smem_setup<28, 1, false>(A);
+      construct_kernel<28, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 20:
-      construct_kernel<20, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 36: {
+      const size_t smem = construct_smem_setup<36, 1, false>(A);
+      construct_kernel<36, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 24:
-      construct_kernel<24, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 44: {
+      const size_t smem = construct_smem_setup<44, 1, false>(A);
+      construct_kernel<44, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 32:
-      construct_kernel<32, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 52: {
+      const size_t smem = construct_smem_setup<52, 1, false>(A);
+      construct_kernel<52, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 40:
-      construct_kernel<40, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 60: {
+      const size_t smem = construct_smem_setup<60, 1, false>(A);
+      construct_kernel<60, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 48:
-      construct_kernel<48, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 68: {
+      const size_t smem = construct_smem_setup<68, 1, false>(A);
+      construct_kernel<68, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 64:
-      construct_kernel<64, 1><<<grid, threads, 0, st>>>(I);
+    }
+    case 76: {
+      const size_t smem = construct_smem_setup<76, 1, false>(A);
+      construct_kernel<76, 1><<<grid, threads, smem, st>>>(I);
       break;
-    case 80:
-      construct_kernel<80, 1><<<grid, threads, 0, st>>>(I);
-      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }
@@ -53,39 +70,56 @@ cudaError_t launch_construct_items_g1(const Instance* insts, const int2* items, 
   const int threads = 32 * 1 * A;
   const int grid = (count + A - 1) / A;
   switch (C) {
-    case 4:
-      construct_items_kernel<4, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    case 4: {
+      const size_t smem = construct_smem_setup<4, 1, true>(A);
+      construct_items_kernel<4, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 8:
-      construct_items_kernel<8, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 12: {
+      const size_t smem = construct_smem_setup<12, 1, true>(A);
+      construct_items_kernel<12, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 12:
-      construct_items_kernel<12, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 20: {
+      const size_t smem = construct_smem_setup<20, 1, true>(A);
+      construct_items_kernel<20, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 16:
-      construct_items_kernel<16, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 28: {
+      const size_t smem = construct_smem_setup<28, 1, true>(A);
+      construct_items_kernel<28, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 20:
-      construct_items_kernel<20, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 36: {
+      const size_t smem = construct_smem_setup<36, 1, true>(A);
+      construct_items_kernel<36, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 24:
-      construct_items_kernel<24, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 44: {
+      const size_t smem = construct_smem_setup<44, 1, true>(A);
+      construct_items_kernel<44, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 32:
-      construct_items_kernel<32, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 52: {
+      const size_t smem = construct_smem_setup<52, 1, true>(A);
+      construct_items_kernel<52, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 40:
-      construct_items_kernel<40, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 60: {
+      const size_t smem = construct_smem_setup<60, 1, true>(A);
+      construct_items_kernel<60, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 48:
-      construct_items_kernel<48, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 68: {
+      const size_t smem = construct_smem_setup<68, 1, true>(A);
+      construct_items_kernel<68, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 64:
-      construct_items_kernel<64, 1><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 76: {
+      const size_t smem = construct_smem_setup<76, 1, true>(A);
+      construct_items_kernel<76, 1><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 80:
-      construct_items_kernel<80, 1><<<grid, threads, 0, st>>>(insts, items, count);
-      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }

@@ -8,33 +8,46 @@ cudaError_t launch_construct_g2(const Instance& I, int C, int A, cudaStream_t st
   const int threads = 32 * 2 * A;
   const int grid = (I.m + A - 1) / A;
   switch (C) {
-    case 8:
-      construct_kernel<8, 2><<<grid, threads, 0, st>>>(I);
+    case 12: {
+      const size_t smem = construct_smem_setup<12, 2, false>(A);
+      construct_kernel<12, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 12:
-      construct_kernel<12, 2><<<grid, threads, 0, st>>>(I);
+    }
+    case 20: {
+      const size_t smem = construct_smem_setup<20, 2, false>(A);
+      construct_kernel<20, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 16:
-      construct_kernel<16, 2><<<grid, threads, 0, st>>>(I);
+    }
+    case 28: {
+      const size_t smem = construct_smem_setup<28, 2, false>(A);
+      construct_kernel<28, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 20:
-      construct_kernel<20, 2><<<grid, threads, 0, st>>>(I);
+    }
+    case 36: {
+      const size_t smem = construct_smem_setup<36, 2, false>(A);
+      construct_kernel<36, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 24:
-      construct_kernel<24, 2><<<grid, threads, 0, st>>>(I);
+    }
+    case 44: {
+      const size_t smem = construct_smem_setup<44, 2, false>(A);
+      construct_kernel<44, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 32:
-      construct_kernel<32, 2><<<grid, threads, 0, st>>>(I);
+    }
+    case 52: {
+      const size_t smem = construct_smem_setup<52, 2, false>(A);
+      construct_kernel<52, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 40:
-      construct_kernel<40, 2><<<grid, threads, 0, st>>>(I);
+    }
+    case 60: {
+      const size_t smem = construct_smem_setup<60, 2, false>(A);
+      construct_kernel<60, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 48:
-      construct_kernel<48, 2><<<grid, threads, 0, st>>>(I);
+    }
+    case 68: {
+      const size_t smem = construct_smem_setup<68, 2, false>(A);
+      construct_kernel<68, 2><<<grid, threads, smem, st>>>(I);
       break;
-    case 64:
-      construct_kernel<64, 2><<<grid, threads, 0, st>>>(I);
-      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }
@@ -47,33 +60,46 @@ cudaError_t launch_construct_items_g2(const Instance* insts, const int2* items, 
   const int threads = 32 * 2 * A;
   const int grid = (count + A - 1) / A;
   switch (C) {
-    case 8:
-      construct_items_kernel<8, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    case 12: {
+      const size_t smem = construct_smem_setup<12, 2, true>(A);
+      construct_items_kernel<12, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 12:
-      construct_items_kernel<12, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 20: {
+      const size_t smem = construct_smem_setup<20, 2, true>(A);
+      construct_items_kernel<20, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 16:
-      construct_items_kernel<16, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 28: {
+      const size_t smem = construct_smem_setup<28, 2, true>(A);
+      construct_items_kernel<28, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 20:
-      construct_items_kernel<20, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 36: {
+      const size_t smem = construct_smem_setup<36, 2, true>(A);
+      construct_items_kernel<36, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 24:
-      construct_items_kernel<24, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 44: {
+      const size_t smem = construct_smem_setup<44, 2, true>(A);
+      construct_items_kernel<44, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 32:
-      construct_items_kernel<32, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 52: {
+      const size_t smem = construct_smem_setup<52, 2, true>(A);
+      construct_items_kernel<52, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 40:
-      construct_items_kernel<40, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 60: {
+      const size_t smem = construct_smem_setup<60, 2, true>(A);
+      construct_items_kernel<60, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 48:
-      construct_items_kernel<48, 2><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 68: {
+      const size_t smem = construct_smem_setup<68, 2, true>(A);
+      construct_items_kernel<68, 2><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 64:
-      construct_items_kernel<64, 2><<<grid, threads, 0, st>>>(insts, items, count);
-      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }

@@ -8,27 +8,31 @@ cudaError_t launch_construct_g4(const Instance& I, int C, int A, cudaStream_t st
   const int threads = 32 * 4 * A;
   const int grid = (I.m + A - 1) / A;
   switch (C) {
-    case 4:
-      construct_kernel<4, 4><<<grid, threads, 0, st>>>(I);
+    case 4: {
+      const size_t smem = construct_smem_setup<4, 4, false>(A);
+      construct_kernel<4, 4><<<grid, threads, smem, st>>>(I);
       break;
-    case 8:
-      construct_kernel<8, 4><<<grid, threads, 0, st>>>(I);
+    }
+    case 12: {
+      const size_t smem = construct_smem_setup<12, 4, false>(A);
+      construct_kernel<12, 4><<<grid, threads, smem, st>>>(I);
       break;
-    case 12:
-      construct_kernel<12, 4><<<grid, threads, 0, st>>>(I);
+    }
+    case 20: {
+      const size_t smem = construct_smem_setup<20, 4, false>(A);
+      construct_kernel<20, 4><<<grid, threads, smem, st>>>(I);
       break;
-    case 16:
-      construct_kernel<16, 4><<<grid, threads, 0, st>>>(I);
+    }
+    case 28: {
+      const size_t smem = construct_smem_setup<28, 4, false>(A);
+      construct_kernel<28, 4><<<grid, threads, smem, st>>>(I);
       break;
-    case 20:
-      construct_kernel<20, 4><<<grid, threads, 0, st>>>(I);
+    }
+    case 36: {
+      const size_t smem = construct_smem_setup<36, 4, false>(A);
+      construct_kernel<36, 4><<<grid, threads, smem, st>>>(I);
       break;
-    case 24:
-      construct_kernel<24, 4><<<grid, threads, 0, st>>>(I);
-      break;
-    case 32:
-      construct_kernel<32, 4><<<grid, threads, 0, st>>>(I);
-      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }
@@ -41,27 +45,31 @@ cudaError_t launch_construct_items_g4(const Instance* insts, const int2* items, 
   const int threads = 32 * 4 * A;
   const int grid = (count + A - 1) / A;
   switch (C) {
-    case 4:
-      construct_items_kernel<4, 4><<<grid, threads, 0, st>>>(insts, items, count);
+    case 4: {
+      const size_t smem = construct_smem_setup<4, 4, true>(A);
+      construct_items_kernel<4, 4><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 8:
-      construct_items_kernel<8, 4><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 12: {
+      const size_t smem = construct_smem_setup<12, 4, true>(A);
+      construct_items_kernel<12, 4><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 12:
-      construct_items_kernel<12, 4><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 20: {
+      const size_t smem = construct_smem_setup<20, 4, true>(A);
+      construct_items_kernel<20, 4><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 16:
-      construct_items_kernel<16, 4><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 28: {
+      const size_t smem = construct_smem_setup<28, 4, true>(A);
+      construct_items_kernel<28, 4><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 20:
-      construct_items_kernel<20, 4><<<grid, threads, 0, st>>>(insts, items, count);
+    }
+    case 36: {
+      const size_t smem = construct_smem_setup<36, 4, true>(A);
+      construct_items_kernel<36, 4><<<grid, threads, smem, st>>>(insts, items, count);
       break;
-    case 24:
-      construct_items_kernel<24, 4><<<grid, threads, 0, st>>>(insts, items, count);
-      break;
-    case 32:
-      construct_items_kernel<32, 4><<<grid, threads, 0, st>>>(insts, items, count);
-      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }
