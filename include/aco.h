@@ -293,6 +293,48 @@ int aco_batch_iterate(aco_batch b, int32_t iterations);
 int aco_batch_best(aco_batch b, int32_t idx, int32_t *tour, int64_t *len);
 int aco_batch_destroy(aco_batch b);
 
+/* ======================================================================== *
+ * Allocation-free pheromone update.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: code running while someone else is
+ * capturing a CUDA graph, runtimes without a device allocator, and hosts
+ * that reserve all device memory up front.  It performs the same update as
+ * aco_update_pheromone with ACO_DEPOSIT_ATOMIC_U64 (same results bit for
+ * bit), but on arrays the caller owns and with its scratch (a 64-bit
+ * accumulator of ACO_NOALLOC_MAX_N^2 entries plus ACO_NOALLOC_MAX_M per-ant
+ * deposits, about 8.4 MB) in one static device array that the library
+ * reserves on every GPU that loads it, until the process exits.
+ * ======================================================================== */
+#define ACO_NOALLOC_MAX_N 1024
+#define ACO_NOALLOC_MAX_M 4096
+
+/*
+ * aco_update_pheromone_noalloc - evaporation (Eq. 2), deposit (Eqs. 3-4)
+ * and choice_info, on device arrays, without allocating.
+ *   n, m    cities (3..ACO_NOALLOC_MAX_N) and ants (1..ACO_NOALLOC_MAX_M);
+ *           larger sizes are rejected with ACO_EINVAL.
+ *   tours   device, m rows of n+1 int32 cities (closed tours); entries
+ *           outside [0, n) are ignored.
+ *   lens    device, m int64 tour lengths C^k (>= 1).
+ *   heta    device, n*n float eta^beta, row-major.
+ *   tau     device, n*n float, updated in place.
+ *   choice  device, n*n float, written with tau'^alpha * eta^beta.
+ *   alpha, rho  as in aco_create.
+ *   stream  cudaStream_t as int64 (0 = the legacy default stream); the work
+ *           is enqueued there and the call returns without synchronising.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ * call on a device looks up the static array's device address with
+ * cudaGetSymbolAddress (the current device must be the one the pointers
+ * belong to); make that first call before any stream capture.  Every call
+ * shares the one array and each call clears what it uses first, so calls
+ * that overlap on the GPU (different streams, or different host threads on
+ * one device) race and corrupt each other's results: serialise them.
+ */
+int aco_update_pheromone_noalloc(int32_t n, int32_t m, const int32_t *tours, const int64_t *lens,
+                                 const float *heta, float *tau, float *choice, float alpha,
+                                 float rho, int64_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,8 @@ SIGNATURES = [
     ("aco_batch_iterate", C.c_int, [_vp, C.c_int32]),
     ("aco_batch_best", C.c_int, [_vp, C.c_int32, _vp, _vp]),
     ("aco_batch_destroy", C.c_int, [_vp]),
+    ("aco_update_pheromone_noalloc", C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp,
+                                               C.c_float, C.c_float, C.c_int64]),
 ]
 
 _lock = threading.Lock()
@@ -353,6 +355,19 @@ def aco_batch_best(b, idx: int, n: int):
 
 def aco_batch_destroy(b) -> None:
     _check(load().aco_batch_destroy(b), "aco_batch_destroy")
+
+
+ACO_NOALLOC_MAX_N = 1024
+ACO_NOALLOC_MAX_M = 4096
+
+
+def aco_update_pheromone_noalloc(n: int, m: int, tours_ptr: int, lens_ptr: int, heta_ptr: int,
+                                 tau_ptr: int, choice_ptr: int, alpha: float, rho: float,
+                                 stream: int = 0) -> None:
+    """Pheromone update on caller-owned device arrays (raw device pointers), no allocation."""
+    _check(load().aco_update_pheromone_noalloc(n, m, tours_ptr, lens_ptr, heta_ptr, tau_ptr,
+                                               choice_ptr, alpha, rho, stream),
+           "aco_update_pheromone_noalloc")
 
 
 class Colony:
