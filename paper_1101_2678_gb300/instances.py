@@ -21,18 +21,25 @@ from dataclasses import dataclass
 import numpy as np
 
 
-@dataclass(frozen=True)
 class Instance:
-    """One symmetric TSP instance: int64 coordinates and an int32 distance matrix."""
+    """One symmetric TSP instance: int64 coordinates; the int32 distance matrix
+    (symmetric, zero diagonal, >= 1 elsewhere) is built on first use."""
 
-    coords: np.ndarray  # (n, 2) int64
-    dist: np.ndarray  # (n, n) int32, symmetric, zero diagonal, >= 1 elsewhere
-    kind: str
-    seed: int
+    def __init__(self, coords: np.ndarray, kind: str, seed: int):
+        self.coords = coords  # (n, 2) int64
+        self.kind = kind
+        self.seed = seed
+        self._dist = None
+
+    @property
+    def dist(self) -> np.ndarray:
+        if self._dist is None:
+            self._dist = distance_matrix(self.coords)
+        return self._dist
 
     @property
     def n(self) -> int:
-        return int(self.dist.shape[0])
+        return int(self.coords.shape[0])
 
 
 def distance_matrix(coords: np.ndarray) -> np.ndarray:
@@ -64,7 +71,7 @@ def uniform_instance(n: int, side: int, seed: int) -> Instance:
     rng = np.random.Generator(np.random.PCG64(seed))
     draw = lambda k: rng.integers(0, side + 1, size=(k, 2), dtype=np.int64)
     coords = _dedupe(draw(n), draw)
-    return Instance(coords, distance_matrix(coords), "uniform", seed)
+    return Instance(coords, "uniform", seed)
 
 
 def clustered_instance(n: int, seed: int, clusters: int = 64, sigma: float = 300.0,
@@ -84,7 +91,7 @@ def clustered_instance(n: int, seed: int, clusters: int = 64, sigma: float = 300
         return np.clip(np.rint(pts), 0, side).astype(np.int64)
 
     coords = _dedupe(draw(n), draw)
-    return Instance(coords, distance_matrix(coords), "clustered", seed)
+    return Instance(coords, "clustered", seed)
 
 
 def log_uniform_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
