@@ -82,13 +82,21 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """Largest v over all ranks (the slowest rank's time sets the job's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, my_seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas: all ranks' units
+    divided by the slowest rank's time (every rank does the same work)."""
+    return units_per_rank * world / max_over_ranks(my_seconds, world)
 
 
 # ---------------------------------------------------------------------------
@@ -338,10 +346,9 @@ def run_ours(args, w, rank, world, local):
     best_tour, best_len = aco.aco_best_tour(h, n)
     col.close()
 
-    total_ms = max_over_ranks(sum(step_ms), world)
     steps = args.steps
-    ant_steps = m * (n - 1) * steps * world
-    value = ant_steps / (total_ms / 1e3)
+    value = replica_throughput(m * (n - 1) * steps, sum(step_ms) / 1e3, world)
+    total_ms = m * (n - 1) * steps * world / value * 1e3
     con_ms = phase_ms[aco.ACO_PHASE_CONSTRUCT] / steps
     upd_ms = (phase_ms[aco.ACO_PHASE_DEPOSIT] + phase_ms[aco.ACO_PHASE_UPDATE]) / steps
     best_ms = phase_ms[aco.ACO_PHASE_BEST] / steps

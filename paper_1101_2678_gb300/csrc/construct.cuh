@@ -9,9 +9,9 @@
 //   2. M = max over unvisited (REDUX on the float bit patterns, which order
 //      like the values for w >= 0), across warps through shared memory;
 //   3. q_j = floor(w_j * 2^(45-ilogb M)) split exactly into two 23-bit halves
-//      by FP32 round-toward-zero additions (FP32 pipe only; no float-to-int
-//      conversion and few integer ops), per-thread u64 sums, warp inclusive
-//      scan, group totals -> Q;
+//      by three round-toward-zero FP32 FMAs (FP32 pipe; no float-to-int
+//      conversion), per-thread u64 sums, warp inclusive scan, group totals
+//      -> Q;
 //   4. T = floor(r Q / 2^64) with r from Philox (one Philox call per lane per
 //      32 steps, broadcast by shuffle);
 //   5. the thread whose prefix range holds T is found by ballot; its chunk is
@@ -51,41 +51,50 @@ constexpr int kRouletteBits = 46;
 constexpr float kTwo23 = 8388608.0f;
 constexpr uint32_t kTwo23Bits = 0x4b000000u;
 
-// q = floor(w * 2^sc) < 2^46 as hi * 2^23 + lo, on the FP32 pipe only.
-// t = w * 2^(sc-23) < 2^23 is exact (a power-of-two scaling); adding 2^23
-// with round-toward-zero gives 2^23 + floor(t); t - floor(t) is exact
-// (Sterbenz); fma.rz(frac, 2^23, 2^23) gives 2^23 + floor(frac * 2^23).
-// The two results are floats in [2^23, 2^24) whose bit patterns are
-// 0x4b000000 + hi and 0x4b000000 + lo.  f2 != 1 only when 2^(sc-23) is not
-// a float (largest unvisited weight below 2^-105): both scalings are exact.
+// q = floor(w * 2^sc) < 2^46 as hi * 2^23 + lo, in three FP32 FMAs.
+// With t = w * f1 (f1 = 2^(sc-23), so t < 2^23):
+//   zh = fma.rz(w, f1, 2^23)           = 2^23 + floor(t)          (one rounding of w*f1 + 2^23)
+//   c  = fma(zh, -2^23, 2^46 + 2^23)   = 2^23 - floor(t) * 2^23   (exact: representable)
+//   zl = fma.rz(w, f1 * 2^23, c)       = 2^23 + floor(frac(t) * 2^23)
+// zh and zl are floats in [2^23, 2^24) whose bit patterns are 0x4b000000 +
+// hi and 0x4b000000 + lo.  Each rounding is of an exactly known value, so
+// both floors are exact for every w >= 0 (subnormal products included: the
+// fused multiply-add never rounds w * f1 on its own).
 struct QuantParts {
   uint32_t hi_bits, lo_bits;
 };
 
-__device__ __forceinline__ QuantParts quant_parts(uint32_t b, float f1, float f2) {
-  float t = __fmul_rn(__uint_as_float(b), f1);
-  if (f2 != 1.0f) t = __fmul_rn(t, f2);
-  const float zh = __fadd_rz(t, kTwo23);
-  const float hf = __fsub_rn(zh, kTwo23);
-  const float fr = __fsub_rn(t, hf);
-  const float zl = __fmaf_rz(fr, kTwo23, kTwo23);
+constexpr float kTwo46p23 = 70368752566272.0f;  // 2^46 + 2^23
+
+__device__ __forceinline__ QuantParts quant_parts(uint32_t b, float f1, float f1s) {
+  const float w = __uint_as_float(b);
+  const float zh = __fmaf_rz(w, f1, kTwo23);
+  const float c = __fmaf_rn(zh, -kTwo23, kTwo46p23);
+  const float zl = __fmaf_rz(w, f1s, c);
   return QuantParts{__float_as_uint(zh), __float_as_uint(zl)};
 }
 
-__device__ __forceinline__ unsigned long long quant_value(uint32_t b, float f1, float f2) {
-  const QuantParts q = quant_parts(b, f1, f2);
+// q of a weight that still needs the pre-scaling by f2 (see quant_factors).
+__device__ __forceinline__ unsigned long long quant_value(uint32_t b, float f1, float f1s,
+                                                          float f2) {
+  if (f2 != 1.0f) b = __float_as_uint(__fmul_rn(__uint_as_float(b), f2));
+  const QuantParts q = quant_parts(b, f1, f1s);
   return ((unsigned long long)(q.hi_bits - kTwo23Bits) << 23) + (q.lo_bits - kTwo23Bits);
 }
 
-// Scale factors 2^(sc-23) for the step: one float when it exists.
-__device__ __forceinline__ void quant_factors(int sc, float& f1, float& f2) {
+// Factors for the step: f1 = 2^(sc-23) and f1s = f1 * 2^23 must both be
+// normal floats, i.e. sc - 23 <= 104.  Beyond that (largest unvisited
+// weight below 2^-82) the weights are first scaled up exactly by f2.
+__device__ __forceinline__ void quant_factors(int sc, float& f1, float& f1s, float& f2) {
   const int e = sc - 23;
-  if (e <= 127) {
+  if (e <= 104) {
     f1 = pow2f(e);
+    f1s = pow2f(e + 23);
     f2 = 1.0f;
   } else {
-    f1 = pow2f(127);
-    f2 = pow2f(e - 127);
+    f1 = pow2f(104);
+    f1s = pow2f(127);
+    f2 = pow2f(e - 104);
   }
 }
 
@@ -94,12 +103,13 @@ __device__ __forceinline__ void quant_factors(int sc, float& f1, float& f2) {
 // and the C offsets of 0x4b000000 removed once; the true part sums are below
 // C * 2^23 <= 2^30, so the wrap-around is exact.
 template <int C>
-__device__ __forceinline__ unsigned long long chunk_sum(const uint32_t (&v)[C], float f1) {
+__device__ __forceinline__ unsigned long long chunk_sum(const uint32_t (&v)[C], float f1,
+                                                        float f1s) {
   uint32_t hi0 = 0, lo0 = 0, hi1 = 0, lo1 = 0;
 #pragma unroll
   for (int i = 0; i < C; i += 4) {
-    const QuantParts a = quant_parts(v[i], f1, 1.0f), b = quant_parts(v[i + 1], f1, 1.0f);
-    const QuantParts c = quant_parts(v[i + 2], f1, 1.0f), d = quant_parts(v[i + 3], f1, 1.0f);
+    const QuantParts a = quant_parts(v[i], f1, f1s), b = quant_parts(v[i + 1], f1, f1s);
+    const QuantParts c = quant_parts(v[i + 2], f1, f1s), d = quant_parts(v[i + 3], f1, f1s);
     hi0 += a.hi_bits + b.hi_bits;
     lo0 += a.lo_bits + b.lo_bits;
     hi1 += c.hi_bits + d.hi_bits;
@@ -108,6 +118,27 @@ __device__ __forceinline__ unsigned long long chunk_sum(const uint32_t (&v)[C], 
   const uint32_t off = (uint32_t)C * kTwo23Bits;
   const uint32_t hi = hi0 + hi1 - off, lo = lo0 + lo1 - off;
   return ((unsigned long long)hi << 23) + lo;
+}
+
+// Same sum, also keeping each group of four weights' hi/lo part sums (with
+// their 4 * 0x4b000000 offsets) for the in-lane search of the selected city.
+template <int C>
+__device__ __forceinline__ unsigned long long chunk_sum_groups(const uint32_t (&v)[C], float f1,
+                                                               float f1s, uint32_t (&ghi)[C / 4],
+                                                               uint32_t (&glo)[C / 4]) {
+  uint32_t hi = 0, lo = 0;
+#pragma unroll
+  for (int g = 0; g < C / 4; ++g) {
+    const QuantParts a = quant_parts(v[4 * g], f1, f1s), b = quant_parts(v[4 * g + 1], f1, f1s);
+    const QuantParts c = quant_parts(v[4 * g + 2], f1, f1s),
+                     d = quant_parts(v[4 * g + 3], f1, f1s);
+    ghi[g] = a.hi_bits + b.hi_bits + c.hi_bits + d.hi_bits;
+    glo[g] = a.lo_bits + b.lo_bits + c.lo_bits + d.lo_bits;
+    hi += ghi[g];
+    lo += glo[g];
+  }
+  const uint32_t off = (uint32_t)C * kTwo23Bits;
+  return ((unsigned long long)(hi - off) << 23) + (lo - off);
 }
 
 __device__ __forceinline__ unsigned long long warp_inclusive_scan(unsigned long long x, int lane) {
@@ -136,6 +167,11 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   static_assert(G == 1 || G == 2 || G == 4, "G must be 1, 2 or 4");
   constexpr int NW = (C + 31) / 32;  // tabu words per thread
   constexpr int P = (C + 31) / 32;   // cities per lane in the rescan
+  // The smallest chunk (4 cities) keeps its sums in registers and the
+  // selected lane finds the city alone; larger chunks are rescanned by the
+  // whole warp, which measured faster than a serial in-lane search.
+  constexpr bool kGroupPick = C <= 4;
+  constexpr int NG = kGroupPick ? C / 4 : 1;
   constexpr int NT = 32 * G;
   const int n = I.n, ld = I.ld;
   const int lane = tg & 31, wg = tg >> 5;
@@ -213,13 +249,13 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       v[i + 2] = t.z;
       v[i + 3] = t.w;
     }
-    uint32_t mx = 0;
+    uint32_t m4[4] = {0u, 0u, 0u, 0u};  // four independent max chains
 #pragma unroll
     for (int i = 0; i < C; ++i) {
       if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
-      mx = max(mx, v[i]);
+      m4[i & 3] = max(m4[i & 3], v[i]);
     }
-    mx = __reduce_max_sync(FULL, mx);
+    uint32_t mx = __reduce_max_sync(FULL, max(max(m4[0], m4[1]), max(m4[2], m4[3])));
     if (G > 1) {
       if (lane == 0) gs->wmax[wg] = mx;
       group_sync(bar_id, NT);
@@ -246,16 +282,20 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       next = (int)cand;
     } else {
       const int sc = kRouletteBits - 1 - exponent_of_bits(mx);
-      float f1, f2;
-      quant_factors(sc, f1, f2);
+      float f1, f1s, f2;
+      quant_factors(sc, f1, f1s, f2);
       if (f2 != 1.0f) {
-        // Largest unvisited weight below 2^-105 (rare): scale the chunk up
-        // first, exactly; quant_value() below applies f1 then f2, the same
-        // two exact products in the other order.
+        // Largest unvisited weight below 2^-82 (rare): scale the chunk up
+        // first, exactly (quant_value() does the same for reloaded weights).
 #pragma unroll
         for (int i = 0; i < C; ++i) v[i] = __float_as_uint(__fmul_rn(__uint_as_float(v[i]), f2));
       }
-      const unsigned long long mine = chunk_sum<C>(v, f1);
+      uint32_t ghi[NG], glo[NG];
+      unsigned long long mine;
+      if constexpr (kGroupPick)
+        mine = chunk_sum_groups<C>(v, f1, f1s, ghi, glo);
+      else
+        mine = chunk_sum<C>(v, f1, f1s);
       const unsigned long long incl = warp_inclusive_scan(mine, lane);
       const unsigned long long wtot = shfl_u64(incl, 31);
       unsigned long long woff = 0, Q = wtot;
@@ -277,6 +317,37 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
         const int L = max(__ffs(__ballot_sync(FULL, incl > t1)) - 1, 0);
         const unsigned long long t2 = t1 - shfl_u64(incl - mine, L);
         const int baseL = (wg * 32 + L) * C;  // within the staged row
+        if constexpr (kGroupPick) {
+          // Lane L walks its group sums, then the four cities of the group
+          // holding the target (all from registers).
+          int pick = 0;
+          if (lane == L) {
+            unsigned long long cum = 0;
+            bool found = false;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+              const unsigned long long gv =
+                  ((unsigned long long)(ghi[g] - 4u * kTwo23Bits) << 23) + (glo[g] - 4u * kTwo23Bits);
+              if (!found && cum + gv > t2) {
+                found = true;
+                unsigned long long c = cum + quant_value(v[4 * g], f1, f1s, 1.0f);
+                int e = 0;
+                if (c <= t2) {
+                  c += quant_value(v[4 * g + 1], f1, f1s, 1.0f);
+                  e = 1;
+                  if (c <= t2) {
+                    c += quant_value(v[4 * g + 2], f1, f1s, 1.0f);
+                    e = c <= t2 ? 3 : 2;
+                  }
+                }
+                pick = 4 * g + e;
+              }
+              cum += gv;
+            }
+          }
+          next = baseL + __shfl_sync(FULL, pick, L);
+          if (G > 1 && lane == 0) gs->next = next;
+        } else {
         uint32_t visL[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) visL[w] = __shfl_sync(FULL, vis[w], L);
@@ -292,7 +363,7 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
           uint32_t w8 = 0u;
           if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u))
             w8 = __float_as_uint(row[baseL + li]);
-          qv[p] = quant_value(w8, f1, f2);
+          qv[p] = quant_value(w8, f1, f1s, f2);
           ps += qv[p];
         }
         const unsigned long long incl2 = warp_inclusive_scan(ps, lane);
@@ -310,6 +381,7 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
         pick = max(__shfl_sync(FULL, pick, L2), 0);
         next = baseL + L2 * P + pick;
         if (G > 1 && lane == 0) gs->next = next;
+        }
       }
       if (G > 1) {
         group_sync(bar_id, NT);

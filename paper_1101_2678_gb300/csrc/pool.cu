@@ -123,6 +123,12 @@ struct aco_pool {
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
   bool unlimited = false;  // static batch: no iteration budget
+  // Construction classes run concurrently on these streams (fork/join events
+  // inside the captured step graph).
+  static constexpr int kClassStreams = 8;
+  cudaStream_t class_stream[kClassStreams] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kClassStreams] = {};
 };
 
 static void pool_drop_graph(aco_pool* p) {
@@ -239,10 +245,27 @@ static int pool_rebuild(aco_pool* p) {
 static int pool_enqueue_step(aco_pool* p) {
   cudaError_t e;
   int launches = 0;
-  for (const auto& c : p->classes) {
-    e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, p->stream);
+  // Fork: every tiling class gets its own stream so that the tail of one
+  // class overlaps the others; join before the best/update launches.
+  const int ncls = (int)p->classes.size();
+  const int nstreams = std::min(ncls, (int)aco_pool::kClassStreams);
+  if (nstreams > 1 && (e = cudaEventRecord(p->fork_ev, p->stream)) != cudaSuccess)
+    return cuda_fail(e, "pool fork");
+  for (int i = 0; i < nstreams && nstreams > 1; ++i)
+    if ((e = cudaStreamWaitEvent(p->class_stream[i], p->fork_ev, 0)) != cudaSuccess)
+      return cuda_fail(e, "pool fork wait");
+  for (int ci = 0; ci < ncls; ++ci) {
+    const auto& c = p->classes[(size_t)ci];
+    cudaStream_t st = nstreams > 1 ? p->class_stream[ci % nstreams] : p->stream;
+    e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, st);
     if (e != cudaSuccess) return cuda_fail(e, "pool construct");
     ++launches;
+  }
+  for (int i = 0; i < nstreams && nstreams > 1; ++i) {
+    if ((e = cudaEventRecord(p->join_ev[i], p->class_stream[i])) != cudaSuccess)
+      return cuda_fail(e, "pool join");
+    if ((e = cudaStreamWaitEvent(p->stream, p->join_ev[i], 0)) != cudaSuccess)
+      return cuda_fail(e, "pool join wait");
   }
   if ((e = launch_best_slots(p->d_inst, p->d_live, (int)p->h_live.size(), p->stream)) !=
       cudaSuccess)
@@ -391,6 +414,11 @@ int aco_pool_create(int32_t max_slots, uint64_t budget_bytes, aco_pool_handle* o
     if ((e = cudaMalloc(&p->arena, p->budget)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->d_inst, sizeof(Instance) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->d_live, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
+    if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess) break;
+    for (int i = 0; i < aco_pool::kClassStreams && e == cudaSuccess; ++i) {
+      e = cudaStreamCreateWithFlags(&p->class_stream[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming);
+    }
   } while (0);
   if (e != cudaSuccess) {
     const int rc = cuda_fail(e, "pool create");
@@ -414,6 +442,14 @@ int aco_pool_destroy(aco_pool_handle p) {
   if (p->d_live) cudaFree(p->d_live);
   if (p->d_items) cudaFree(p->d_items);
   if (p->d_rows) cudaFree(p->d_rows);
+  for (int i = 0; i < aco_pool::kClassStreams; ++i) {
+    if (p->class_stream[i]) {
+      cudaStreamSynchronize(p->class_stream[i]);
+      cudaStreamDestroy(p->class_stream[i]);
+    }
+    if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
+  }
+  if (p->fork_ev) cudaEventDestroy(p->fork_ev);
   if (p->stream) cudaStreamDestroy(p->stream);
   if (p->side) cudaStreamDestroy(p->side);
   delete p;

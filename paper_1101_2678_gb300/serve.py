@@ -51,11 +51,24 @@ class Outcome:
         return self.finished - self.arrival
 
 
+def step_work(r: Request) -> int:
+    """Candidate evaluations one iteration of request r costs (m ants x n steps x n cities)."""
+    return int(r.m) * r.n * r.n
+
+
 class Server:
-    def __init__(self, budget_bytes: int = 64 << 30, max_slots: int = 2048):
+    """Admission is bounded by the pool's HBM budget and by `max_step_work`,
+    the candidate evaluations one step may contain (the sum of step_work over
+    live requests): a larger batch raises throughput but every live request
+    waits for the whole step, so the bound trades throughput for latency.  A
+    request larger than the bound is admitted alone."""
+
+    def __init__(self, budget_bytes: int = 64 << 30, max_slots: int = 2048,
+                 max_step_work: int = 20_000_000_000):
         self.pool = aco.aco_pool_create(max_slots, budget_bytes)
         self.budget = budget_bytes
         self.max_slots = max_slots
+        self.max_step_work = max_step_work
 
     def close(self):
         if self.pool is not None:
@@ -81,6 +94,7 @@ class Server:
         order = np.argsort(np.asarray(arrivals), kind="stable")
         queue = collections.deque()
         live = {}  # slot -> (request index, admit time)
+        live_work = 0
         outcomes = []
         nxt = 0
         steps = 0
@@ -95,11 +109,15 @@ class Server:
                 nxt += 1
             while queue:
                 r = requests[queue[0]]
+                w = step_work(r)
+                if live and live_work + w > self.max_step_work:
+                    break
                 slot = aco.aco_pool_admit_coords(pool, r.coords, r.alpha, r.beta, r.rho, r.m,
                                                  r.seed, r.iterations)
                 if slot is None:
                     break
                 live[slot] = (queue.popleft(), time.perf_counter() - t0)
+                live_work += w
             if not live:
                 if nxt < total:
                     time.sleep(max(0.0, min(0.01, arrivals[order[nxt]] - now)))
@@ -109,6 +127,7 @@ class Server:
             steps += 1
             for slot in aco.aco_pool_finished(pool):
                 ri, tadm = live.pop(slot)
+                live_work -= step_work(requests[ri])
                 tour, length = aco.aco_pool_result(pool, slot, requests[ri].n)
                 tfin = time.perf_counter() - t0
                 outcomes.append(Outcome(ri, float(arrivals[ri]), tadm, tfin, length, tour))

@@ -141,3 +141,26 @@ def test_pool_rejects_bad_arguments(aco):
             aco.aco_pool_result(p, 0, 10)
     finally:
         aco.aco_pool_destroy(p)
+
+
+def test_server_results_equal_alone(aco):
+    # Continuous batching through serve.Server: requests of different sizes
+    # arrive together and in a small step-work budget (so admission is
+    # staggered); each result must be the one the request gets alone.
+    from paper_1101_2678_gb300 import serve
+    reqs, arrivals = [], []
+    for i, (n, kind) in enumerate([(90, "u"), (300, "c"), (48, "u"), (600, "c"), (150, "u")]):
+        inst = (I.uniform_instance(n, 1000, seed=70 + i) if kind == "u"
+                else I.clustered_instance(n, seed=70 + i, clusters=6, side=4000))
+        reqs.append(serve.Request(inst.coords, m=min(n, 128), iterations=3 + i, seed=800 + i))
+        arrivals.append(0.001 * i)
+    with serve.Server(budget_bytes=1 << 30, max_slots=8, max_step_work=600 * 600 * 128) as srv:
+        outs, st = srv.run(reqs, np.array(arrivals), realtime=False)
+    assert st["completed"] == len(reqs) and st["backlog"] == 0
+    for o in outs:
+        r = reqs[o.index]
+        d = I.distance_matrix(r.coords)
+        with aco.Colony(d, r.m, seed=r.seed) as c:
+            aco.aco_iterate(c.h, r.iterations)
+            tour, length = aco.aco_best_tour(c.h, r.n)
+        assert o.best_len == length and np.array_equal(o.best_tour, tour), o.index
