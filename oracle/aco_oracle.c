@@ -51,6 +51,15 @@
  *     powf(tau, alpha) * eta^beta otherwise.
  *  R7 the best-so-far tour is replaced only by a strictly shorter one; within
  *     an iteration the lowest ant index wins ties.
+ *  R8 (optional selection rule) the paper's data-parallel construction
+ *     (Section III-A): every unvisited city j draws u_j in (0, 1], its score
+ *     is fl(u_j * w_j), and the ant moves to the highest score (ties to the
+ *     lower index; if every score is 0, to the lowest unvisited city).  The
+ *     paper's "best among the tile winners" is read as the highest score of
+ *     the same product, so tiling does not change the choice.  u_j =
+ *     (floor(x / 2^8) + 1) * 2^-24 with x word (j mod 4) of Philox counter
+ *     (step, ant, iteration, 1 + floor(j / 4)).  This is not Eq. 1: for two
+ *     cities with w_1 >= w_2 it picks city 2 with probability w_2 / (2 w_1).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared -lm.
  * -ffp-contract=off matters: a fused multiply-add would change the rounding of
@@ -172,6 +181,37 @@ uint64_t orc_roulette_weights(int n, const float *w, const uint8_t *visited, uin
 }
 
 /* ------------------------------------------------------------------------- */
+/* The paper's data-parallel selection rule (reading R8).                     */
+/* ------------------------------------------------------------------------- */
+float orc_candidate_uniform(uint64_t seed, uint32_t step, uint32_t ant, uint32_t iteration,
+                            int j)
+{
+    uint32_t ctr[4] = {step, ant, iteration, 1u + (uint32_t)(j / 4)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    return (float)((x[j % 4] >> 8) + 1u) * (1.0f / 16777216.0f);
+}
+
+int orc_iroulette(int n, const float *w, const uint8_t *visited, uint64_t seed, uint32_t step,
+                  uint32_t ant, uint32_t iteration)
+{
+    int best = -1, first_unvisited = -1;
+    float best_score = 0.0f;
+    for (int j = 0; j < n; ++j) {
+        if (visited[j]) continue;
+        if (first_unvisited < 0) first_unvisited = j;
+        float u = orc_candidate_uniform(seed, step, ant, iteration, j);
+        float score = u * w[j];
+        if (score > best_score) {
+            best_score = score;
+            best = j;
+        }
+    }
+    return best >= 0 ? best : first_unvisited;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Setup: heuristic, nearest-neighbour tour, initial pheromone.              */
 /* ------------------------------------------------------------------------- */
 
@@ -247,8 +287,18 @@ void orc_choice(int n, const float *tau, const float *heta, float alpha, float *
 /* Tour construction (Section II): one ant.                                  */
 /* tour has n+1 entries, tour[n] = tour[0].  Returns C^k.                    */
 /* ------------------------------------------------------------------------- */
+/* rule 0: Eq. 1 (reading R2); rule 1: the paper's data-parallel rule (R8). */
+int64_t orc_construct_ant_rule(int n, const float *choice, const int32_t *d, uint64_t seed,
+                               uint32_t iteration, uint32_t ant, int rule, int32_t *tour);
+
 int64_t orc_construct_ant(int n, const float *choice, const int32_t *d, uint64_t seed,
                           uint32_t iteration, uint32_t ant, int32_t *tour)
+{
+    return orc_construct_ant_rule(n, choice, d, seed, iteration, ant, 0, tour);
+}
+
+int64_t orc_construct_ant_rule(int n, const float *choice, const int32_t *d, uint64_t seed,
+                               uint32_t iteration, uint32_t ant, int rule, int32_t *tour)
 {
     uint8_t *visited = (uint8_t *)calloc((size_t)n, 1);
     uint32_t x[4];
@@ -258,9 +308,15 @@ int64_t orc_construct_ant(int n, const float *choice, const int32_t *d, uint64_t
     visited[start] = 1;
     int cur = start;
     for (int s = 1; s < n; ++s) {
-        draw(seed, (uint32_t)s, ant, iteration, x);
-        uint64_t r = ((uint64_t)x[1] << 32) | (uint64_t)x[0];
-        int next = orc_roulette(n, choice + (size_t)cur * n, visited, r);
+        int next;
+        if (rule == 1) {
+            next = orc_iroulette(n, choice + (size_t)cur * n, visited, seed, (uint32_t)s, ant,
+                                 iteration);
+        } else {
+            draw(seed, (uint32_t)s, ant, iteration, x);
+            uint64_t r = ((uint64_t)x[1] << 32) | (uint64_t)x[0];
+            next = orc_roulette(n, choice + (size_t)cur * n, visited, r);
+        }
         tour[s] = next;
         visited[next] = 1;
         cur = next;
@@ -272,12 +328,18 @@ int64_t orc_construct_ant(int n, const float *choice, const int32_t *d, uint64_t
     return len;
 }
 
+void orc_construct_rule(int n, int m, const float *choice, const int32_t *d, uint64_t seed,
+                        uint32_t iteration, int rule, int32_t *tours, int64_t *lens)
+{
+    for (int k = 0; k < m; ++k)
+        lens[k] = orc_construct_ant_rule(n, choice, d, seed, iteration, (uint32_t)k, rule,
+                                         tours + (size_t)k * (n + 1));
+}
+
 void orc_construct(int n, int m, const float *choice, const int32_t *d, uint64_t seed,
                    uint32_t iteration, int32_t *tours, int64_t *lens)
 {
-    for (int k = 0; k < m; ++k)
-        lens[k] = orc_construct_ant(n, choice, d, seed, iteration, (uint32_t)k,
-                                    tours + (size_t)k * (n + 1));
+    orc_construct_rule(n, m, choice, d, seed, iteration, 0, tours, lens);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -345,9 +407,23 @@ void orc_update_fp64(int n, int m, const int32_t *tours, const int64_t *lens, do
 /*   last_lens[m], iter_best[iterations] (shortest C^k of each iteration).   */
 /* first_iteration lets a caller continue a run (the counter of R1).         */
 /* ------------------------------------------------------------------------- */
+int orc_run_rule(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+                 uint64_t seed, int iterations, int rule, int32_t *best_tour, int64_t *best_len,
+                 float *tau32_out, double *tau64_out, int32_t *last_tours, int64_t *last_lens,
+                 int64_t *iter_best);
+
 int orc_run(int n, const int32_t *d, float alpha, float beta, float rho, int m, uint64_t seed,
             int iterations, int32_t *best_tour, int64_t *best_len, float *tau32_out,
             double *tau64_out, int32_t *last_tours, int64_t *last_lens, int64_t *iter_best)
+{
+    return orc_run_rule(n, d, alpha, beta, rho, m, seed, iterations, 0, best_tour, best_len,
+                        tau32_out, tau64_out, last_tours, last_lens, iter_best);
+}
+
+int orc_run_rule(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+                 uint64_t seed, int iterations, int rule, int32_t *best_tour, int64_t *best_len,
+                 float *tau32_out, double *tau64_out, int32_t *last_tours, int64_t *last_lens,
+                 int64_t *iter_best)
 {
     size_t nn = (size_t)n * n;
     float *heta = (float *)malloc(nn * sizeof(float));
@@ -373,7 +449,7 @@ int orc_run(int n, const int32_t *d, float alpha, float beta, float rho, int m, 
     int64_t best = INT64_MAX;
     for (int it = 0; it < iterations; ++it) {
         orc_choice(n, tau, heta, alpha, choice);
-        orc_construct(n, m, choice, d, seed, (uint32_t)it, tours, lens);
+        orc_construct_rule(n, m, choice, d, seed, (uint32_t)it, rule, tours, lens);
         int kbest = 0;
         for (int k = 1; k < m; ++k)
             if (lens[k] < lens[kbest]) kbest = k;

@@ -78,6 +78,18 @@ def lib():
             L.orc_run.argtypes = [C.c_int, i32p, C.c_float, C.c_float, C.c_float, C.c_int,
                                   C.c_uint64, C.c_int, vp, vp, vp, vp, vp, vp, vp]
             L.orc_run.restype = C.c_int
+            L.orc_candidate_uniform.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                                C.c_int]
+            L.orc_candidate_uniform.restype = C.c_float
+            L.orc_iroulette.argtypes = [C.c_int, f32p, u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                        C.c_uint32]
+            L.orc_iroulette.restype = C.c_int
+            L.orc_construct_rule.argtypes = [C.c_int, C.c_int, f32p, i32p, C.c_uint64, C.c_uint32,
+                                             C.c_int, i32p, i64p]
+            L.orc_construct_rule.restype = None
+            L.orc_run_rule.argtypes = [C.c_int, i32p, C.c_float, C.c_float, C.c_float, C.c_int,
+                                       C.c_uint64, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_run_rule.restype = C.c_int
             L.orc_brute_force.argtypes = [C.c_int, i32p, i32p]
             L.orc_brute_force.restype = C.c_int64
             _lib = L
@@ -146,14 +158,25 @@ def construct_ant(choice_, dist, seed: int, iteration: int, ant: int):
     return tour, int(length)
 
 
-def construct(choice_, dist, m: int, seed: int, iteration: int):
+def construct(choice_, dist, m: int, seed: int, iteration: int, rule: int = 0):
+    """rule 0: Eq. 1 by the integer roulette; rule 1: the paper's data-parallel rule."""
     ch = np.ascontiguousarray(choice_, np.float32)
     d = _i32(dist)
     n = d.shape[0]
     tours = np.zeros((m, n + 1), np.int32)
     lens = np.zeros(m, np.int64)
-    lib().orc_construct(n, m, ch, d, C.c_uint64(seed), iteration, tours, lens)
+    lib().orc_construct_rule(n, m, ch, d, C.c_uint64(seed), iteration, rule, tours, lens)
     return tours, lens
+
+
+def candidate_uniform(seed: int, step: int, ant: int, iteration: int, j: int) -> float:
+    return float(np.float32(lib().orc_candidate_uniform(C.c_uint64(seed), step, ant, iteration, j)))
+
+
+def iroulette(w, visited, seed: int, step: int, ant: int, iteration: int) -> int:
+    w = np.ascontiguousarray(w, np.float32)
+    v = np.ascontiguousarray(visited, np.uint8)
+    return int(lib().orc_iroulette(len(w), w, v, C.c_uint64(seed), step, ant, iteration))
 
 
 def deposit_scale(lens) -> int:
@@ -177,8 +200,11 @@ def update_fp64(tau, tours, lens, rho: float) -> np.ndarray:
     return tau
 
 
-def run(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.5) -> dict:
-    """A whole Ant System run in mirror mode, with the fp64 pheromone carried alongside."""
+def run(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.5,
+        rule: int = 0) -> dict:
+    """A whole Ant System run in mirror mode, with the fp64 pheromone carried alongside.
+
+    rule 0 selects by Eq. 1, rule 1 by the paper's data-parallel rule."""
     d = _i32(dist)
     n = d.shape[0]
     best_tour = np.zeros(n + 1, np.int32)
@@ -188,8 +214,9 @@ def run(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.5) 
     tours = np.zeros((m, n + 1), np.int32)
     lens = np.zeros(m, np.int64)
     iter_best = np.zeros(max(iterations, 1), np.int64)
-    rc = lib().orc_run(n, d, float(alpha), float(beta), float(rho), int(m), C.c_uint64(seed),
-                       int(iterations), best_tour.ctypes.data, best_len.ctypes.data,
+    rc = lib().orc_run_rule(n, d, float(alpha), float(beta), float(rho), int(m),
+                       C.c_uint64(seed), int(iterations), int(rule), best_tour.ctypes.data,
+                       best_len.ctypes.data,
                        tau32.ctypes.data, tau64.ctypes.data, tours.ctypes.data,
                        lens.ctypes.data, iter_best.ctypes.data)
     if rc != 0:

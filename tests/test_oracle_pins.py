@@ -338,3 +338,68 @@ def test_run_fp32_mirror_tracks_fp64(orc):
     assert res["best_len"] == res["iter_best"].min()
     again = orc.run(w["inst"].dist, w["m"], 100, w["seed"])
     assert np.array_equal(again["tau32"], res["tau32"]) and again["best_len"] == res["best_len"]
+
+
+# --------------------------------------------------------------------------
+# The paper's data-parallel selection rule (Section III-A; reading R8)
+# --------------------------------------------------------------------------
+
+def _iroulette_freqs(orc, w, vis, draws):
+    counts = np.zeros(len(w), np.int64)
+    for i in range(draws):
+        counts[orc.iroulette(w, vis, 17, 1 + (i % 997), i // 997, 3)] += 1
+    return counts
+
+
+def test_candidate_uniforms_lie_in_unit_interval_and_are_uniform(orc):
+    from scipy.stats import kstest
+    u = np.array([orc.candidate_uniform(5, s, 3, 0, j) for s in range(50) for j in range(40)])
+    assert u.min() > 0 and u.max() <= 1
+    assert np.all(u * 2**24 == np.rint(u * 2**24))
+    assert kstest(u, "uniform").pvalue > 0.01
+
+
+def test_iroulette_two_candidates_closed_form(orc):
+    # w1 >= w2: city 2 wins u2 w2 > u1 w1 with probability w2 / (2 w1).
+    from scipy.stats import binomtest
+    w = np.array([0.0, 3.0, 1.0], np.float32)
+    vis = np.array([1, 0, 0], np.uint8)
+    counts = _iroulette_freqs(orc, w, vis, 40_000)
+    assert counts[0] == 0
+    assert binomtest(int(counts[2]), int(counts.sum()), 1.0 / 6.0).pvalue > 0.01
+
+
+def test_iroulette_chi_squared_against_integral_closed_form(orc):
+    # P(j) = int_0^1 prod_{l != j} min(1, x w_j / w_l) dx for independent
+    # uniforms u_l; checked on four candidates and one visited city.
+    from scipy.integrate import quad
+    from scipy.stats import chisquare
+    w = np.array([1.0, 2.0, 0.5, 4.0, 3.0], np.float32)
+    vis = np.array([0, 0, 0, 0, 1], np.uint8)
+    cand = [j for j in range(5) if not vis[j]]
+    p = []
+    for j in cand:
+        f = lambda x, j=j: np.prod([min(1.0, x * w[j] / w[l]) for l in cand if l != j])
+        p.append(quad(f, 0, 1, limit=200)[0])
+    p = np.array(p)
+    assert abs(p.sum() - 1) < 1e-9
+    counts = _iroulette_freqs(orc, w, vis, 60_000)
+    assert counts[4] == 0
+    assert chisquare(counts[cand], p * counts.sum()).pvalue > 0.01
+
+
+def test_iroulette_degenerate_rows_and_tours(orc):
+    w = np.zeros(6, np.float32)
+    vis = np.array([1, 0, 1, 0, 0, 0], np.uint8)
+    assert orc.iroulette(w, vis, 1, 1, 0, 0) == 1
+    inst = I.uniform_instance(23, 1000, seed=3)
+    h = orc.heta(inst.dist, 2.0)
+    ch = orc.choice(np.where(np.eye(23) > 0, 0, 0.3).astype(np.float32), h, 1.0)
+    tours, lens = orc.construct(ch, inst.dist, 11, seed=2, iteration=1, rule=1)
+    for k in range(11):
+        t = tours[k]
+        assert sorted(t[:-1].tolist()) == list(range(23)) and t[-1] == t[0]
+        assert lens[k] == int(inst.dist[t[:-1], t[1:]].astype(np.int64).sum())
+    # starts are shared with Eq. 1 (same counter), later moves differ in general
+    t0, _ = orc.construct(ch, inst.dist, 11, seed=2, iteration=1, rule=0)
+    assert np.array_equal(t0[:, 0], tours[:, 0])
