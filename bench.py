@@ -53,7 +53,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--warps-per-ant", type=int, default=0, help="0 = library default")
     ap.add_argument("--ants-per-cta", type=int, default=0, help="0 = library default")
+    ap.add_argument("--lanes-per-ant", type=int, default=0, help="0 = library default (32)")
+    ap.add_argument("--selection", default="eq1", choices=["eq1", "data-parallel"],
+                    help="eq1: Eq. 1 (default); data-parallel: the paper's product-argmax kernel")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-iterations", type=int, default=0,
+                    help="0 = the workload's 100; fewer for profiling runs")
+    ap.add_argument("--no-loop-baseline", action="store_true",
+                    help="skip the per-instance loop (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the Poisson arrival window for --workload served")
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -312,10 +319,15 @@ def run_ours(args, w, rank, world, local):
     aco.aco_set_option(h, aco.ACO_OPT_PROFILE, 1)
     if args.warps_per_ant:
         aco.aco_set_option(h, aco.ACO_OPT_WARPS_PER_ANT, args.warps_per_ant)
+    if args.selection == "data-parallel":
+        aco.aco_set_option(h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
+    if args.lanes_per_ant:
+        aco.aco_set_option(h, aco.ACO_OPT_LANES_PER_ANT, args.lanes_per_ant)
     if args.ants_per_cta:
         aco.aco_set_option(h, aco.ACO_OPT_ANTS_PER_CTA, args.ants_per_cta)
     tiling = (aco.aco_get_option(h, aco.ACO_OPT_WARPS_PER_ANT),
-              aco.aco_get_option(h, aco.ACO_OPT_ANTS_PER_CTA))
+              aco.aco_get_option(h, aco.ACO_OPT_ANTS_PER_CTA),
+              aco.aco_get_option(h, aco.ACO_OPT_LANES_PER_ANT))
     launches = aco.aco_kernel_launches_per_iteration(h)
 
     with torch.cuda.stream(stream):
@@ -379,6 +391,7 @@ def run_ours(args, w, rank, world, local):
         "config": {"workload": w["name"], "n": n, "m": m, "alpha": w["alpha"],
                    "beta": w["beta"], "rho": w["rho"], "deposit": args.deposit,
                    "warps_per_ant": tiling[0], "ants_per_cta": tiling[1],
+                   "lanes_per_ant": tiling[2], "selection": args.selection,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed between steps (256 MB write)"},
         "construct_ant_steps_per_s": m * (n - 1) / (con_ms / 1e3),
@@ -447,6 +460,8 @@ def run_batched(args, rank, world, local):
     aco.load()
     w = instances.workload_batched(args.batch_count)
     insts, ms, seeds, iters = w["insts"], w["ms"], w["seeds"], w["iterations"]
+    if args.batch_iterations:
+        iters = args.batch_iterations
     dists = [x.dist for x in insts]
     # warm-up (module load, graph code paths)
     b = aco.aco_batch_create(dists[:4], ms[:4], seeds[:4])
@@ -470,7 +485,7 @@ def run_batched(args, rank, world, local):
     # per-instance loop
     t_loop = 0.0
     best_loop = []
-    for i, x in enumerate(insts):
+    for i, x in enumerate([] if args.no_loop_baseline else insts):
         c = aco.Colony(x.dist, ms[i], seed=seeds[i])
         aco.aco_synchronize(c.h)
         t0 = time.perf_counter()
@@ -491,8 +506,8 @@ def run_batched(args, rank, world, local):
         "config": {"workload": w["name"], "instances": len(insts), "n_min": min(x.n for x in insts),
                    "n_max": max(x.n for x in insts), "iterations": iters,
                    "l2": "not flushed (one continuous 100-step run)"},
-        "per_instance_loop_solves_per_s": len(insts) / t_loop,
-        "speedup_vs_loop": t_loop / t_batch,
+        "per_instance_loop_solves_per_s": len(insts) / t_loop if t_loop else None,
+        "speedup_vs_loop": t_loop / t_batch if t_loop else None,
         "identical_best_lengths": best_batch == best_loop,
         "ant_steps_per_s": ant_steps / t_batch,
         "gpu_launches": launches * iters, "clocks": clk,

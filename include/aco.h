@@ -75,7 +75,24 @@ extern "C" {
 #define ACO_OPT_USE_GRAPH 3    /* 1 (default): aco_iterate replays a CUDA graph */
 #define ACO_OPT_PROFILE 4      /* 1: record CUDA events around every kernel     */
 #define ACO_OPT_WARPS_PER_ANT 5 /* 0 (default) = automatic, else 1, 2 or 4      */
-#define ACO_OPT_ANTS_PER_CTA 6 /* 0 (default) = automatic, else 1..8            */
+#define ACO_OPT_ANTS_PER_CTA 6 /* 0 (default) = automatic, else 1..32; at most 8
+                                  warps per CTA                                */
+#define ACO_OPT_LANES_PER_ANT 7 /* 0 (default) = 32; 8 or 16: 32/H ants share a
+                                  warp (one warp per ant group)                */
+#define ACO_OPT_SELECTION 8    /* ACO_SELECT_* below; default ACO_SELECT_EQ1     */
+
+#define ACO_SELECT_EQ1 0       /* Eq. 1 (random proportional rule), exact      */
+#define ACO_SELECT_DATA_PARALLEL 1 /* the paper's data-parallel kernel (Section
+                                  III-A, Fig. 1): every unvisited city j draws
+                                  u_j in (0,1] (Philox counter (step, ant,
+                                  iteration, 1 + j/4), word j mod 4, u_j =
+                                  (floor(x/2^8) + 1) 2^-24), scores fl(u_j w_j),
+                                  and the highest score wins (ties to the lower
+                                  index; all scores 0: lowest unvisited city).
+                                  Not Eq. 1: for two cities with w1 >= w2 it
+                                  picks city 2 with probability w2 / (2 w1).
+                                  Whole warps per ant only (lanes per ant 32,
+                                  warps per ant 1 or 2).                       */
 
 #define ACO_DEPOSIT_GATHER 0   /* atomic-free: edges bucketed per city by the
                                   construction kernel, one warp reduces a row  */

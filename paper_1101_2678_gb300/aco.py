@@ -31,6 +31,10 @@ ACO_OPT_USE_GRAPH = 3
 ACO_OPT_PROFILE = 4
 ACO_OPT_WARPS_PER_ANT = 5
 ACO_OPT_ANTS_PER_CTA = 6
+ACO_OPT_LANES_PER_ANT = 7
+ACO_OPT_SELECTION = 8
+ACO_SELECT_EQ1 = 0
+ACO_SELECT_DATA_PARALLEL = 1
 
 ACO_DEPOSIT_GATHER = 0
 ACO_DEPOSIT_ATOMIC_U64 = 1

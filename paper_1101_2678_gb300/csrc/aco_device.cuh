@@ -30,6 +30,8 @@ struct Instance {
   int ldt;   // tour row stride (>= n + 1, multiple of 4)
   int ldm;   // nbr row stride (>= m, multiple of 32)
   float alpha, beta, rho;
+  int rule;                     // 0: Eq. 1 (integer roulette); 1: product of a uniform and the
+                                // weight, highest wins (the paper's data-parallel kernel)
   unsigned long long seed;
   const int32_t* dist;          // [n][ld]
   float* heta;                  // [n][ld]  eta^beta
@@ -74,6 +76,13 @@ __device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint3
     c3 = lo0;
   }
   return Philox4{c0, c1, c2, c3};
+}
+
+// Uniform in (0, 1] of candidate j at one construction step:
+// (floor(x / 2^8) + 1) * 2^-24 with x word (j mod 4) of Philox counter
+// (step, ant, iteration, 1 + j / 4); this returns all four words' uniforms.
+__device__ __forceinline__ float candidate_uniform_of(uint32_t x) {
+  return __fmaf_rn(__uint2float_rn(x >> 8), 5.9604644775390625e-08f, 5.9604644775390625e-08f);
 }
 
 // The draw of one construction step: counter (step, ant, iteration, 0).

@@ -36,58 +36,91 @@ int cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // Cities per thread: multiples of 4 with C/4 odd (conflict-free chunk reads
 // from the staged row).
-static const int kCg1[] = {4, 12, 20, 28, 36, 44, 52, 60, 68, 76};
-static const int kCg2[] = {12, 20, 28, 36, 44, 52, 60, 68};
-static const int kCg4[] = {4, 12, 20, 28, 36};
+static const int kC1[] = {4, 12, 20, 28, 36, 44, 52, 60, 68, 76};
+static const int kC2[] = {12, 20, 28, 36, 44, 52, 60, 68};
+static const int kC4[] = {4, 12, 20, 28, 36};
 
-bool construct_supported(int C, int G) {
-  const int* set = G == 1 ? kCg1 : G == 2 ? kCg2 : G == 4 ? kCg4 : nullptr;
-  const int cnt = G == 1 ? 10 : G == 2 ? 8 : G == 4 ? 5 : 0;
+static const int* c_set(int G, int H, int* cnt) {
+  if (G == 1 && (H == 8 || H == 16 || H == 32)) {
+    *cnt = 10;
+    return kC1;
+  }
+  if (H == 32 && G == 2) {
+    *cnt = 8;
+    return kC2;
+  }
+  if (H == 32 && G == 4) {
+    *cnt = 5;
+    return kC4;
+  }
+  *cnt = 0;
+  return nullptr;
+}
+
+bool construct_supported(int C, int G, int H) {
+  int cnt = 0;
+  const int* set = c_set(G, H, &cnt);
   for (int i = 0; i < cnt; ++i)
-    if (set && set[i] == C) return true;
+    if (set[i] == C) return true;
   return false;
 }
 
-ConstructTiling construct_tiling(int n, int G, int A) {
-  const int* set = G == 1 ? kCg1 : G == 2 ? kCg2 : G == 4 ? kCg4 : nullptr;
-  const int cnt = G == 1 ? 10 : G == 2 ? 8 : G == 4 ? 5 : 0;
+int ants_per_cta(ConstructTiling t) { return t.H == 32 ? t.W / t.G : t.W * (32 / t.H); }
+
+ConstructTiling construct_tiling(int n, int G, int H, int ants) {
+  int cnt = 0;
+  const int* set = c_set(G, H, &cnt);
+  const int W = H == 32 ? G * ants : (ants * H + 31) / 32;
   for (int i = 0; i < cnt; ++i)
-    if (32 * G * set[i] >= n) return ConstructTiling{set[i], G, A};
-  return ConstructTiling{0, G, A};
+    if (H * G * set[i] >= n) return ConstructTiling{set[i], G, H, W};
+  return ConstructTiling{0, G, H, W};
 }
 
 ConstructTiling default_construct_tiling(int n) {
-  if (n <= 32 * 76) return construct_tiling(n, 1, 4);
-  return construct_tiling(n, 2, 4);
+  if (n <= 32 * 76) return construct_tiling(n, 1, 32, 4);
+  return construct_tiling(n, 2, 32, 4);
+}
+
+// Warp instructions per ant step: about 7.25 per city slot plus a fixed
+// per-step part that grows with the scan depth, shared by the 32/H ants of a
+// warp.
+ConstructTiling batched_construct_tiling(int n) {
+  ConstructTiling best = default_construct_tiling(n);
+  double best_cost = 1e30;
+  const int hs[] = {8, 16, 32};
+  for (int H : hs) {
+    const ConstructTiling t = construct_tiling(n, 1, H, H == 32 ? 4 : 4 * (32 / H));
+    if (t.C == 0) continue;
+    const double lg = H == 8 ? 3 : H == 16 ? 4 : 5;
+    const double cost = (7.25 * t.C + 110.0 + 20.0 * lg) * H / 32.0;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = t;
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_construct(const Instance& I, ConstructTiling t, cudaStream_t st) {
-  if (t.G * t.A > 8) return cudaErrorInvalidValue;
-  switch (t.G) {
-    case 1:
-      return launch_construct_g1(I, t.C, t.A, st);
-    case 2:
-      return launch_construct_g2(I, t.C, t.A, st);
-    case 4:
-      return launch_construct_g4(I, t.C, t.A, st);
-    default:
-      return cudaErrorInvalidValue;
-  }
+  if (t.W < 1 || t.W > 8) return cudaErrorInvalidValue;
+  if (I.rule == 1) return launch_construct_rule1(I, t, st);
+  if (t.G == 1 && t.H == 8) return launch_construct_g1h8(I, t.C, t.W, st);
+  if (t.G == 1 && t.H == 16) return launch_construct_g1h16(I, t.C, t.W, st);
+  if (t.G == 1 && t.H == 32) return launch_construct_g1h32(I, t.C, t.W, st);
+  if (t.G == 2 && t.H == 32) return launch_construct_g2h32(I, t.C, t.W, st);
+  if (t.G == 4 && t.H == 32) return launch_construct_g4h32(I, t.C, t.W, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
                                    ConstructTiling t, cudaStream_t st) {
-  if (t.G * t.A > 8) return cudaErrorInvalidValue;
-  switch (t.G) {
-    case 1:
-      return launch_construct_items_g1(insts, items, count, t.C, t.A, st);
-    case 2:
-      return launch_construct_items_g2(insts, items, count, t.C, t.A, st);
-    case 4:
-      return launch_construct_items_g4(insts, items, count, t.C, t.A, st);
-    default:
-      return cudaErrorInvalidValue;
-  }
+  if (t.W < 1 || t.W > 8) return cudaErrorInvalidValue;
+  if (t.G == 1 && t.H == 8) return launch_construct_items_g1h8(insts, items, count, t.C, t.W, st);
+  if (t.G == 1 && t.H == 16) return launch_construct_items_g1h16(insts, items, count, t.C, t.W, st);
+  if (t.G == 1 && t.H == 32) return launch_construct_items_g1h32(insts, items, count, t.C, t.W, st);
+  if (t.G == 2 && t.H == 32) return launch_construct_items_g2h32(insts, items, count, t.C, t.W, st);
+  if (t.G == 4 && t.H == 32) return launch_construct_items_g4h32(insts, items, count, t.C, t.W, st);
+  return cudaErrorInvalidValue;
 }
 
 int device_sms() {
@@ -134,6 +167,7 @@ struct aco_colony {
   int use_graph = 1;
   int profile = 0;
   int warps_per_ant = 0;
+  int lanes_per_ant = 0;
   int ants_per_cta = 0;
   bool tours_valid = false;
   bool constructed = false;
@@ -144,14 +178,23 @@ struct aco_colony {
 
 static ConstructTiling tiling_of(const aco_colony* h) {
   const int n = h->I.n;
-  if (h->warps_per_ant == 0) {
+  if (h->warps_per_ant == 0 && h->lanes_per_ant == 0) {
     ConstructTiling t = default_construct_tiling(n);
-    if (h->ants_per_cta) t.A = h->ants_per_cta;
+    if (h->ants_per_cta) t = construct_tiling(n, t.G, t.H, h->ants_per_cta);
     return t;
   }
-  const int G = h->warps_per_ant;
-  int A = h->ants_per_cta ? h->ants_per_cta : (G == 1 ? 4 : G == 2 ? 2 : 1);
-  return construct_tiling(n, G, A);
+  const int G = h->warps_per_ant ? h->warps_per_ant : 1;
+  const int H = h->lanes_per_ant ? h->lanes_per_ant : 32;
+  const int A = h->ants_per_cta ? h->ants_per_cta
+                                : (H < 32 ? 4 * (32 / H) : G == 1 ? 4 : G == 2 ? 2 : 1);
+  return construct_tiling(n, G, H, A);
+}
+
+static bool tiling_ok(ConstructTiling t, int rule) {
+  if (t.C == 0 || t.W < 1 || t.W > 8) return false;
+  if (t.H < 32 && t.G != 1) return false;
+  if (rule == 1 && (t.H != 32 || t.G > 2)) return false;
+  return ants_per_cta(t) >= 1;
 }
 
 // External records so that the events also become graph nodes under capture.
@@ -169,7 +212,7 @@ static void drop_graph(aco_colony* h) {
 
 static int enqueue_construct(aco_colony* h) {
   const ConstructTiling t = tiling_of(h);
-  if (t.C == 0) return fail(ACO_EINVAL, "no construction tiling for n=%d", h->I.n);
+  if (!tiling_ok(t, h->I.rule)) return fail(ACO_EINVAL, "no construction tiling for n=%d", h->I.n);
   cudaError_t e;
   if (h->profile && (e = record_event(h, h->ev[0], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
@@ -522,33 +565,40 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
     case ACO_OPT_USE_GRAPH:
       h->use_graph = value != 0;
       break;
-    case ACO_OPT_PROFILE:
-      h->profile = value != 0;
-      break;
-    case ACO_OPT_WARPS_PER_ANT: {
-      if (value != 0 && value != 1 && value != 2 && value != 4)
-        return fail(ACO_EINVAL, "warps per ant must be 0, 1, 2 or 4");
-      const int old = h->warps_per_ant;
-      h->warps_per_ant = (int)value;
-      if (tiling_of(h).C == 0) {
-        h->warps_per_ant = old;
-        return fail(ACO_EINVAL, "no tiling with %lld warps per ant for n=%d", (long long)value,
-                    h->I.n);
+    case ACO_OPT_SELECTION: {
+      if (value != ACO_SELECT_EQ1 && value != ACO_SELECT_DATA_PARALLEL)
+        return fail(ACO_EINVAL, "selection rule %lld", (long long)value);
+      const int old = h->I.rule;
+      h->I.rule = (int)value;
+      if (!tiling_ok(tiling_of(h), h->I.rule)) {
+        h->I.rule = old;
+        return fail(ACO_EINVAL, "the data-parallel rule needs whole warps per ant (H = 32, G <= 2)");
       }
       break;
     }
-    case ACO_OPT_ANTS_PER_CTA:
-      if (value < 0 || value > 8) return fail(ACO_EINVAL, "ants per CTA must be in [0, 8]");
-      {
-        const int old = h->ants_per_cta;
-        h->ants_per_cta = (int)value;
-        const ConstructTiling t = tiling_of(h);
-        if (t.G * t.A > 8) {
-          h->ants_per_cta = old;
-          return fail(ACO_EINVAL, "more than 8 warps per CTA");
-        }
+    case ACO_OPT_PROFILE:
+      h->profile = value != 0;
+      break;
+    case ACO_OPT_WARPS_PER_ANT:
+    case ACO_OPT_LANES_PER_ANT:
+    case ACO_OPT_ANTS_PER_CTA: {
+      if (key == ACO_OPT_WARPS_PER_ANT && value != 0 && value != 1 && value != 2 && value != 4)
+        return fail(ACO_EINVAL, "warps per ant must be 0, 1, 2 or 4");
+      if (key == ACO_OPT_LANES_PER_ANT && value != 0 && value != 8 && value != 16 && value != 32)
+        return fail(ACO_EINVAL, "lanes per ant must be 0, 8, 16 or 32");
+      if (key == ACO_OPT_ANTS_PER_CTA && (value < 0 || value > 32))
+        return fail(ACO_EINVAL, "ants per CTA must be in [0, 32]");
+      int* field = key == ACO_OPT_WARPS_PER_ANT   ? &h->warps_per_ant
+                   : key == ACO_OPT_LANES_PER_ANT ? &h->lanes_per_ant
+                                                  : &h->ants_per_cta;
+      const int old = *field;
+      *field = (int)value;
+      if (!tiling_ok(tiling_of(h), h->I.rule)) {
+        *field = old;
+        return fail(ACO_EINVAL, "no construction tiling for n=%d with this option", h->I.n);
       }
       break;
+    }
     default:
       return fail(ACO_EINVAL, "unknown option %d", key);
   }
@@ -568,14 +618,20 @@ int aco_get_option(aco_handle h, int32_t key, int64_t* value) {
     case ACO_OPT_USE_GRAPH:
       *value = h->use_graph;
       break;
+    case ACO_OPT_SELECTION:
+      *value = h->I.rule;
+      break;
     case ACO_OPT_PROFILE:
       *value = h->profile;
       break;
     case ACO_OPT_WARPS_PER_ANT:
       *value = tiling_of(h).G;
       break;
+    case ACO_OPT_LANES_PER_ANT:
+      *value = tiling_of(h).H;
+      break;
     case ACO_OPT_ANTS_PER_CTA:
-      *value = tiling_of(h).A;
+      *value = ants_per_cta(tiling_of(h));
       break;
     default:
       return fail(ACO_EINVAL, "unknown option %d", key);

@@ -1,24 +1,31 @@
 // Tour construction (Section II, Eq. 1; data-parallel design of Section III-A).
 //
-// One group of G warps builds one ant's tour.  Thread t of the group owns the
-// contiguous cities [t*C, t*C + C) of every row: it loads them with float4
-// loads into registers, keeps their tabu bits (the paper's "1 = unvisited"
+// One group of threads builds one ant's tour: G whole warps (H = 32), or an
+// H-lane segment of a warp (H = 8 or 16, G = 1), so that 32/H ants share
+// every warp instruction.  Thread t of the group owns the contiguous cities
+// [t*C, t*C + C) of every row: it reads them from the row staged in shared
+// memory into registers, keeps their tabu bits (the paper's "1 = unvisited"
 // integer per city, here one bit per city in registers) and takes part in the
 // selection.  Each step:
-//   1. load row choice[cur] (C floats per thread), zero visited cities;
-//   2. M = max over unvisited (REDUX on the float bit patterns, which order
+//   1. one thread copies row choice[cur] into shared memory with the
+//      bulk-copy engine; the group waits on an mbarrier and reads its chunks
+//      (C floats per thread, conflict-free 16-byte loads); visited cities
+//      are zeroed;
+//   2. M = max over unvisited (max on the float bit patterns, which order
 //      like the values for w >= 0), across warps through shared memory;
 //   3. q_j = floor(w_j * 2^(45-ilogb M)) split exactly into two 23-bit halves
 //      by three round-toward-zero FP32 FMAs (FP32 pipe; no float-to-int
 //      conversion), per-thread u64 sums, warp inclusive scan, group totals
 //      -> Q;
 //   4. T = floor(r Q / 2^64) with r from Philox (one Philox call per lane per
-//      32 steps, broadcast by shuffle);
+//      H steps, broadcast by shuffle);
 //   5. the thread whose prefix range holds T is found by ballot; its chunk is
-//      rescanned by all 32 lanes of its warp (P = ceil(C/32) cities each),
-//      a second scan and ballot give the city.
+//      rescanned by all lanes of its warp segment (P = ceil(C/H) cities
+//      each), a second scan and ballot give the city.
 // Every operation is an exact max or an exact integer sum, so the chosen city
-// is the same for every (C, G) tiling and equals the CPU oracle's choice.
+// is the same for every (C, G, H) tiling and equals the CPU oracle's choice.
+// Every warp-level intrinsic names only the segment's lanes, so segments of
+// one warp never wait on each other even when their control flow differs.
 // After the last step the group computes C^k = sum of d over the tour and
 // writes, for every city of the tour, its predecessor and successor into
 // nbr[city][ant] (the bucketing used by the gather deposit).
@@ -141,43 +148,102 @@ __device__ __forceinline__ unsigned long long chunk_sum_groups(const uint32_t (&
   return ((unsigned long long)(hi - off) << 23) + (lo - off);
 }
 
-__device__ __forceinline__ unsigned long long warp_inclusive_scan(unsigned long long x, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long t = __shfl_up_sync(FULL, x, o);
-    if (lane >= o) x += t;
+// The lanes of one warp segment (H = 32: the whole warp).
+template <int H>
+struct Seg {
+  unsigned mask;
+  int sub;  // segment index within the warp
+  int hl;   // lane within the segment
+  __device__ __forceinline__ explicit Seg(int lane)
+      : mask(H == 32 ? FULL : (((1u << H) - 1u) << ((lane / H) * H))), sub(lane / H),
+        hl(lane % H) {}
+  template <typename T>
+  __device__ __forceinline__ T shfl(T v, int src) const {
+    return __shfl_sync(mask, v, src, H);
   }
-  return x;
-}
+  template <typename T>
+  __device__ __forceinline__ T shfl_up(T v, int d) const {
+    return __shfl_up_sync(mask, v, d, H);
+  }
+  template <typename T>
+  __device__ __forceinline__ T shfl_xor(T v, int d) const {
+    return __shfl_xor_sync(mask, v, d, H);
+  }
+  __device__ __forceinline__ uint32_t ballot(bool p) const {
+    const uint32_t b = __ballot_sync(mask, p);
+    return H == 32 ? b : (b >> (sub * H)) & ((1u << H) - 1u);
+  }
+  __device__ __forceinline__ uint32_t max_u32(uint32_t v) const {
+    if (H == 32) return __reduce_max_sync(FULL, v);
+#pragma unroll
+    for (int o = H / 2; o > 0; o >>= 1) v = max(v, shfl_xor(v, o));
+    return v;
+  }
+  __device__ __forceinline__ uint32_t min_u32(uint32_t v) const {
+    if (H == 32) return __reduce_min_sync(FULL, v);
+#pragma unroll
+    for (int o = H / 2; o > 0; o >>= 1) v = min(v, shfl_xor(v, o));
+    return v;
+  }
+  __device__ __forceinline__ unsigned long long inclusive_scan(unsigned long long x) const {
+#pragma unroll
+    for (int o = 1; o < H; o <<= 1) {
+      const unsigned long long t = shfl_up(x, o);
+      if (hl >= o) x += t;
+    }
+    return x;
+  }
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+};
 
-// Shared memory of one ant group: the staged row (32*G*C floats, 16-byte
+// Shared memory of one ant group: the staged row (H*G*C floats, 16-byte
 // aligned) followed by its mbarrier.
-template <int C, int G>
+template <int C, int G, int H>
 struct StageLayout {
-  static constexpr int kRowFloats = 32 * G * C;
+  static constexpr int kRowFloats = H * G * C;
   static constexpr int kBytes = ((kRowFloats * 4 + 8) + 15) / 16 * 16;
 };
 
-template <int C, int G>
+// Ant groups per CTA of `warps` warps.
+template <int G, int H>
+__host__ __device__ constexpr int groups_per_cta(int warps) {
+  return H == 32 ? warps / G : warps * (32 / H);
+}
+
+// R = 0: Eq. 1 by the integer roulette.  R = 1: the paper's data-parallel
+// rule: every unvisited city scores u_j * w_j with its own uniform u_j, the
+// highest score wins (ties to the lower index; all scores 0: the lowest
+// unvisited city).
+template <int C, int G, int H, int R = 0>
 __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, const int tg,
-                                              GroupSmem* gs, const int bar_id, float* srow) {
+                                              const Seg<H> seg, GroupSmem* gs, const int bar_id,
+                                              float* srow) {
   static_assert(C % 4 == 0 && C >= 4 && C <= 128, "C must be a multiple of 4 in [4,128]");
   static_assert((C / 4) % 2 == 1, "C/4 must be odd: lanes then read their chunks from shared "
                                   "memory without bank conflicts");
   static_assert(G == 1 || G == 2 || G == 4, "G must be 1, 2 or 4");
+  static_assert(H == 8 || H == 16 || H == 32, "H must be 8, 16 or 32");
+  static_assert(H == 32 || G == 1, "segments smaller than a warp serve one ant each");
   constexpr int NW = (C + 31) / 32;  // tabu words per thread
-  constexpr int P = (C + 31) / 32;   // cities per lane in the rescan
+  constexpr int P = (C + H - 1) / H;  // cities per lane in the rescan
   // The smallest chunk (4 cities) keeps its sums in registers and the
   // selected lane finds the city alone; larger chunks are rescanned by the
-  // whole warp, which measured faster than a serial in-lane search.
+  // whole segment, which measured faster than a serial in-lane search.
   constexpr bool kGroupPick = C <= 4;
   constexpr int NG = kGroupPick ? C / 4 : 1;
-  constexpr int NT = 32 * G;
+  constexpr int NT = H == 32 ? 32 * G : H;  // threads per ant
   const int n = I.n, ld = I.ld;
-  const int lane = tg & 31, wg = tg >> 5;
+  const int hl = seg.hl;          // lane within the segment
+  const int wg = H == 32 ? tg >> 5 : 0;  // warp within the group (G > 1)
   const int base = tg * C;
   const uint32_t iter = (uint32_t)I.st->iteration;
   const unsigned long long seed = I.seed;
+  auto group_wait = [&]() {
+    if (H == 32)
+      group_sync(bar_id, NT);
+    else
+      seg.sync();
+  };
 
   // Tabu bits: 1 = visited.  Padding cities (index >= n) and bits beyond C
   // start out visited.
@@ -206,11 +272,8 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   int cur = start;
   unsigned long long rwin = 0;
 
-  // Row staging: one thread copies row `cur` (4*ld bytes) into shared memory
-  // with the bulk-copy engine; the group waits on the mbarrier and every
-  // thread reads its contiguous chunk with conflict-free 16-byte loads.
   const uint32_t srow_a = smem_u32(srow);
-  const uint32_t bar = srow_a + (uint32_t)StageLayout<C, G>::kRowFloats * 4u;
+  const uint32_t bar = srow_a + (uint32_t)StageLayout<C, G, H>::kRowFloats * 4u;
   const uint32_t row_bytes = (uint32_t)ld * 4u;
   uint32_t phase = 0;
   bool waits_ok = true;
@@ -218,7 +281,7 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     mbar_init(bar, 1);
     fence_mbar_init();
   }
-  group_sync(bar_id, NT);
+  group_wait();
 
   for (int s = 1; s < n; ++s) {
     // Everyone is done with the previous row (the group agreed on `cur`).
@@ -226,12 +289,12 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       fence_proxy_async_smem();
       bulk_load(srow_a, I.choice + (size_t)cur * ld, row_bytes, bar);
     }
-    const int off = (s - 1) & 31;
+    const int off = (s - 1) % H;
     if (off == 0) {
-      const Philox4 x = step_draw(seed, (uint32_t)(s + lane), (uint32_t)ant, iter);
+      const Philox4 x = step_draw(seed, (uint32_t)(s + hl), (uint32_t)ant, iter);
       rwin = ((unsigned long long)x.x1 << 32) | x.x0;
     }
-    const unsigned long long r = shfl_u64(rwin, off);
+    const unsigned long long r = seg.shfl(rwin, off);
     if (waits_ok && !mbar_wait_bounded(bar, phase)) {
       waits_ok = false;  // stale data from here on; the status word says so
       if (tg == 0) atomicOr(&I.st->status, kStatusTimeout);
@@ -255,16 +318,51 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
       m4[i & 3] = max(m4[i & 3], v[i]);
     }
-    uint32_t mx = __reduce_max_sync(FULL, max(max(m4[0], m4[1]), max(m4[2], m4[3])));
+    uint32_t mx = seg.max_u32(max(max(m4[0], m4[1]), max(m4[2], m4[3])));
     if (G > 1) {
-      if (lane == 0) gs->wmax[wg] = mx;
+      if (hl == 0) gs->wmax[wg] = mx;
       group_sync(bar_id, NT);
 #pragma unroll
       for (int w = 0; w < G; ++w) mx = max(mx, gs->wmax[w]);
     }
 
     int next;
-    if (mx == 0u) {
+    if constexpr (R == 1) {
+      // Scores u_j * w_j; a thread's four consecutive cities share one
+      // Philox call (C and base are multiples of 4).
+      uint64_t key = 0;  // (score bits << 32) | ~index: max = best score, lowest index
+#pragma unroll
+      for (int i = 0; i < C; i += 4) {
+        const Philox4 x = philox4x32_10((uint32_t)s, (uint32_t)ant, iter,
+                                        1u + (uint32_t)((base + i) >> 2), (uint32_t)seed,
+                                        (uint32_t)(seed >> 32));
+        const uint32_t xs[4] = {x.x0, x.x1, x.x2, x.x3};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float score = __fmul_rn(candidate_uniform_of(xs[e]), __uint_as_float(v[i + e]));
+          const uint64_t k = ((uint64_t)__float_as_uint(score) << 32) |
+                             (uint32_t)(0xffffffffu - (uint32_t)(base + i + e));
+          if (score > 0.0f && k > key) key = k;
+        }
+      }
+#pragma unroll
+      for (int o = H / 2; o > 0; o >>= 1) {
+        const uint64_t other = seg.shfl_xor(key, o);
+        key = other > key ? other : key;
+      }
+      if (G > 1) {
+        if (hl == 0) gs->wsum[wg] = key;
+        group_sync(bar_id, NT);
+#pragma unroll
+        for (int w = 0; w < G; ++w) key = gs->wsum[w] > key ? gs->wsum[w] : key;
+      }
+      if (key != 0) mx = 1u;  // a positive score exists
+      else mx = 0u;           // every score is 0: the rule below takes the lowest unvisited
+      next = (int)(0xffffffffu - (uint32_t)key);
+    }
+    if (R == 1 && mx != 0u) {
+      // chosen above
+    } else if (mx == 0u) {
       // Every unvisited weight is zero: the lowest-index unvisited city.
       uint32_t cand = 0xffffffffu;
 #pragma unroll
@@ -272,15 +370,15 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
         const uint32_t fr = ~vis[w];
         if (fr) cand = (uint32_t)(base + 32 * w + __ffs(fr) - 1);
       }
-      cand = __reduce_min_sync(FULL, cand);
+      cand = seg.min_u32(cand);
       if (G > 1) {
-        if (lane == 0) gs->wmin[wg] = (int)cand;
+        if (hl == 0) gs->wmin[wg] = (int)cand;
         group_sync(bar_id, NT);
 #pragma unroll
         for (int w = 0; w < G; ++w) cand = min(cand, (uint32_t)gs->wmin[w]);
       }
       next = (int)cand;
-    } else {
+    } else if constexpr (R == 0) {
       const int sc = kRouletteBits - 1 - exponent_of_bits(mx);
       float f1, f1s, f2;
       quant_factors(sc, f1, f1s, f2);
@@ -296,11 +394,11 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
         mine = chunk_sum_groups<C>(v, f1, f1s, ghi, glo);
       else
         mine = chunk_sum<C>(v, f1, f1s);
-      const unsigned long long incl = warp_inclusive_scan(mine, lane);
-      const unsigned long long wtot = shfl_u64(incl, 31);
+      const unsigned long long incl = seg.inclusive_scan(mine);
+      const unsigned long long wtot = seg.shfl(incl, H - 1);
       unsigned long long woff = 0, Q = wtot;
       if (G > 1) {
-        if (lane == 0) gs->wsum[wg] = wtot;
+        if (hl == 0) gs->wsum[wg] = wtot;
         group_sync(bar_id, NT);
         Q = 0;
 #pragma unroll
@@ -314,14 +412,14 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       next = 0;
       if (G == 1 || (T >= woff && T - woff < wtot)) {
         const unsigned long long t1 = T - woff;
-        const int L = max(__ffs(__ballot_sync(FULL, incl > t1)) - 1, 0);
-        const unsigned long long t2 = t1 - shfl_u64(incl - mine, L);
-        const int baseL = (wg * 32 + L) * C;  // within the staged row
+        const int L = max(__ffs(seg.ballot(incl > t1)) - 1, 0);
+        const unsigned long long t2 = t1 - seg.shfl(incl - mine, L);
+        const int baseL = (wg * H + L) * C;  // within the staged row
         if constexpr (kGroupPick) {
           // Lane L walks its group sums, then the four cities of the group
           // holding the target (all from registers).
           int pick = 0;
-          if (lane == L) {
+          if (hl == L) {
             unsigned long long cum = 0;
             bool found = false;
 #pragma unroll
@@ -345,43 +443,42 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
               cum += gv;
             }
           }
-          next = baseL + __shfl_sync(FULL, pick, L);
-          if (G > 1 && lane == 0) gs->next = next;
+          next = baseL + seg.shfl(pick, L);
         } else {
-        uint32_t visL[NW];
+          uint32_t visL[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) visL[w] = __shfl_sync(FULL, vis[w], L);
-        unsigned long long qv[P];
-        unsigned long long ps = 0;
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-          const int li = lane * P + p;
-          uint32_t word = FULL;
-#pragma unroll
-          for (int w = 0; w < NW; ++w)
-            if (w == (li >> 5)) word = visL[w];
-          uint32_t w8 = 0u;
-          if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u))
-            w8 = __float_as_uint(row[baseL + li]);
-          qv[p] = quant_value(w8, f1, f1s, f2);
-          ps += qv[p];
-        }
-        const unsigned long long incl2 = warp_inclusive_scan(ps, lane);
-        const int L2 = max(__ffs(__ballot_sync(FULL, incl2 > t2)) - 1, 0);
-        int pick = 0;
-        if (lane == L2) {
-          unsigned long long c = incl2 - ps;
-          pick = -1;
+          for (int w = 0; w < NW; ++w) visL[w] = seg.shfl(vis[w], L);
+          unsigned long long qv[P];
+          unsigned long long ps = 0;
 #pragma unroll
           for (int p = 0; p < P; ++p) {
-            c += qv[p];
-            if (pick < 0 && c > t2) pick = p;
+            const int li = hl * P + p;
+            uint32_t word = FULL;
+#pragma unroll
+            for (int w = 0; w < NW; ++w)
+              if (w == (li >> 5)) word = visL[w];
+            uint32_t w8 = 0u;
+            if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u))
+              w8 = __float_as_uint(row[baseL + li]);
+            qv[p] = quant_value(w8, f1, f1s, f2);
+            ps += qv[p];
           }
+          const unsigned long long incl2 = seg.inclusive_scan(ps);
+          const int L2 = max(__ffs(seg.ballot(incl2 > t2)) - 1, 0);
+          int pick = 0;
+          if (hl == L2) {
+            unsigned long long c = incl2 - ps;
+            pick = -1;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+              c += qv[p];
+              if (pick < 0 && c > t2) pick = p;
+            }
+          }
+          pick = max(seg.shfl(pick, L2), 0);
+          next = baseL + L2 * P + pick;
         }
-        pick = max(__shfl_sync(FULL, pick, L2), 0);
-        next = baseL + L2 * P + pick;
-        if (G > 1 && lane == 0) gs->next = next;
-        }
+        if (G > 1 && hl == 0) gs->next = next;
       }
       if (G > 1) {
         group_sync(bar_id, NT);
@@ -403,10 +500,10 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     }
     if (tg == 0) tour[s] = next;
     cur = next;
-    group_sync(bar_id, NT);
+    group_wait();
   }
   if (tg == 0) tour[n] = start;
-  group_sync(bar_id, NT);
+  group_wait();
 
   // C^k (Section II) and the per-city neighbour buckets.
   long long len = 0;
@@ -417,9 +514,9 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     I.nbr[(size_t)a * I.ldm + ant] = ((uint32_t)p << 16) | (uint32_t)b;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
+  for (int o = H / 2; o > 0; o >>= 1) len += seg.shfl_xor(len, o);
   if (G > 1) {
-    if (lane == 0) gs->wlen[wg] = len;
+    if (hl == 0) gs->wlen[wg] = len;
     group_sync(bar_id, NT);
     len = 0;
 #pragma unroll
@@ -428,50 +525,66 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   if (tg == 0) I.lens[ant] = len;
 }
 
-// One CTA holds blockDim.x / (32 G) ant groups; dynamic shared memory holds
-// one StageLayout<C, G> per group.
-template <int C, int G>
+// Placement of one thread: its ant group within the CTA and its index tg
+// within the group.
+template <int G, int H>
+__device__ __forceinline__ void group_of_thread(int& grp, int& tg) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (H == 32) {
+    grp = threadIdx.x / (32 * G);
+    tg = threadIdx.x % (32 * G);
+  } else {
+    grp = warp * (32 / H) + lane / H;
+    tg = lane % H;
+  }
+}
+
+// One CTA holds groups_per_cta<G, H>(blockDim.x / 32) ant groups; dynamic
+// shared memory holds one StageLayout<C, G, H> per group.
+template <int C, int G, int H, int R = 0>
 __global__ void __launch_bounds__(256) construct_kernel(Instance I) {
   __shared__ GroupSmem gs[kMaxGroupsPerCta];
   extern __shared__ __align__(16) unsigned char stage[];
-  const int grp = threadIdx.x / (32 * G);
-  const int tg = threadIdx.x % (32 * G);
-  const int ant = blockIdx.x * (blockDim.x / (32 * G)) + grp;
+  int grp, tg;
+  group_of_thread<G, H>(grp, tg);
+  const int ant = blockIdx.x * groups_per_cta<G, H>(blockDim.x >> 5) + grp;
   if (ant >= I.m) return;
-  construct_ant<C, G>(I, ant, tg, &gs[grp], 1 + grp,
-                      reinterpret_cast<float*>(stage + grp * StageLayout<C, G>::kBytes));
+  construct_ant<C, G, H, R>(I, ant, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
+                            reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes));
 }
 
 // Batched form: group g of block b builds ant items[b*A + g].y of instance
 // insts[items[b*A + g].x].  Items are listed longest instance first.
-template <int C, int G>
+template <int C, int G, int H>
 __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __restrict__ insts,
                                                               const int2* __restrict__ items,
                                                               int count) {
   __shared__ GroupSmem gs[kMaxGroupsPerCta];
-  const int grp = threadIdx.x / (32 * G);
-  const int tg = threadIdx.x % (32 * G);
-  const int idx = blockIdx.x * (blockDim.x / (32 * G)) + grp;
+  extern __shared__ __align__(16) unsigned char stage[];
+  int grp, tg;
+  group_of_thread<G, H>(grp, tg);
+  const int idx = blockIdx.x * groups_per_cta<G, H>(blockDim.x >> 5) + grp;
   if (idx >= count) return;
   const int2 it = items[idx];
   const Instance I = insts[it.x];
-  extern __shared__ __align__(16) unsigned char stage[];
-  construct_ant<C, G>(I, it.y, tg, &gs[grp], 1 + grp,
-                      reinterpret_cast<float*>(stage + grp * StageLayout<C, G>::kBytes));
+  construct_ant<C, G, H>(I, it.y, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
+                         reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes));
 }
 
-// Dynamic shared memory for A groups, with the opt-in above 48 KB set once.
-template <int C, int G, bool kItems>
-inline size_t construct_smem_setup(int A) {
-  const size_t bytes = (size_t)A * StageLayout<C, G>::kBytes;
+// Dynamic shared memory for a CTA of `warps` warps, with the opt-in above
+// 48 KB set once per kernel.
+template <int C, int G, int H, bool kItems, int R = 0>
+inline size_t construct_smem_setup(int warps) {
+  const size_t bytes = (size_t)groups_per_cta<G, H>(warps) * StageLayout<C, G, H>::kBytes;
   static bool done = false;
   if (!done) {
-    if (kItems)
-      cudaFuncSetAttribute(construct_items_kernel<C, G>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * StageLayout<C, G>::kBytes);
+    const int most = groups_per_cta<G, H>(8) * StageLayout<C, G, H>::kBytes;
+    if constexpr (kItems)
+      cudaFuncSetAttribute(construct_items_kernel<C, G, H>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     else
-      cudaFuncSetAttribute(construct_kernel<C, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           8 * StageLayout<C, G>::kBytes);
+      cudaFuncSetAttribute(construct_kernel<C, G, H, R>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     done = true;
   }
   return bytes;

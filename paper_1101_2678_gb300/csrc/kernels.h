@@ -11,17 +11,24 @@ constexpr int kDepositGather = 0;
 constexpr int kDepositAtomicU64 = 1;
 constexpr int kDepositAtomicF32 = 2;
 
-// Tiling of the construction kernel: C cities per thread, G warps per ant,
-// A ants per CTA.
+// Tiling of the construction kernel: C cities per thread, G warps per ant
+// group, H lanes per ant (H < 32: 32/H ants share a warp, G = 1), W warps
+// per CTA.
 struct ConstructTiling {
-  int C, G, A;
+  int C, G, H, W;
 };
 
-// Smallest supported tiling for n cities with G warps per ant (C = 0 if none).
-ConstructTiling construct_tiling(int n, int G, int A);
-// Default choice of G and A for n cities.
+// Smallest supported C for n cities with G warps and H lanes per ant, and
+// `ants_per_cta` ants per CTA (C = 0 if there is none).
+ConstructTiling construct_tiling(int n, int G, int H, int ants_per_cta);
+// Default tiling of a single instance (latency: whole warps per ant).
 ConstructTiling default_construct_tiling(int n);
+// Default tiling of batched instances (throughput: the fewest issued
+// instructions per ant step).
+ConstructTiling batched_construct_tiling(int n);
 cudaError_t launch_construct(const Instance& I, ConstructTiling t, cudaStream_t st);
+// Ants per CTA of a tiling.
+int ants_per_cta(ConstructTiling t);
 
 cudaError_t launch_setup(const Instance& I, int sms, cudaStream_t st);
 cudaError_t launch_choice(const Instance& I, int sms, cudaStream_t st);
@@ -31,17 +38,20 @@ cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t 
 int launches_for_variant(int variant);
 int gather_warps_per_cta(int ld);
 
-// Per-G dispatchers (one translation unit each, compiled in parallel).
-cudaError_t launch_construct_g1(const Instance& I, int C, int A, cudaStream_t st);
-cudaError_t launch_construct_g2(const Instance& I, int C, int A, cudaStream_t st);
-cudaError_t launch_construct_g4(const Instance& I, int C, int A, cudaStream_t st);
-bool construct_supported(int C, int G);
-cudaError_t launch_construct_items_g1(const Instance* insts, const int2* items, int count, int C,
-                                      int A, cudaStream_t st);
-cudaError_t launch_construct_items_g2(const Instance* insts, const int2* items, int count, int C,
-                                      int A, cudaStream_t st);
-cudaError_t launch_construct_items_g4(const Instance* insts, const int2* items, int count, int C,
-                                      int A, cudaStream_t st);
+// Per-(G, H) dispatchers (one translation unit each, compiled in parallel).
+#define ACO_DECLARE_CONSTRUCT(tag)                                                              \
+  cudaError_t launch_construct_##tag(const Instance& I, int C, int warps, cudaStream_t st);     \
+  cudaError_t launch_construct_items_##tag(const Instance* insts, const int2* items, int count, \
+                                           int C, int warps, cudaStream_t st);
+ACO_DECLARE_CONSTRUCT(g1h8)
+ACO_DECLARE_CONSTRUCT(g1h16)
+ACO_DECLARE_CONSTRUCT(g1h32)
+ACO_DECLARE_CONSTRUCT(g2h32)
+ACO_DECLARE_CONSTRUCT(g4h32)
+#undef ACO_DECLARE_CONSTRUCT
+bool construct_supported(int C, int G, int H);
+// The paper's data-parallel selection rule (Instance::rule == 1); H = 32, G = 1 or 2.
+cudaError_t launch_construct_rule1(const Instance& I, ConstructTiling t, cudaStream_t st);
 cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
                                    ConstructTiling t, cudaStream_t st);
 

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -199,17 +200,17 @@ static int pool_rebuild(aco_pool* p) {
   });
   p->h_live = live;
   // group by tiling class, keeping the longest-first order inside a class
-  std::map<std::pair<int, int>, std::vector<int>> by_class;
-  std::vector<std::pair<int, int>> class_order;
+  std::map<std::tuple<int, int, int>, std::vector<int>> by_class;
+  std::vector<std::tuple<int, int, int>> class_order;
   for (int s : live) {
-    const ConstructTiling t = default_construct_tiling(p->slots[(size_t)s].n);
-    const auto key = std::make_pair(t.G, t.C);
+    const ConstructTiling t = batched_construct_tiling(p->slots[(size_t)s].n);
+    const auto key = std::make_tuple(t.G, t.H, t.C);
     if (!by_class.count(key)) class_order.push_back(key);
     by_class[key].push_back(s);
   }
   for (const auto& key : class_order) {
     aco_pool::Class c;
-    c.t = default_construct_tiling(p->slots[(size_t)by_class[key][0]].n);
+    c.t = batched_construct_tiling(p->slots[(size_t)by_class[key][0]].n);
     c.begin = (int)p->h_items.size();
     for (int s : by_class[key])
       for (int k = 0; k < p->slots[(size_t)s].m; ++k) p->h_items.push_back(make_int2(s, k));

@@ -62,26 +62,32 @@ def test_setup_matches_oracle(aco, orc, n, beta):
 # Tour construction (Eq. 1)
 # ---------------------------------------------------------------------------
 
-TILINGS = [(0, 0), (1, 1), (1, 4), (2, 2), (4, 1), (4, 2)]
+# (warps per ant, lanes per ant, ants per CTA); 0 = library default
+TILINGS = [(0, 0, 0), (1, 32, 1), (1, 32, 4), (2, 32, 2), (4, 32, 1), (4, 32, 2),
+           (1, 16, 2), (1, 16, 8), (1, 8, 4), (1, 8, 32)]
 
 
-@pytest.mark.parametrize("n", [3, 5, 31, 48, 97, 129, 300, 517])
+@pytest.mark.parametrize("n", [3, 5, 31, 48, 97, 129, 300, 517, 1100])
 def test_first_iteration_tours_match_oracle(aco, orc, n):
     inst = I.uniform_instance(n, 1000, seed=100 + n)
     m = n + 3
     ch = oracle_initial_choice(orc, inst.dist, m)
     otours, olens = orc.construct(ch, inst.dist, m, seed=7, iteration=0)
     with aco.Colony(inst.dist, m, seed=7) as c:
-        for G, A in TILINGS:
+        for G, H, A in TILINGS:
             if G:
+                aco.aco_set_option(c.h, aco.ACO_OPT_WARPS_PER_ANT, 0)
+                aco.aco_set_option(c.h, aco.ACO_OPT_LANES_PER_ANT, 0)
+                aco.aco_set_option(c.h, aco.ACO_OPT_ANTS_PER_CTA, 0)
                 try:
                     aco.aco_set_option(c.h, aco.ACO_OPT_WARPS_PER_ANT, G)
+                    aco.aco_set_option(c.h, aco.ACO_OPT_LANES_PER_ANT, H)
+                    aco.aco_set_option(c.h, aco.ACO_OPT_ANTS_PER_CTA, A)
                 except aco.AcoError:
-                    continue  # no tiling for this n and G
-                aco.aco_set_option(c.h, aco.ACO_OPT_ANTS_PER_CTA, A)
+                    continue  # no tiling for this n with these options
             tours, lens = aco.aco_construct_tours(c.h, n, m)
-            assert np.array_equal(tours, otours), (G, A)
-            assert np.array_equal(lens, olens), (G, A)
+            assert np.array_equal(tours, otours), (G, H, A)
+            assert np.array_equal(lens, olens), (G, H, A)
 
 
 @pytest.mark.parametrize("wl,ants", [("n1002", 12), ("n2392", 6)])
@@ -286,3 +292,40 @@ def test_profiled_phase_times(aco):
         t = aco.aco_get_kernel_times(c.h)
         assert t[aco.ACO_PHASE_CONSTRUCT] > 0 and t[aco.ACO_PHASE_UPDATE] > 0
         assert aco.aco_kernel_launches_per_iteration(c.h) == 3
+
+
+# ---------------------------------------------------------------------------
+# The paper's data-parallel selection rule (optional, ACO_SELECT_DATA_PARALLEL)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [5, 48, 300, 1100, 2400])
+def test_data_parallel_rule_tours_match_oracle(aco, orc, n):
+    inst = I.uniform_instance(n, 1000, seed=300 + n)
+    m = 17 if n > 1000 else n + 1
+    ch = oracle_initial_choice(orc, inst.dist, m)
+    with aco.Colony(inst.dist, m, seed=4) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
+        ref_t, ref_l = orc.construct(ch, inst.dist, m, seed=4, iteration=0, rule=1)
+        for G, A in [(0, 0), (1, 1), (2, 2)]:
+            if G:
+                try:
+                    aco.aco_set_option(c.h, aco.ACO_OPT_WARPS_PER_ANT, G)
+                    aco.aco_set_option(c.h, aco.ACO_OPT_ANTS_PER_CTA, A)
+                except aco.AcoError:
+                    continue
+            tours, lens = aco.aco_construct_tours(c.h, n, m)
+            assert np.array_equal(tours, ref_t), (G, A)
+            assert np.array_equal(lens, ref_l), (G, A)
+        with pytest.raises(aco.AcoError):
+            aco.aco_set_option(c.h, aco.ACO_OPT_LANES_PER_ANT, 16)
+
+
+def test_data_parallel_rule_run_bit_exact(aco, orc):
+    inst = I.clustered_instance(97, seed=8, clusters=5, side=3000)
+    ref = orc.run(inst.dist, 50, 8, 21, rule=1)
+    with aco.Colony(inst.dist, 50, seed=21) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
+        aco.aco_iterate(c.h, 8)
+        assert np.array_equal(aco.aco_get_pheromone(c.h, 97), ref["tau32"])
+        tour, best = aco.aco_best_tour(c.h, 97)
+    assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
