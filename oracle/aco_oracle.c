@@ -60,6 +60,13 @@
  *     (floor(x / 2^8) + 1) * 2^-24 with x word (j mod 4) of Philox counter
  *     (step, ant, iteration, 1 + floor(j / 4)).  This is not Eq. 1: for two
  *     cities with w_1 >= w_2 it picks city 2 with probability w_2 / (2 w_1).
+ *  R9 (optional) nearest-neighbour lists (Section II, the construction the
+ *     paper's Table 2 versions 4-6 use with nn = 30): list(i) holds the nn
+ *     cities j != i with the smallest d_ij, ties to the lower index, in that
+ *     order.  An ant at i samples Eq. 1 restricted to the unvisited entries
+ *     of list(i) by the integer roulette of R2 in list order; if every entry
+ *     is visited it moves to the unvisited city with the largest weight,
+ *     ties to the lower index.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared -lm.
  * -ffp-contract=off matters: a fused multiply-add would change the rounding of
@@ -212,6 +219,51 @@ int orc_iroulette(int n, const float *w, const uint8_t *visited, uint64_t seed, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Nearest-neighbour lists and the list-restricted step (reading R9).        */
+/* ------------------------------------------------------------------------- */
+void orc_nn_lists(int n, const int32_t *d, int nn, int32_t *lists)
+{
+    for (int i = 0; i < n; ++i) {
+        /* selection by repeated minimum of (d_ij, j) above the previous pick */
+        long long last_d = -1;
+        int last_j = -1;
+        for (int l = 0; l < nn; ++l) {
+            int best = -1;
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                long long dj = d[(size_t)i * n + j];
+                int after_last = dj > last_d || (dj == last_d && j > last_j);
+                if (!after_last) continue;
+                if (best < 0 || dj < d[(size_t)i * n + best]) best = j;
+            }
+            lists[(size_t)i * nn + l] = best;
+            last_d = d[(size_t)i * n + best];
+            last_j = best;
+        }
+    }
+}
+
+int orc_nn_select(int n, int nn, const int32_t *list, const float *w, const uint8_t *visited,
+                  uint64_t r)
+{
+    float wl[32];
+    uint8_t vl[32];
+    int any = 0;
+    for (int l = 0; l < nn; ++l) {
+        wl[l] = w[list[l]];
+        vl[l] = visited[list[l]];
+        if (!vl[l]) any = 1;
+    }
+    if (any) return list[orc_roulette(nn, wl, vl, r)];
+    int best = -1;
+    for (int j = 0; j < n; ++j) {
+        if (visited[j]) continue;
+        if (best < 0 || w[j] > w[best]) best = j;
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Setup: heuristic, nearest-neighbour tour, initial pheromone.              */
 /* ------------------------------------------------------------------------- */
 
@@ -287,9 +339,17 @@ void orc_choice(int n, const float *tau, const float *heta, float alpha, float *
 /* Tour construction (Section II): one ant.                                  */
 /* tour has n+1 entries, tour[n] = tour[0].  Returns C^k.                    */
 /* ------------------------------------------------------------------------- */
-/* rule 0: Eq. 1 (reading R2); rule 1: the paper's data-parallel rule (R8). */
+/* rule 0: Eq. 1 (reading R2); rule 1: the paper's data-parallel rule (R8);
+   rule 2: nearest-neighbour lists of length nn (R9). */
+int64_t orc_construct_ant_nn(int n, const float *choice, const int32_t *d, uint64_t seed,
+                             uint32_t iteration, uint32_t ant, int rule, int nn,
+                             const int32_t *lists, int32_t *tour);
+
 int64_t orc_construct_ant_rule(int n, const float *choice, const int32_t *d, uint64_t seed,
-                               uint32_t iteration, uint32_t ant, int rule, int32_t *tour);
+                               uint32_t iteration, uint32_t ant, int rule, int32_t *tour)
+{
+    return orc_construct_ant_nn(n, choice, d, seed, iteration, ant, rule, 0, NULL, tour);
+}
 
 int64_t orc_construct_ant(int n, const float *choice, const int32_t *d, uint64_t seed,
                           uint32_t iteration, uint32_t ant, int32_t *tour)
@@ -297,8 +357,9 @@ int64_t orc_construct_ant(int n, const float *choice, const int32_t *d, uint64_t
     return orc_construct_ant_rule(n, choice, d, seed, iteration, ant, 0, tour);
 }
 
-int64_t orc_construct_ant_rule(int n, const float *choice, const int32_t *d, uint64_t seed,
-                               uint32_t iteration, uint32_t ant, int rule, int32_t *tour)
+int64_t orc_construct_ant_nn(int n, const float *choice, const int32_t *d, uint64_t seed,
+                             uint32_t iteration, uint32_t ant, int rule, int nn,
+                             const int32_t *lists, int32_t *tour)
 {
     uint8_t *visited = (uint8_t *)calloc((size_t)n, 1);
     uint32_t x[4];
@@ -309,7 +370,12 @@ int64_t orc_construct_ant_rule(int n, const float *choice, const int32_t *d, uin
     int cur = start;
     for (int s = 1; s < n; ++s) {
         int next;
-        if (rule == 1) {
+        if (rule == 2) {
+            draw(seed, (uint32_t)s, ant, iteration, x);
+            uint64_t r = ((uint64_t)x[1] << 32) | (uint64_t)x[0];
+            next = orc_nn_select(n, nn, lists + (size_t)cur * nn, choice + (size_t)cur * n,
+                                 visited, r);
+        } else if (rule == 1) {
             next = orc_iroulette(n, choice + (size_t)cur * n, visited, seed, (uint32_t)s, ant,
                                  iteration);
         } else {
@@ -328,12 +394,19 @@ int64_t orc_construct_ant_rule(int n, const float *choice, const int32_t *d, uin
     return len;
 }
 
+void orc_construct_nn(int n, int m, const float *choice, const int32_t *d, uint64_t seed,
+                      uint32_t iteration, int rule, int nn, const int32_t *lists,
+                      int32_t *tours, int64_t *lens)
+{
+    for (int k = 0; k < m; ++k)
+        lens[k] = orc_construct_ant_nn(n, choice, d, seed, iteration, (uint32_t)k, rule, nn,
+                                       lists, tours + (size_t)k * (n + 1));
+}
+
 void orc_construct_rule(int n, int m, const float *choice, const int32_t *d, uint64_t seed,
                         uint32_t iteration, int rule, int32_t *tours, int64_t *lens)
 {
-    for (int k = 0; k < m; ++k)
-        lens[k] = orc_construct_ant_rule(n, choice, d, seed, iteration, (uint32_t)k, rule,
-                                         tours + (size_t)k * (n + 1));
+    orc_construct_nn(n, m, choice, d, seed, iteration, rule, 0, NULL, tours, lens);
 }
 
 void orc_construct(int n, int m, const float *choice, const int32_t *d, uint64_t seed,
@@ -411,6 +484,10 @@ int orc_run_rule(int n, const int32_t *d, float alpha, float beta, float rho, in
                  uint64_t seed, int iterations, int rule, int32_t *best_tour, int64_t *best_len,
                  float *tau32_out, double *tau64_out, int32_t *last_tours, int64_t *last_lens,
                  int64_t *iter_best);
+int orc_run_nn(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+               uint64_t seed, int iterations, int rule, int nn, int32_t *best_tour,
+               int64_t *best_len, float *tau32_out, double *tau64_out, int32_t *last_tours,
+               int64_t *last_lens, int64_t *iter_best);
 
 int orc_run(int n, const int32_t *d, float alpha, float beta, float rho, int m, uint64_t seed,
             int iterations, int32_t *best_tour, int64_t *best_len, float *tau32_out,
@@ -425,12 +502,28 @@ int orc_run_rule(int n, const int32_t *d, float alpha, float beta, float rho, in
                  float *tau32_out, double *tau64_out, int32_t *last_tours, int64_t *last_lens,
                  int64_t *iter_best)
 {
-    size_t nn = (size_t)n * n;
-    float *heta = (float *)malloc(nn * sizeof(float));
-    double *h64 = (double *)malloc(nn * sizeof(double));
-    float *tau = (float *)malloc(nn * sizeof(float));
-    double *tau64 = (double *)malloc(nn * sizeof(double));
-    float *choice = (float *)malloc(nn * sizeof(float));
+    return orc_run_nn(n, d, alpha, beta, rho, m, seed, iterations, rule, 0, best_tour, best_len,
+                      tau32_out, tau64_out, last_tours, last_lens, iter_best);
+}
+
+int orc_run_nn(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+               uint64_t seed, int iterations, int rule, int nn, int32_t *best_tour,
+               int64_t *best_len, float *tau32_out, double *tau64_out, int32_t *last_tours,
+               int64_t *last_lens, int64_t *iter_best)
+{
+    int32_t *lists = NULL;
+    if (rule == 2) {
+        if (nn < 1 || nn > 32 || nn > n - 1) return -1;
+        lists = (int32_t *)malloc((size_t)n * nn * sizeof(int32_t));
+        if (!lists) return -2;
+        orc_nn_lists(n, d, nn, lists);
+    }
+    size_t cells = (size_t)n * n;
+    float *heta = (float *)malloc(cells * sizeof(float));
+    double *h64 = (double *)malloc(cells * sizeof(double));
+    float *tau = (float *)malloc(cells * sizeof(float));
+    double *tau64 = (double *)malloc(cells * sizeof(double));
+    float *choice = (float *)malloc(cells * sizeof(float));
     int32_t *tours = (int32_t *)malloc((size_t)m * (n + 1) * sizeof(int32_t));
     int64_t *lens = (int64_t *)malloc((size_t)m * sizeof(int64_t));
     if (!heta || !h64 || !tau || !tau64 || !choice || !tours || !lens) return -2;
@@ -449,7 +542,7 @@ int orc_run_rule(int n, const int32_t *d, float alpha, float beta, float rho, in
     int64_t best = INT64_MAX;
     for (int it = 0; it < iterations; ++it) {
         orc_choice(n, tau, heta, alpha, choice);
-        orc_construct_rule(n, m, choice, d, seed, (uint32_t)it, rule, tours, lens);
+        orc_construct_nn(n, m, choice, d, seed, (uint32_t)it, rule, nn, lists, tours, lens);
         int kbest = 0;
         for (int k = 1; k < m; ++k)
             if (lens[k] < lens[kbest]) kbest = k;
@@ -462,12 +555,13 @@ int orc_run_rule(int n, const int32_t *d, float alpha, float beta, float rho, in
         orc_update_fp64(n, m, tours, lens, (double)rho, tau64);
     }
     if (best_len) *best_len = best;
-    if (tau32_out) memcpy(tau32_out, tau, nn * sizeof(float));
-    if (tau64_out) memcpy(tau64_out, tau64, nn * sizeof(double));
+    if (tau32_out) memcpy(tau32_out, tau, cells * sizeof(float));
+    if (tau64_out) memcpy(tau64_out, tau64, cells * sizeof(double));
     if (last_tours) memcpy(last_tours, tours, (size_t)m * (n + 1) * sizeof(int32_t));
     if (last_lens) memcpy(last_lens, lens, (size_t)m * sizeof(int64_t));
     (void)h64;
     free(heta); free(h64); free(tau); free(tau64); free(choice); free(tours); free(lens);
+    free(lists);
     return 0;
 }
 

@@ -90,6 +90,17 @@ def lib():
             L.orc_run_rule.argtypes = [C.c_int, i32p, C.c_float, C.c_float, C.c_float, C.c_int,
                                        C.c_uint64, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp]
             L.orc_run_rule.restype = C.c_int
+            L.orc_nn_lists.argtypes = [C.c_int, i32p, C.c_int, i32p]
+            L.orc_nn_lists.restype = None
+            L.orc_nn_select.argtypes = [C.c_int, C.c_int, i32p, f32p, u8p, C.c_uint64]
+            L.orc_nn_select.restype = C.c_int
+            L.orc_construct_nn.argtypes = [C.c_int, C.c_int, f32p, i32p, C.c_uint64, C.c_uint32,
+                                           C.c_int, C.c_int, vp, i32p, i64p]
+            L.orc_construct_nn.restype = None
+            L.orc_run_nn.argtypes = [C.c_int, i32p, C.c_float, C.c_float, C.c_float, C.c_int,
+                                     C.c_uint64, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp,
+                                     vp, vp]
+            L.orc_run_nn.restype = C.c_int
             L.orc_brute_force.argtypes = [C.c_int, i32p, i32p]
             L.orc_brute_force.restype = C.c_int64
             _lib = L
@@ -169,6 +180,34 @@ def construct(choice_, dist, m: int, seed: int, iteration: int, rule: int = 0):
     return tours, lens
 
 
+def nn_lists(dist, nn: int) -> np.ndarray:
+    d = _i32(dist)
+    n = d.shape[0]
+    out = np.zeros((n, nn), np.int32)
+    lib().orc_nn_lists(n, d, nn, out)
+    return out
+
+
+def nn_select(list_row, w, visited, r: int) -> int:
+    lst = np.ascontiguousarray(list_row, np.int32)
+    w = np.ascontiguousarray(w, np.float32)
+    v = np.ascontiguousarray(visited, np.uint8)
+    return int(lib().orc_nn_select(len(w), len(lst), lst, w, v, C.c_uint64(r)))
+
+
+def construct_nn(choice_, dist, m: int, seed: int, iteration: int, nn: int):
+    """Tours by the nearest-neighbour-list rule (reading R9)."""
+    ch = np.ascontiguousarray(choice_, np.float32)
+    d = _i32(dist)
+    n = d.shape[0]
+    lists = nn_lists(d, nn)
+    tours = np.zeros((m, n + 1), np.int32)
+    lens = np.zeros(m, np.int64)
+    lib().orc_construct_nn(n, m, ch, d, C.c_uint64(seed), iteration, 2, nn, lists.ctypes.data,
+                           tours, lens)
+    return tours, lens
+
+
 def candidate_uniform(seed: int, step: int, ant: int, iteration: int, j: int) -> float:
     return float(np.float32(lib().orc_candidate_uniform(C.c_uint64(seed), step, ant, iteration, j)))
 
@@ -201,10 +240,11 @@ def update_fp64(tau, tours, lens, rho: float) -> np.ndarray:
 
 
 def run(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.5,
-        rule: int = 0) -> dict:
+        rule: int = 0, nn: int = 0) -> dict:
     """A whole Ant System run in mirror mode, with the fp64 pheromone carried alongside.
 
-    rule 0 selects by Eq. 1, rule 1 by the paper's data-parallel rule."""
+    rule 0 selects by Eq. 1, rule 1 by the paper's data-parallel rule, rule 2
+    by nearest-neighbour lists of length nn."""
     d = _i32(dist)
     n = d.shape[0]
     best_tour = np.zeros(n + 1, np.int32)
@@ -214,9 +254,9 @@ def run(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.5,
     tours = np.zeros((m, n + 1), np.int32)
     lens = np.zeros(m, np.int64)
     iter_best = np.zeros(max(iterations, 1), np.int64)
-    rc = lib().orc_run_rule(n, d, float(alpha), float(beta), float(rho), int(m),
-                       C.c_uint64(seed), int(iterations), int(rule), best_tour.ctypes.data,
-                       best_len.ctypes.data,
+    rc = lib().orc_run_nn(n, d, float(alpha), float(beta), float(rho), int(m),
+                       C.c_uint64(seed), int(iterations), int(rule), int(nn),
+                       best_tour.ctypes.data, best_len.ctypes.data,
                        tau32.ctypes.data, tau64.ctypes.data, tours.ctypes.data,
                        lens.ctypes.data, iter_best.ctypes.data)
     if rc != 0:

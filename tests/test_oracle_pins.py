@@ -403,3 +403,86 @@ def test_iroulette_degenerate_rows_and_tours(orc):
     # starts are shared with Eq. 1 (same counter), later moves differ in general
     t0, _ = orc.construct(ch, inst.dist, 11, seed=2, iteration=1, rule=0)
     assert np.array_equal(t0[:, 0], tours[:, 0])
+
+
+# --------------------------------------------------------------------------
+# Nearest-neighbour lists (reading R9; Table 2 versions 4-6 use nn = 30)
+# --------------------------------------------------------------------------
+
+def test_nn_lists_on_a_line(orc):
+    # cities at x = 0..n-1 in order: list(k) = k-1, k+1, k-2, k+2, ... (the
+    # lower index first on equal distance), truncated at the ends
+    n, nn = 12, 5
+    coords = np.stack([np.arange(n), np.zeros(n)], 1)
+    lists = orc.nn_lists(I.distance_matrix(coords), nn)
+    for k in range(n):
+        expect = []
+        for step in range(1, n):
+            for j in (k - step, k + step):
+                if 0 <= j < n:
+                    expect.append(j)
+        assert lists[k].tolist() == expect[:nn]
+
+
+def test_nn_lists_properties(orc):
+    inst = I.uniform_instance(60, 100, seed=9)  # small grid: many equal distances
+    lists = orc.nn_lists(inst.dist, 20)
+    for i in range(60):
+        row = lists[i]
+        assert i not in row and len(set(row.tolist())) == 20
+        dd = inst.dist[i, row]
+        assert np.all(np.diff(dd) >= 0)
+        # every city outside the list is at least as far as the last entry,
+        # and on equal distance has a larger index
+        outside = [j for j in range(60) if j != i and j not in row]
+        last = (dd[-1], row[-1])
+        assert all((inst.dist[i, j], j) > tuple(last) for j in outside)
+
+
+def test_nn_select_rules(orc):
+    from scipy.stats import chisquare
+    n = 7
+    w = np.array([0.0, 1.0, 4.0, 2.0, 8.0, 0.5, 3.0], np.float32)
+    lst = np.array([2, 5, 3], np.int32)
+    vis = np.zeros(n, np.uint8)
+    vis[0] = 1
+    # Eq. 1 restricted to the list: probabilities 4 : 0.5 : 2
+    counts = np.zeros(n, np.int64)
+    for i in range(30_000):
+        x = orc.philox4x32_10([1, i, 0, 0], [3, 0])
+        counts[orc.nn_select(lst, w, vis, (int(x[1]) << 32) | int(x[0]))] += 1
+    assert counts[[0, 1, 4, 6]].sum() == 0
+    p = np.array([4.0, 0.5, 2.0]) / 6.5
+    assert chisquare(counts[[2, 5, 3]], p * counts.sum()).pvalue > 0.01
+    # all list entries visited: the heaviest unvisited city (4), ties low
+    vis2 = vis.copy()
+    vis2[[2, 5, 3]] = 1
+    assert orc.nn_select(lst, w, vis2, 123) == 4
+    w2 = w.copy()
+    w2[4] = 3.0
+    assert orc.nn_select(lst, w2, vis2, 123) == 4  # 3.0 at 4 and 6: the lower index
+
+
+def test_nn_construction_tours_and_nn1_walk(orc):
+    inst = I.uniform_instance(40, 1000, seed=12)
+    h = orc.heta(inst.dist, 2.0)
+    ch = orc.choice(np.where(np.eye(40) > 0, 0, 0.1).astype(np.float32), h, 1.0)
+    tours, lens = orc.construct_nn(ch, inst.dist, 9, seed=3, iteration=0, nn=8)
+    for k in range(9):
+        t = tours[k]
+        assert sorted(t[:-1].tolist()) == list(range(40)) and t[-1] == t[0]
+        assert lens[k] == int(inst.dist[t[:-1], t[1:]].astype(np.int64).sum())
+    # nn = 1: the walk goes to the nearest city while it is unvisited and
+    # otherwise to the heaviest unvisited one; replay that rule by hand
+    lists = orc.nn_lists(inst.dist, 1)
+    t1, _ = orc.construct_nn(ch, inst.dist, 4, seed=3, iteration=0, nn=1)
+    for k in range(4):
+        seen = {int(t1[k, 0])}
+        for s in range(1, 40):
+            cur = int(t1[k, s - 1])
+            nxt = int(lists[cur, 0])
+            if nxt in seen:
+                cand = [j for j in range(40) if j not in seen]
+                nxt = max(cand, key=lambda j: (ch[cur, j], -j))
+            assert int(t1[k, s]) == nxt
+            seen.add(nxt)
