@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--warps-per-ant", type=int, default=0, help="0 = library default")
     ap.add_argument("--ants-per-cta", type=int, default=0, help="0 = library default")
     ap.add_argument("--lanes-per-ant", type=int, default=0, help="0 = library default (32)")
+    ap.add_argument("--nn", type=int, default=0,
+                    help="nearest-neighbour list length (0 = every unvisited city)")
     ap.add_argument("--selection", default="eq1", choices=["eq1", "data-parallel"],
                     help="eq1: Eq. 1 (default); data-parallel: the paper's product-argmax kernel")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -321,6 +323,8 @@ def run_ours(args, w, rank, world, local):
         aco.aco_set_option(h, aco.ACO_OPT_WARPS_PER_ANT, args.warps_per_ant)
     if args.selection == "data-parallel":
         aco.aco_set_option(h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
+    if args.nn:
+        aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, args.nn)
     if args.lanes_per_ant:
         aco.aco_set_option(h, aco.ACO_OPT_LANES_PER_ANT, args.lanes_per_ant)
     if args.ants_per_cta:
@@ -391,7 +395,7 @@ def run_ours(args, w, rank, world, local):
         "config": {"workload": w["name"], "n": n, "m": m, "alpha": w["alpha"],
                    "beta": w["beta"], "rho": w["rho"], "deposit": args.deposit,
                    "warps_per_ant": tiling[0], "ants_per_cta": tiling[1],
-                   "lanes_per_ant": tiling[2], "selection": args.selection,
+                   "lanes_per_ant": tiling[2], "selection": args.selection, "nn_list": args.nn,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed between steps (256 MB write)"},
         "construct_ant_steps_per_s": m * (n - 1) / (con_ms / 1e3),

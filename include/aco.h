@@ -80,6 +80,18 @@ extern "C" {
 #define ACO_OPT_LANES_PER_ANT 7 /* 0 (default) = 32; 8 or 16: 32/H ants share a
                                   warp (one warp per ant group)                */
 #define ACO_OPT_SELECTION 8    /* ACO_SELECT_* below; default ACO_SELECT_EQ1     */
+#define ACO_OPT_NN_LIST 9      /* 0 (default): every unvisited city is a
+                                  candidate.  k in [1, min(32, n-1)]: the
+                                  nearest-neighbour-list construction (Section
+                                  II; the paper's Table 2 versions 4-6 use 30):
+                                  list(i) = the k nearest cities of i (ties to
+                                  the lower index, in that order); an ant at i
+                                  samples Eq. 1 among the unvisited entries of
+                                  list(i) (the integer roulette in list order)
+                                  and, when all are visited, moves to the
+                                  unvisited city with the largest choice_info
+                                  value (ties to the lower index).  Needs
+                                  ACO_SELECT_EQ1; not available in pools.      */
 
 #define ACO_SELECT_EQ1 0       /* Eq. 1 (random proportional rule), exact      */
 #define ACO_SELECT_DATA_PARALLEL 1 /* the paper's data-parallel kernel (Section

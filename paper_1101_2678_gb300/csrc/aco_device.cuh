@@ -45,7 +45,14 @@ struct Instance {
   unsigned long long* acc;      // [n][ld] fixed-point accumulator (atomic u64 variant)
   int32_t* best_tour;           // [n + 1]
   IterState* st;
+  // Nearest-neighbour lists (optional; nn = 0: off): list(i) in nnlist[i][0..nn)
+  // (rows of kNnStride), and their choice_info values in list order.
+  int nn;
+  int32_t* nnlist;              // [n][kNnStride]
+  float* nnchoice;              // [n][kNnStride]
 };
+
+constexpr int kNnStride = 32;   // longest supported list
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32

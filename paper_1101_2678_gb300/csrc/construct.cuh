@@ -566,7 +566,9 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
   const int idx = blockIdx.x * groups_per_cta<G, H>(blockDim.x >> 5) + grp;
   if (idx >= count) return;
   const int2 it = items[idx];
-  const Instance I = insts[it.x];
+  // A reference into the descriptor table (read-only, L1-cached) rather than
+  // a register copy of the whole descriptor, which cost ~40 registers.
+  const Instance& I = insts[it.x];
   construct_ant<C, G, H>(I, it.y, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
                          reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes));
 }

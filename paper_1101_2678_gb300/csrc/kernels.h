@@ -55,6 +55,12 @@ cudaError_t launch_construct_rule1(const Instance& I, ConstructTiling t, cudaStr
 cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
                                    ConstructTiling t, cudaStream_t st);
 
+// Nearest-neighbour lists: build list(i) (nn <= kNnStride), refresh their
+// choice_info values, and the list-restricted construction.
+cudaError_t launch_nn_lists(const Instance& I, int nn, cudaStream_t st);
+cudaError_t launch_nn_choice(const Instance& I, cudaStream_t st);
+cudaError_t launch_construct_nn(const Instance& I, cudaStream_t st);
+
 // Batched best / gather update over device-side lists.
 cudaError_t launch_best_slots(const Instance* insts, const int* slots, int count, cudaStream_t st);
 cudaError_t launch_update_rows(const Instance* insts, const int2* rows, int count, int max_ld,

@@ -221,8 +221,7 @@ __global__ void deposit_atomic_f32_kernel(Instance I) {
 __global__ void best_slots_kernel(const Instance* __restrict__ insts, const int* __restrict__ slots,
                                   int count) {
   if ((int)blockIdx.x >= count) return;
-  const Instance I = insts[slots[blockIdx.x]];
-  best_body(I);
+  best_body(insts[slots[blockIdx.x]]);
 }
 
 __global__ void update_rows_kernel(const Instance* __restrict__ insts, const int2* __restrict__ rows,
@@ -233,7 +232,7 @@ __global__ void update_rows_kernel(const Instance* __restrict__ insts, const int
   const int idx = blockIdx.x * warps + wi;
   if (idx >= count) return;
   const int2 it = rows[idx];
-  const Instance I = insts[it.x];
+  const Instance& I = insts[it.x];
   if (it.y == 0 && lane == 0) I.st->iteration += 1;
   gather_row(I, it.y, acc_rows + (size_t)wi * max_ld, lane);
 }

@@ -329,3 +329,48 @@ def test_data_parallel_rule_run_bit_exact(aco, orc):
         assert np.array_equal(aco.aco_get_pheromone(c.h, 97), ref["tau32"])
         tour, best = aco.aco_best_tour(c.h, 97)
     assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+
+
+# ---------------------------------------------------------------------------
+# Nearest-neighbour-list construction (optional, ACO_OPT_NN_LIST)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,nn,m", [(10, 9, 12), (48, 8, 48), (300, 30, 64), (333, 1, 20)])
+def test_nn_list_tours_match_oracle(aco, orc, n, nn, m):
+    inst = I.clustered_instance(n, seed=n + nn, clusters=6, side=4000)
+    ch = oracle_initial_choice(orc, inst.dist, m)
+    ref_t, ref_l = orc.construct_nn(ch, inst.dist, m, seed=6, iteration=0, nn=nn)
+    with aco.Colony(inst.dist, m, seed=6) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, nn)
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+    assert np.array_equal(tours, ref_t) and np.array_equal(lens, ref_l)
+
+
+def test_nn_list_full_size_sampled(aco, orc):
+    w = I.workload_n1002()
+    d, m = w["inst"].dist, w["m"]
+    ch = oracle_initial_choice(orc, d, m)
+    with aco.Colony(d, m, seed=w["seed"]) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 30)
+        tours, lens = aco.aco_construct_tours(c.h, 1002, m)
+    check_tours(tours, lens, d)
+    ref_t, ref_l = orc.construct_nn(ch, d, 6, seed=w["seed"], iteration=0, nn=30)
+    assert np.array_equal(tours[:6], ref_t) and np.array_equal(lens[:6], ref_l)
+
+
+def test_nn_list_run_bit_exact_and_option_rules(aco, orc):
+    inst = I.uniform_instance(130, 1000, seed=77)
+    ref = orc.run(inst.dist, 60, 6, 5, rule=2, nn=20)
+    with aco.Colony(inst.dist, 60, seed=5) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 20)
+        aco.aco_iterate(c.h, 6)
+        assert np.array_equal(aco.aco_get_pheromone(c.h, 130), ref["tau32"])
+        tour, best = aco.aco_best_tour(c.h, 130)
+        assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+        assert aco.aco_kernel_launches_per_iteration(c.h) == 4
+        with pytest.raises(aco.AcoError):
+            aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
+        with pytest.raises(aco.AcoError):
+            aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 33)
+        aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 0)
+        assert aco.aco_get_option(c.h, aco.ACO_OPT_NN_LIST) == 0
