@@ -7,7 +7,7 @@ L2 is flushed by writing a 256 MB buffer (outside the timed region); each step
 is timed with CUDA events on the stream the library launches on.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n1002]
-                  [--deposit gather|u64|f32] [--impl ours|reference]
+                  [--deposit sym|gather|u64|f32] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the slow, plain restatement of the
 method used by the tests) on a bounded sample of the same workload.
@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="n1002", choices=sorted(WORKLOADS))
-    ap.add_argument("--deposit", default="gather", choices=["gather", "u64", "f32"])
+    ap.add_argument("--deposit", default="sym", choices=["gather", "u64", "f32", "sym"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -311,7 +311,7 @@ def run_ours(args, w, rank, world, local):
     d = w["inst"].dist
     n, m = d.shape[0], w["m"]
     dep = {"gather": aco.ACO_DEPOSIT_GATHER, "u64": aco.ACO_DEPOSIT_ATOMIC_U64,
-           "f32": aco.ACO_DEPOSIT_ATOMIC_F32}[args.deposit]
+           "f32": aco.ACO_DEPOSIT_ATOMIC_F32, "sym": aco.ACO_DEPOSIT_SYMMETRIC}[args.deposit]
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     col = aco.Colony(d, m, seed=w["seed"] + rank, alpha=w["alpha"], beta=w["beta"], rho=w["rho"])
@@ -378,6 +378,9 @@ def run_ours(args, w, rank, world, local):
         return
     peaks, peak_kind = measured_peaks()
     roof = construct_roofline(n, m, con_ms, peaks, peak_kind)
+    if not (args.nn or args.selection != "eq1" or args.lanes_per_ant or args.warps_per_ant
+            or args.ants_per_cta):
+        roof["traffic"], roof["traffic_source"] = recorded_traffic(w["name"])
     l2_gbs = measure_l2_copy_gbs()
     algo = roof["algorithmic_bytes_per_launch"]
     dense = 4.0 * m * (n - 1) * n
@@ -413,6 +416,41 @@ def run_ours(args, w, rank, world, local):
         line["cpu_baseline"] = {"value": v, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": desc}
     print(json.dumps(line), flush=True)
+
+
+CONSTRUCT_SOURCES = ("aco_device.cuh", "construct.cuh", "construct_g1h8.cu", "construct_g1h16.cu",
+                     "construct_g1h32.cu", "construct_g2h32.cu", "construct_g4h32.cu",
+                     "construct_rule1.cu")
+
+
+def construct_sources_sha256() -> str:
+    """SHA-256 over the construction kernel's sources, in a fixed order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in CONSTRUCT_SOURCES:
+        with open(os.path.join(ROOT, "paper_1101_2678_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes (read + write) per construct launch from a committed ncu capture.
+
+    The summaries under profiles/ carry a line
+    `traffic-record: workload=<name> dram_bytes_per_launch=<B> sources_sha256=<H>`;
+    the figure is used only if H equals the hash of the current sources (else
+    the counters describe another kernel and traffic is null)."""
+    import glob
+    sha = construct_sources_sha256()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "construct_kernel_*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                if not line.startswith("traffic-record:"):
+                    continue
+                kv = dict(x.split("=", 1) for x in line.split()[1:])
+                if kv.get("workload") == workload and kv.get("sources_sha256") == sha:
+                    return float(kv["dram_bytes_per_launch"]), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def construct_roofline(n, m, con_ms, peaks, peak_kind):

@@ -70,7 +70,8 @@ extern "C" {
 #define ACO_MAX_M 16384   /* ants per instance                               */
 
 /* ---- options (aco_set_option / aco_get_option) --------------------------- */
-#define ACO_OPT_DEPOSIT 1      /* ACO_DEPOSIT_* below; default GATHER           */
+#define ACO_OPT_DEPOSIT 1      /* ACO_DEPOSIT_* below; default SYMMETRIC (the
+                                  fastest measured on GB300)                  */
 #define ACO_OPT_STREAM 2       /* cudaStream_t as int64; 0 = the handle's own   */
 #define ACO_OPT_USE_GRAPH 3    /* 1 (default): aco_iterate replays a CUDA graph */
 #define ACO_OPT_PROFILE 4      /* 1: record CUDA events around every kernel     */
@@ -113,6 +114,16 @@ extern "C" {
                                   evaporation (the paper's atomic kernel; the
                                   order of additions, hence the last bits of
                                   tau, is not deterministic)                   */
+#define ACO_DEPOSIT_SYMMETRIC 3  /* the paper's "Reduction" version (Section
+                                  III-B): for the symmetric TSP the edge (a,b)
+                                  adds q_k once, to the upper-triangle cell
+                                  (min, max), with red.global.add.u64 (half the
+                                  atomics of ATOMIC_U64); the apply pass reads
+                                  tau, eta^beta and the accumulator in the
+                                  upper triangle only and writes both halves
+                                  of tau and choice_info through shared-memory
+                                  tiles.  Results equal GATHER and ATOMIC_U64
+                                  bit for bit.                                 */
 
 /* ---- phases reported by aco_get_kernel_times ------------------------------ */
 #define ACO_PHASE_CONSTRUCT 0  /* tour construction kernel                      */

@@ -40,6 +40,7 @@ ACO_SELECT_DATA_PARALLEL = 1
 ACO_DEPOSIT_GATHER = 0
 ACO_DEPOSIT_ATOMIC_U64 = 1
 ACO_DEPOSIT_ATOMIC_F32 = 2
+ACO_DEPOSIT_SYMMETRIC = 3
 
 ACO_PHASE_CONSTRUCT = 0
 ACO_PHASE_BEST = 1

@@ -148,7 +148,7 @@ struct aco_colony {
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   int sms = 148;
-  int deposit = kDepositGather;
+  int deposit = kDepositSymmetric;
   int use_graph = 1;
   int profile = 0;
   int warps_per_ant = 0;
@@ -550,7 +550,7 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
   if (!h) return fail(ACO_EINVAL, "NULL handle");
   switch (key) {
     case ACO_OPT_DEPOSIT:
-      if (value < 0 || value > 2) return fail(ACO_EINVAL, "deposit variant %lld", (long long)value);
+      if (value < 0 || value > 3) return fail(ACO_EINVAL, "deposit variant %lld", (long long)value);
       h->deposit = (int)value;
       break;
     case ACO_OPT_STREAM:

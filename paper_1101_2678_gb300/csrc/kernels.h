@@ -10,6 +10,7 @@ namespace aco {
 constexpr int kDepositGather = 0;
 constexpr int kDepositAtomicU64 = 1;
 constexpr int kDepositAtomicF32 = 2;
+constexpr int kDepositSymmetric = 3;
 
 // Tiling of the construction kernel: C cities per thread, G warps per ant
 // group, H lanes per ant (H < 32: 32/H ants share a warp, G = 1), W warps

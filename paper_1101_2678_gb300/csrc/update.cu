@@ -2,6 +2,8 @@
 // Section III-B for the atomic and scatter-to-gather designs).
 #include <climits>
 
+#include "../../include/aco.h"
+
 #include "aco_device.cuh"
 #include "kernels.h"
 #include "update.cuh"
@@ -13,69 +15,77 @@ namespace aco {
 // ---------------------------------------------------------------------------
 
 // Nearest-neighbour tour from city 0 (ties to the lower index), C_nn and
-// tau0 = m / C_nn.  One CTA; the cities of a row are strided over its threads.
-__global__ void nn_tour_kernel(Instance I) {
-  extern __shared__ uint32_t seen[];
-  __shared__ long long red_d[32];
-  __shared__ int red_j[32];
-  __shared__ int s_next;
+// tau0 = m / C_nn.  One CTA of kNnTourThreads threads; thread t owns the
+// cities 4t + 4*kNnTourThreads*r + e (e < 4), reads them with one 16-byte
+// load per r and keeps their visited bits in a register.  Each step takes
+// the minimum of the key (d << 32 | j) (lexicographic (d, j): ties to the
+// lower index) over the unvisited cities: a warp butterfly, then the warps'
+// minima through double-buffered shared memory, one barrier per step.
+constexpr int kNnTourThreads = 256;
+constexpr int kNnTourRounds = (ACO_MAX_N + 4 * kNnTourThreads - 1) / (4 * kNnTourThreads);
+
+__global__ void __launch_bounds__(kNnTourThreads) nn_tour_kernel(Instance I) {
+  __shared__ unsigned long long wmin[2][kNnTourThreads / 32];
   const int n = I.n, ld = I.ld;
-  const int words = (n + 31) / 32;
-  for (int w = threadIdx.x; w < words; w += blockDim.x) seen[w] = 0;
-  __syncthreads();
-  if (threadIdx.x == 0) seen[0] = 1u;
-  __syncthreads();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int kWarps = kNnTourThreads / 32;
+  uint32_t visited = 0;  // bit 4r + e: city 4t + 4*kNnTourThreads*r + e
+#pragma unroll
+  for (int r = 0; r < kNnTourRounds; ++r)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 4 * t + 4 * kNnTourThreads * r + e;
+      if (j >= n || j == 0) visited |= 1u << (4 * r + e);
+    }
   int cur = 0;
   long long len = 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int s = 1; s < n; ++s) {
-    long long bd = LLONG_MAX;
-    int bj = INT_MAX;
     const int32_t* row = I.dist + (size_t)cur * ld;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      if ((seen[j >> 5] >> (j & 31)) & 1u) continue;
-      const long long dj = row[j];
-      if (dj < bd) {
-        bd = dj;
-        bj = j;
+    int4 d4[kNnTourRounds];
+#pragma unroll
+    for (int r = 0; r < kNnTourRounds; ++r) {
+      const int j0 = 4 * t + 4 * kNnTourThreads * r;
+      // ld is a multiple of 4, so a 16-byte load that starts below n ends below ld
+      d4[r] = j0 < n ? *reinterpret_cast<const int4*>(row + j0) : make_int4(0, 0, 0, 0);
+    }
+    unsigned long long key = ~0ull;
+#pragma unroll
+    for (int r = 0; r < kNnTourRounds; ++r) {
+      const int j0 = 4 * t + 4 * kNnTourThreads * r;
+      const int dv[4] = {d4[r].x, d4[r].y, d4[r].z, d4[r].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const unsigned long long k =
+            ((unsigned long long)(uint32_t)dv[e] << 32) | (uint32_t)(j0 + e);
+        if (!((visited >> (4 * r + e)) & 1u) && k < key) key = k;
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const long long od = __shfl_xor_sync(FULL, bd, o);
-      const int oj = __shfl_xor_sync(FULL, bj, o);
-      if (od < bd || (od == bd && oj < bj)) {
-        bd = od;
-        bj = oj;
-      }
+      const unsigned long long other = __shfl_xor_sync(FULL, key, o);
+      key = other < key ? other : key;
     }
-    if (lane == 0) {
-      red_d[warp] = bd;
-      red_j[warp] = bj;
-    }
+    if (lane == 0) wmin[s & 1][warp] = key;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      long long d0 = red_d[0];
-      int j0 = red_j[0];
-      for (int w = 1; w < nwarps; ++w)
-        if (red_d[w] < d0 || (red_d[w] == d0 && red_j[w] < j0)) {
-          d0 = red_d[w];
-          j0 = red_j[w];
-        }
-      if ((unsigned)j0 >= (unsigned)n) {  // cannot happen while a city is unvisited
-        atomicOr(&I.st->status, kStatusBadTour);
-        j0 = 0;
-      }
-      s_next = j0;
-      seen[j0 >> 5] |= 1u << (j0 & 31);
+    key = wmin[s & 1][0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) {
+      const unsigned long long other = wmin[s & 1][w];
+      key = other < key ? other : key;
     }
-    __syncthreads();
-    const int nx = s_next;
-    len += row[nx];
-    cur = nx;
+    int next = (int)(uint32_t)key;
+    if (key == ~0ull || next >= n) {  // cannot happen while a city is unvisited
+      if (t == 0) atomicOr(&I.st->status, kStatusBadTour);
+      next = 0;
+    }
+    const int rel = next - 4 * t;
+    if (rel >= 0 && (rel % (4 * kNnTourThreads)) < 4)
+      visited |= 1u << (4 * (rel / (4 * kNnTourThreads)) + (rel % (4 * kNnTourThreads)));
+    len += (long long)(key >> 32);
+    cur = next;
   }
-  len += I.dist[(size_t)cur * ld];
-  if (threadIdx.x == 0) {
+  if (t == 0) {
+    len += I.dist[(size_t)cur * ld];
     I.st->nn_len = len;
     I.st->tau0 = (float)((double)I.m / (double)len);
   }
@@ -184,6 +194,72 @@ __global__ void apply_acc_kernel(Instance I, int bump_iteration) {
   if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
 }
 
+// Symmetric form of the two kernels above (the paper's "Reduction" version,
+// Section III-B: the symmetric TSP needs only half of the pheromone cells).
+// The tour edge (a, b) adds q_k once, to acc[min(a,b)][max(a,b)]: half the
+// atomics of the full form.  The apply pass then reads tau, eta^beta and acc
+// only in the upper triangle and writes both halves of tau and choice_info.
+// tau and eta^beta are symmetric bit for bit (the same arithmetic on the same
+// operands in both halves), so the result equals the full form's exactly.
+__global__ void deposit_symmetric_kernel(Instance I) {
+  const int n = I.n, ld = I.ld;
+  const size_t total = (size_t)I.m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / n), s = (int)(e % n);
+    const int32_t* t = I.tours + (size_t)k * I.ldt;
+    const int a = t[s], b = t[s + 1];
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    atomicAdd(I.acc + (size_t)lo * ld + hi, I.q[k]);
+  }
+}
+
+// One CTA of 32 x 8 threads per 32 x 32 tile (bi, bj), bi <= bj, of the upper
+// triangle: each thread updates four cells (i, j), j > i, with coalesced
+// row accesses, and the tile's new tau and choice_info go through shared
+// memory to the mirrored tile (bj, bi), written with coalesced rows as well.
+constexpr int kSymTile = 32;
+
+__global__ void __launch_bounds__(256) apply_symmetric_kernel(Instance I, int bump_iteration) {
+  __shared__ float tile_tau[kSymTile][kSymTile + 1];
+  __shared__ float tile_ch[kSymTile][kSymTile + 1];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bump_iteration && bi == 0 && bj == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    I.st->iteration += 1;
+  if (bi > bj) return;
+  const int n = I.n, ld = I.ld;
+  const float keep = __fsub_rn(1.0f, I.rho);
+  const float inv = inv_scale_of(I.st->deposit_shift);
+  const float alpha = I.alpha;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j = bj * kSymTile + tx;
+#pragma unroll
+  for (int r = 0; r < kSymTile; r += 8) {
+    const int i = bi * kSymTile + ty + r;
+    if (i < n && j < n && j > i) {
+      const size_t e = (size_t)i * ld + j;
+      const float t = apply_deposit(I.tau[e], I.acc[e], keep, inv);
+      const float c = choice_of(t, I.heta[e], alpha);
+      I.tau[e] = t;
+      I.choice[e] = c;
+      I.acc[e] = 0ull;
+      tile_tau[ty + r][tx] = t;
+      tile_ch[ty + r][tx] = c;
+    }
+  }
+  __syncthreads();
+  const int jt = bi * kSymTile + tx;  // column of the mirrored tile
+#pragma unroll
+  for (int r = 0; r < kSymTile; r += 8) {
+    const int it = bj * kSymTile + ty + r;  // row of the mirrored tile
+    if (it < n && jt < n && jt < it) {
+      const size_t e = (size_t)it * ld + jt;
+      I.tau[e] = tile_tau[tx][ty + r];
+      I.choice[e] = tile_ch[tx][ty + r];
+    }
+  }
+}
+
 // The paper's atomic kernel: evaporation first (Eq. 2) ...
 __global__ void evaporate_kernel(Instance I) {
   const size_t total4 = (size_t)I.n * I.ld / 4;
@@ -269,10 +345,7 @@ static int grid_for(size_t work, int threads, int sms) {
 }
 
 cudaError_t launch_setup(const Instance& I, int sms, cudaStream_t st) {
-  int threads = 32 * ((I.n + 31) / 32);
-  if (threads > 1024) threads = 1024;
-  const size_t smem = sizeof(uint32_t) * ((I.n + 31) / 32);
-  nn_tour_kernel<<<1, threads, smem, st>>>(I);
+  nn_tour_kernel<<<1, kNnTourThreads, 0, st>>>(I);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   init_matrices_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I);
@@ -329,6 +402,8 @@ int gather_warps_per_cta(int ld) {
 cudaError_t launch_deposit(const Instance& I, int variant, int sms, cudaStream_t st) {
   if (variant == kDepositAtomicU64) {
     deposit_atomic_u64_kernel<<<grid_for((size_t)I.m * I.n, 256, sms), 256, 0, st>>>(I);
+  } else if (variant == kDepositSymmetric) {
+    deposit_symmetric_kernel<<<grid_for((size_t)I.m * I.n, 256, sms), 256, 0, st>>>(I);
   } else if (variant == kDepositAtomicF32) {
     evaporate_kernel<<<grid_for((size_t)I.n * I.ld / 4, 256, sms), 256, 0, st>>>(I);
     cudaError_t e = cudaGetLastError();
@@ -351,6 +426,9 @@ cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t 
     update_gather_kernel<<<(I.n + w - 1) / w, 32 * w, smem, st>>>(I, 1);
   } else if (variant == kDepositAtomicU64) {
     apply_acc_kernel<<<grid_for((size_t)I.n * I.ld / 4, 256, sms), 256, 0, st>>>(I, 1);
+  } else if (variant == kDepositSymmetric) {
+    const int nb = (I.n + kSymTile - 1) / kSymTile;
+    apply_symmetric_kernel<<<dim3(nb, nb), dim3(kSymTile, 8), 0, st>>>(I, 1);
   } else {
     choice_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I, 1);
   }
@@ -360,7 +438,7 @@ cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t 
 int launches_for_variant(int variant) {
   // construct + best + deposit kernels + update kernel
   if (variant == kDepositGather) return 3;
-  if (variant == kDepositAtomicU64) return 4;
+  if (variant == kDepositAtomicU64 || variant == kDepositSymmetric) return 4;
   return 5;
 }
 

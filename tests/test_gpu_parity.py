@@ -154,7 +154,7 @@ def test_chi_squared_first_move_on_gpu(aco, orc):
 # Pheromone update (Eqs. 2-4) and whole runs
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("deposit", ["GATHER", "ATOMIC_U64"])
+@pytest.mark.parametrize("deposit", ["GATHER", "ATOMIC_U64", "SYMMETRIC"])
 def test_n48_hundred_iterations_bit_exact(aco, orc, deposit):
     w = I.workload_n48()
     d = w["inst"].dist
@@ -215,13 +215,52 @@ def test_float_atomic_deposit_within_rounding_bound(aco, orc):
 def test_deposit_variants_agree(aco):
     inst = I.uniform_instance(333, 1000, seed=8)
     out = {}
-    for v in ["GATHER", "ATOMIC_U64"]:
+    for v in ["GATHER", "ATOMIC_U64", "SYMMETRIC"]:
         with aco.Colony(inst.dist, 333, seed=9) as c:
             aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, getattr(aco, "ACO_DEPOSIT_" + v))
             aco.aco_iterate(c.h, 8)
-            out[v] = (aco.aco_get_pheromone(c.h, 333), aco.aco_best_tour(c.h, 333))
-    assert np.array_equal(out["GATHER"][0], out["ATOMIC_U64"][0])
-    assert out["GATHER"][1][1] == out["ATOMIC_U64"][1][1]
+            out[v] = (aco.aco_get_pheromone(c.h, 333), aco.aco_best_tour(c.h, 333),
+                      aco.aco_choice_info(c.h, 333))
+    for v in ["ATOMIC_U64", "SYMMETRIC"]:
+        assert np.array_equal(out["GATHER"][0], out[v][0]), v
+        assert np.array_equal(out["GATHER"][2], out[v][2]), v
+        assert out["GATHER"][1][1] == out[v][1][1], v
+
+
+# The upper-triangle update works on 32 x 32 tiles: sizes below, at and
+# around tile multiples, and a few iterations against the oracle.
+@pytest.mark.parametrize("n,m,iters", [(3, 2, 3), (31, 31, 5), (32, 20, 5), (33, 33, 5),
+                                       (64, 64, 4), (97, 50, 4), (257, 100, 3)])
+def test_symmetric_update_bit_exact(aco, orc, n, m, iters):
+    inst = I.uniform_instance(n, 1000, seed=600 + n)
+    ref = orc.run(inst.dist, m, iters, 13)
+    with aco.Colony(inst.dist, m, seed=13) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, aco.ACO_DEPOSIT_SYMMETRIC)
+        aco.aco_iterate(c.h, iters)
+        tau = aco.aco_get_pheromone(c.h, n)
+        ch = aco.aco_choice_info(c.h, n)
+        tour, best = aco.aco_best_tour(c.h, n)
+    assert np.array_equal(tau, ref["tau32"])
+    assert np.array_equal(ch, orc.choice(ref["tau32"], orc.heta(inst.dist, 2.0), 1.0))
+    assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+
+
+@pytest.mark.parametrize("wl", ["workload_n1002", "workload_n2392"])
+def test_symmetric_update_full_size_equals_gather(aco, wl):
+    # The bench's configurations: two iterations with each deterministic
+    # variant give the same tau and choice_info (the gather variant is the
+    # one held bit-exact to the oracle above).
+    w = getattr(I, wl)()
+    d, m = w["inst"].dist, w["m"]
+    n = d.shape[0]
+    out = {}
+    for v in ["GATHER", "SYMMETRIC"]:
+        with aco.Colony(d, m, seed=w["seed"]) as c:
+            aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, getattr(aco, "ACO_DEPOSIT_" + v))
+            aco.aco_iterate(c.h, 2)
+            out[v] = (aco.aco_get_pheromone(c.h, n), aco.aco_choice_info(c.h, n))
+    assert np.array_equal(out["GATHER"][0], out["SYMMETRIC"][0])
+    assert np.array_equal(out["GATHER"][1], out["SYMMETRIC"][1])
 
 
 def test_update_invariants_at_full_size(aco):
@@ -291,6 +330,11 @@ def test_profiled_phase_times(aco):
         aco.aco_iterate(c.h, 2)
         t = aco.aco_get_kernel_times(c.h)
         assert t[aco.ACO_PHASE_CONSTRUCT] > 0 and t[aco.ACO_PHASE_UPDATE] > 0
+        # default (symmetric) update: construct, best, deposit, apply
+        assert aco.aco_get_option(c.h, aco.ACO_OPT_DEPOSIT) == aco.ACO_DEPOSIT_SYMMETRIC
+        assert t[aco.ACO_PHASE_DEPOSIT] > 0
+        assert aco.aco_kernel_launches_per_iteration(c.h) == 4
+        aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, aco.ACO_DEPOSIT_GATHER)
         assert aco.aco_kernel_launches_per_iteration(c.h) == 3
 
 
@@ -367,7 +411,7 @@ def test_nn_list_run_bit_exact_and_option_rules(aco, orc):
         assert np.array_equal(aco.aco_get_pheromone(c.h, 130), ref["tau32"])
         tour, best = aco.aco_best_tour(c.h, 130)
         assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
-        assert aco.aco_kernel_launches_per_iteration(c.h) == 4
+        assert aco.aco_kernel_launches_per_iteration(c.h) == 5
         with pytest.raises(aco.AcoError):
             aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
         with pytest.raises(aco.AcoError):
