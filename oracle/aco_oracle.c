@@ -68,6 +68,20 @@
  *     is visited it moves to the unvisited city with the largest weight,
  *     ties to the lower index.
  *
+ *  R13 (optional variant) the MAX-MIN Ant System, which the paper cites as an
+ *     earlier GPU target (Section II-B) and which stands for the "other ACO
+ *     algorithms" of its future work (Section V); the variant is the one of
+ *     Stutzle and Hoos, "MAX-MIN Ant System", Future Generation Computer
+ *     Systems 16 (2000).  One tour deposits per iteration (the iteration
+ *     best, or the best-so-far tour): dtau = (float)(1 / (double)C) on its n
+ *     edges, both directions; every tau_ij (i != j) is then clamped into
+ *     [tau_min, tau_max].  tau_max = 1 / (rho C_gb), C_gb the best-so-far
+ *     length (the limit of repeated deposits on one tour); tau_min =
+ *     tau_max * f, f = (1 - p^(1/n)) / ((n/2 - 1) p^(1/n)) with p = p_best,
+ *     and tau_min = tau_max where that is larger.  Both limits are computed
+ *     in double in this order and rounded to float once; the trails start at
+ *     tau_max computed from C_nn.  tau' = clamp(fl(fl((1-rho) tau) + dtau)).
+ *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared -lm.
  * -ffp-contract=off matters: a fused multiply-add would change the rounding of
  * fl(fl(a*b)+c).
@@ -561,6 +575,146 @@ int orc_run_nn(int n, const int32_t *d, float alpha, float beta, float rho, int 
     if (last_lens) memcpy(last_lens, lens, (size_t)m * sizeof(int64_t));
     (void)h64;
     free(heta); free(h64); free(tau); free(tau64); free(choice); free(tours); free(lens);
+    free(lists);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* MAX-MIN Ant System (reading R13).                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Trail limits for best-so-far length c_gb, in double, each rounded once.  */
+void orc_mmas_limits(int n, float rho, double p_best, int64_t c_gb, float *tau_min,
+                     float *tau_max)
+{
+    double tmax = 1.0 / ((double)rho * (double)c_gb);
+    double root = pow(p_best, 1.0 / (double)n);
+    double f = (1.0 - root) / (((double)n / 2.0 - 1.0) * root);
+    double tmin = tmax * f;
+    if (tmin > tmax) tmin = tmax;
+    *tau_max = (float)tmax;
+    *tau_min = (float)tmin;
+}
+
+static void mmas_limits64(int n, double rho, double p_best, int64_t c_gb, double *tau_min,
+                          double *tau_max)
+{
+    double tmax = 1.0 / (rho * (double)c_gb);
+    double root = pow(p_best, 1.0 / (double)n);
+    double tmin = tmax * ((1.0 - root) / (((double)n / 2.0 - 1.0) * root));
+    *tau_max = tmax;
+    *tau_min = tmin > tmax ? tmax : tmin;
+}
+
+/* One MMAS update in float: evaporation of every cell, dtau on the n edges
+ * of dep_tour (n+1 entries, length dep_len) in both directions, then the
+ * clamp of every off-diagonal cell.  In a closed tour of n >= 3 cities every
+ * edge occurs once, so every cell receives at most one dtau. */
+void orc_update_mmas(int n, const int32_t *dep_tour, int64_t dep_len, float rho, float tau_min,
+                     float tau_max, float *tau)
+{
+    float keep = 1.0f - rho;
+    float dtau = (float)(1.0 / (double)dep_len);
+    for (size_t c = 0; c < (size_t)n * n; ++c) tau[c] = keep * tau[c];
+    for (int s = 0; s < n; ++s) {
+        int a = dep_tour[s], b = dep_tour[s + 1];
+        tau[(size_t)a * n + b] = tau[(size_t)a * n + b] + dtau;
+        tau[(size_t)b * n + a] = tau[(size_t)b * n + a] + dtau;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            if (i == j) continue;
+            float *t = &tau[(size_t)i * n + j];
+            if (*t < tau_min) *t = tau_min;
+            if (*t > tau_max) *t = tau_max;
+        }
+}
+
+static void update_mmas64(int n, const int32_t *dep_tour, int64_t dep_len, double rho,
+                          double tau_min, double tau_max, double *tau)
+{
+    for (size_t c = 0; c < (size_t)n * n; ++c) tau[c] = (1.0 - rho) * tau[c];
+    for (int s = 0; s < n; ++s) {
+        int a = dep_tour[s], b = dep_tour[s + 1];
+        tau[(size_t)a * n + b] += 1.0 / (double)dep_len;
+        tau[(size_t)b * n + a] += 1.0 / (double)dep_len;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            if (i == j) continue;
+            double *t = &tau[(size_t)i * n + j];
+            if (*t < tau_min) *t = tau_min;
+            if (*t > tau_max) *t = tau_max;
+        }
+}
+
+/* A whole MMAS run (construction as in orc_run_nn: rule 0/1/2, nn).  Extra
+ * output limits[2] = (tau_min, tau_max) after the last iteration. */
+int orc_run_mmas(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+                 uint64_t seed, int iterations, int rule, int nn, double p_best, int best_so_far,
+                 int32_t *best_tour, int64_t *best_len, float *tau32_out, double *tau64_out,
+                 int32_t *last_tours, int64_t *last_lens, int64_t *iter_best, float *limits)
+{
+    if (n < 3) return -1;
+    int32_t *lists = NULL;
+    if (rule == 2) {
+        if (nn < 1 || nn > 32 || nn > n - 1) return -1;
+        lists = (int32_t *)malloc((size_t)n * nn * sizeof(int32_t));
+        if (!lists) return -2;
+        orc_nn_lists(n, d, nn, lists);
+    }
+    size_t cells = (size_t)n * n;
+    float *heta = (float *)malloc(cells * sizeof(float));
+    float *tau = (float *)malloc(cells * sizeof(float));
+    double *tau64 = (double *)malloc(cells * sizeof(double));
+    float *choice = (float *)malloc(cells * sizeof(float));
+    int32_t *tours = (int32_t *)malloc((size_t)m * (n + 1) * sizeof(int32_t));
+    int64_t *lens = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    int32_t *gb = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    if (!heta || !tau || !tau64 || !choice || !tours || !lens || !gb) return -2;
+
+    orc_heta(n, d, (double)beta, heta);
+    int64_t cnn = orc_nn_tour_length(n, d);
+    float tmin, tmax;
+    double tmin64, tmax64;
+    orc_mmas_limits(n, rho, p_best, cnn, &tmin, &tmax);
+    mmas_limits64(n, (double)rho, p_best, cnn, &tmin64, &tmax64);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            tau[(size_t)i * n + j] = (i == j) ? 0.0f : tmax;
+            tau64[(size_t)i * n + j] = (i == j) ? 0.0 : tmax64;
+        }
+
+    int64_t best = INT64_MAX;
+    for (int it = 0; it < iterations; ++it) {
+        orc_choice(n, tau, heta, alpha, choice);
+        orc_construct_nn(n, m, choice, d, seed, (uint32_t)it, rule, nn, lists, tours, lens);
+        int kbest = 0;
+        for (int k = 1; k < m; ++k)
+            if (lens[k] < lens[kbest]) kbest = k;
+        if (iter_best) iter_best[it] = lens[kbest];
+        if (lens[kbest] < best) {
+            best = lens[kbest];
+            memcpy(gb, tours + (size_t)kbest * (n + 1), (size_t)(n + 1) * sizeof(int32_t));
+        }
+        orc_mmas_limits(n, rho, p_best, best, &tmin, &tmax);
+        mmas_limits64(n, (double)rho, p_best, best, &tmin64, &tmax64);
+        const int32_t *dep = best_so_far ? gb : tours + (size_t)kbest * (n + 1);
+        int64_t dep_len = best_so_far ? best : lens[kbest];
+        orc_update_mmas(n, dep, dep_len, rho, tmin, tmax, tau);
+        update_mmas64(n, dep, dep_len, (double)rho, tmin64, tmax64, tau64);
+    }
+    if (best_len) *best_len = best;
+    if (best_tour && iterations > 0) memcpy(best_tour, gb, (size_t)(n + 1) * sizeof(int32_t));
+    if (tau32_out) memcpy(tau32_out, tau, cells * sizeof(float));
+    if (tau64_out) memcpy(tau64_out, tau64, cells * sizeof(double));
+    if (last_tours) memcpy(last_tours, tours, (size_t)m * (n + 1) * sizeof(int32_t));
+    if (last_lens) memcpy(last_lens, lens, (size_t)m * sizeof(int64_t));
+    if (limits) {
+        limits[0] = tmin;
+        limits[1] = tmax;
+    }
+    free(heta); free(tau); free(tau64); free(choice); free(tours); free(lens); free(gb);
     free(lists);
     return 0;
 }

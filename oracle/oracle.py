@@ -101,6 +101,15 @@ def lib():
                                      C.c_uint64, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp,
                                      vp, vp]
             L.orc_run_nn.restype = C.c_int
+            L.orc_mmas_limits.argtypes = [C.c_int, C.c_float, C.c_double, C.c_int64, f32p, f32p]
+            L.orc_mmas_limits.restype = None
+            L.orc_update_mmas.argtypes = [C.c_int, i32p, C.c_int64, C.c_float, C.c_float,
+                                          C.c_float, f32p]
+            L.orc_update_mmas.restype = None
+            L.orc_run_mmas.argtypes = [C.c_int, i32p, C.c_float, C.c_float, C.c_float, C.c_int,
+                                       C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                       vp, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_run_mmas.restype = C.c_int
             L.orc_brute_force.argtypes = [C.c_int, i32p, i32p]
             L.orc_brute_force.restype = C.c_int64
             _lib = L
@@ -237,6 +246,48 @@ def update_fp64(tau, tours, lens, rho: float) -> np.ndarray:
     lens = np.ascontiguousarray(lens, np.int64)
     lib().orc_update_fp64(tau.shape[0], tours.shape[0], tours, lens, float(rho), tau)
     return tau
+
+
+def mmas_limits(n: int, rho: float, p_best: float, c_gb: int):
+    """(tau_min, tau_max) of the MAX-MIN Ant System for best-so-far length c_gb (R13)."""
+    lo = np.zeros(1, np.float32)
+    hi = np.zeros(1, np.float32)
+    lib().orc_mmas_limits(int(n), float(rho), float(p_best), int(c_gb), lo, hi)
+    return float(lo[0]), float(hi[0])
+
+
+def update_mmas(tau, dep_tour, dep_len: int, rho: float, tau_min: float, tau_max: float):
+    """One MMAS update of a copy of tau (float): the tour dep_tour deposits, then the clamp."""
+    tau = np.array(tau, dtype=np.float32, copy=True, order="C")
+    lib().orc_update_mmas(tau.shape[0], _i32(dep_tour), int(dep_len), float(rho),
+                          float(tau_min), float(tau_max), tau)
+    return tau
+
+
+def run_mmas(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.02,
+             p_best=0.05, best_so_far=False, rule: int = 0, nn: int = 0) -> dict:
+    """A whole MAX-MIN Ant System run (R13), float state with fp64 carried alongside."""
+    d = _i32(dist)
+    n = d.shape[0]
+    best_tour = np.zeros(n + 1, np.int32)
+    best_len = np.zeros(1, np.int64)
+    tau32 = np.zeros((n, n), np.float32)
+    tau64 = np.zeros((n, n), np.float64)
+    tours = np.zeros((m, n + 1), np.int32)
+    lens = np.zeros(m, np.int64)
+    iter_best = np.zeros(max(iterations, 1), np.int64)
+    limits = np.zeros(2, np.float32)
+    rc = lib().orc_run_mmas(n, d, float(alpha), float(beta), float(rho), int(m),
+                            C.c_uint64(seed), int(iterations), int(rule), int(nn),
+                            float(p_best), int(bool(best_so_far)),
+                            best_tour.ctypes.data, best_len.ctypes.data, tau32.ctypes.data,
+                            tau64.ctypes.data, tours.ctypes.data, lens.ctypes.data,
+                            iter_best.ctypes.data, limits.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle MMAS run failed")
+    return dict(best_tour=best_tour, best_len=int(best_len[0]), tau32=tau32, tau64=tau64,
+                tours=tours, lens=lens, iter_best=iter_best[:iterations],
+                tau_min=float(limits[0]), tau_max=float(limits[1]))
 
 
 def run(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.5,

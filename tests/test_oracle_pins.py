@@ -486,3 +486,94 @@ def test_nn_construction_tours_and_nn1_walk(orc):
                 nxt = max(cand, key=lambda j: (ch[cur, j], -j))
             assert int(t1[k, s]) == nxt
             seen.add(nxt)
+
+
+# --------------------------------------------------------------------------
+# MAX-MIN Ant System (reading R13: Stutzle and Hoos 2000)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,rho,p,c", [(48, 0.02, 0.05, 33523), (1002, 0.2, 0.05, 259045),
+                                       (100, 0.5, 0.005, 21282)])
+def test_mmas_limits_properties(orc, n, rho, p, c):
+    lo, hi = orc.mmas_limits(n, rho, p, c)
+    # tau_max is the limit of repeated deposits of 1/C on one tour under
+    # evaporation: x <- (1 - rho) x + 1/C, iterated to its fixed point
+    x = 0.0
+    for _ in range(20000):
+        x = (1.0 - rho) * x + 1.0 / c
+    assert abs(hi - x) <= 2.0 ** -23 * x
+    # tau_min makes the probability of choosing the tau_max edge at each of
+    # n steps among n/2 candidates (the others at tau_min) multiply to p_best
+    pdec = hi / (hi + (n / 2.0 - 1.0) * lo)
+    assert abs(pdec ** n / p - 1.0) < 1e-5
+    assert 0.0 < lo < hi
+
+
+def test_mmas_limits_collapse_for_tiny_instances(orc):
+    # n = 3, p = 0.05: the formula gives tau_min > tau_max; tau_min = tau_max
+    lo, hi = orc.mmas_limits(3, 0.1, 0.05, 60)
+    assert lo == hi == np.float32(1.0 / (0.1 * 60))
+    lo, hi = orc.mmas_limits(12, 0.1, 0.05, 60)
+    assert lo < hi
+
+
+def test_mmas_update_closed_form(orc):
+    # Uniform trails c = 0.25 off the diagonal, rho = 1/2, one tour of
+    # length 8 deposits 1/8 = 0.125 on its edges (both directions):
+    #   unclamped: on-tour 0.125 + 0.125 = 0.25, off-tour 0.125;
+    #   [0.15, 0.3]: off-tour raised to 0.15, on-tour 0.25 (a clamp before
+    #   the deposit would give 0.275);
+    #   [0.15, 0.2]: on-tour lowered to 0.2.
+    n = 6
+    tour = np.array([0, 3, 1, 5, 2, 4, 0], np.int32)
+    on = np.zeros((n, n), bool)
+    for a, b in zip(tour[:-1], tour[1:]):
+        on[a, b] = on[b, a] = True
+    tau = np.full((n, n), 0.25, np.float32)
+    np.fill_diagonal(tau, 0)
+    off = ~on & ~np.eye(n, dtype=bool)
+    for lo, hi, v_on, v_off in [(0.01, 1.0, 0.25, 0.125), (0.15, 0.3, 0.25, 0.15),
+                                (0.15, 0.2, 0.2, 0.15)]:
+        out = orc.update_mmas(tau, tour, 8, 0.5, lo, hi)
+        assert np.all(out[on] == np.float32(v_on)) and np.all(out[off] == np.float32(v_off))
+        assert np.all(np.diag(out) == 0)
+    # rho = 0.25 keeps 3/4 (catches rho vs 1 - rho): off-tour 0.1875
+    out = orc.update_mmas(tau, tour, 8, 0.25, 0.01, 1.0)
+    assert np.all(out[off] == np.float32(0.1875)) and np.all(out[on] == np.float32(0.3125))
+
+
+@pytest.mark.parametrize("best_so_far", [False, True])
+def test_mmas_run_bounds_and_depositing_tour(orc, best_so_far):
+    n, m, its = 40, 40, 60
+    inst = I.uniform_instance(n, 1000, seed=21)
+    kw = dict(rho=0.3, p_best=0.05, best_so_far=best_so_far)
+    prev = orc.run_mmas(inst.dist, m, its - 1, 5, **kw)
+    last = orc.run_mmas(inst.dist, m, its, 5, **kw)
+    tau, lo, hi = last["tau32"], last["tau_min"], last["tau_max"]
+    offd = ~np.eye(n, dtype=bool)
+    assert np.all(tau[offd] >= lo) and np.all(tau[offd] <= hi) and np.all(np.diag(tau) == 0)
+    assert np.array_equal(tau, tau.T) and lo > 2.0 ** -126
+    assert (lo, hi) == orc.mmas_limits(n, 0.3, 0.05, last["best_len"])
+    # cells that changed other than by evaporation and the clamp lie on the
+    # depositing tour: the last iteration's best ant, or the best-so-far tour
+    evap = np.clip((np.float32(0.7) * prev["tau32"]).astype(np.float32), lo, hi)
+    changed = (tau != evap) & offd
+    if best_so_far:
+        dep = last["best_tour"]
+    else:
+        dep = last["tours"][int(np.argmin(last["lens"]))]
+    on = np.zeros((n, n), bool)
+    for a, b in zip(dep[:-1], dep[1:]):
+        on[a, b] = on[b, a] = True
+    assert changed.any() and not (changed & ~on).any()
+    # float state tracks the fp64 recurrence
+    r64 = last["tau64"]
+    assert np.all(np.abs(tau - r64) <= 1e-5 * np.abs(r64))
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (9, 2), (10, 3)])
+def test_mmas_reaches_brute_force_optimum(orc, n, seed):
+    inst = I.uniform_instance(n, 1000, seed=seed)
+    opt, _ = orc.brute_force(inst.dist)
+    r = orc.run_mmas(inst.dist, n, 60, seed, rho=0.1)
+    assert r["best_len"] == opt
