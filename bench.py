@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--lanes-per-ant", type=int, default=0, help="0 = library default (32)")
     ap.add_argument("--nn", type=int, default=0,
                     help="nearest-neighbour list length (0 = every unvisited city)")
+    ap.add_argument("--variant", default="as", choices=["as", "mmas"],
+                    help="as: the Ant System update (Eqs. 2-4); mmas: the MAX-MIN Ant System "
+                         "update (p_best 0.05, iteration-best deposit)")
     ap.add_argument("--selection", default="eq1", choices=["eq1", "data-parallel"],
                     help="eq1: Eq. 1 (default); data-parallel: the paper's product-argmax kernel")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -325,6 +328,8 @@ def run_ours(args, w, rank, world, local):
         aco.aco_set_option(h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
     if args.nn:
         aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, args.nn)
+    if args.variant == "mmas":
+        aco.aco_set_mmas(h, 0.05, False)
     if args.lanes_per_ant:
         aco.aco_set_option(h, aco.ACO_OPT_LANES_PER_ANT, args.lanes_per_ant)
     if args.ants_per_cta:
@@ -379,7 +384,7 @@ def run_ours(args, w, rank, world, local):
     peaks, peak_kind = measured_peaks()
     roof = construct_roofline(n, m, con_ms, peaks, peak_kind)
     if not (args.nn or args.selection != "eq1" or args.lanes_per_ant or args.warps_per_ant
-            or args.ants_per_cta):
+            or args.ants_per_cta or args.variant != "as"):
         roof["traffic"], roof["traffic_source"] = recorded_traffic(w["name"])
     l2_gbs = measure_l2_copy_gbs()
     algo = roof["algorithmic_bytes_per_launch"]
@@ -399,6 +404,7 @@ def run_ours(args, w, rank, world, local):
                    "beta": w["beta"], "rho": w["rho"], "deposit": args.deposit,
                    "warps_per_ant": tiling[0], "ants_per_cta": tiling[1],
                    "lanes_per_ant": tiling[2], "selection": args.selection, "nn_list": args.nn,
+                   "variant": args.variant,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed between steps (256 MB write)"},
         "construct_ant_steps_per_s": m * (n - 1) / (con_ms / 1e3),

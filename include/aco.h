@@ -212,6 +212,36 @@ int aco_get_iteration(aco_handle h, int64_t *iteration);
 /* aco_get_tau0 - the initial pheromone m / C_nn and C_nn; either may be NULL. */
 int aco_get_tau0(aco_handle h, float *tau0, int64_t *nn_len);
 
+/*
+ * aco_set_mmas - switch the handle's update rule to the MAX-MIN Ant System,
+ * the ACO variant the paper cites as an earlier GPU target (Section II-B);
+ * the paper leaves other variants to future work (Section V) and does not
+ * define it, so this follows Stutzle and Hoos, "MAX-MIN Ant System", Future
+ * Generation Computer Systems 16 (2000):
+ *  - construction is unchanged (Eq. 1, or the rule/lists the options select);
+ *  - one tour deposits per iteration: the iteration best (best_so_far = 0)
+ *    or the best-so-far tour (best_so_far = 1), dtau = (float)(1/(double)C)
+ *    on its n edges in both directions, after evaporation by (1 - rho);
+ *  - every off-diagonal tau is then clamped into [tau_min, tau_max], where
+ *    tau_max = 1 / (rho C_gb) with C_gb the best-so-far length, and
+ *    tau_min = tau_max * f, f = (1 - p^(1/n)) / ((n/2 - 1) p^(1/n)),
+ *    p = p_best (tau_min = tau_max where that is larger); both computed in
+ *    double, f first, and rounded to float once;
+ *  - tau starts at tau_max computed from C_nn, replacing m / C_nn.
+ * The ACO_OPT_DEPOSIT variants do not apply (a single tour deposits, without
+ * atomics).  Call before the first construction (ACO_ESTATE after it); the
+ * switch cannot be undone.  p_best must lie in (0, 1) and best_so_far be 0
+ * or 1 (ACO_EINVAL).
+ */
+int aco_set_mmas(aco_handle h, double p_best, int32_t best_so_far);
+
+/*
+ * aco_get_mmas_limits - the current trail limits tau_min and tau_max of a
+ * MAX-MIN handle (either output may be NULL); ACO_ESTATE for an Ant System
+ * handle.
+ */
+int aco_get_mmas_limits(aco_handle h, float *tau_min, float *tau_max);
+
 /* aco_set_option / aco_get_option - ACO_OPT_* keys above. */
 int aco_set_option(aco_handle h, int32_t key, int64_t value);
 int aco_get_option(aco_handle h, int32_t key, int64_t *value);

@@ -68,6 +68,8 @@ SIGNATURES = [
     ("aco_get_heuristic", C.c_int, [_vp, _vp]),
     ("aco_get_iteration", C.c_int, [_vp, _i64p]),
     ("aco_get_tau0", C.c_int, [_vp, _f32p, _i64p]),
+    ("aco_set_mmas", C.c_int, [_vp, C.c_double, C.c_int32]),
+    ("aco_get_mmas_limits", C.c_int, [_vp, _f32p, _f32p]),
     ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
     ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
     ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
@@ -210,6 +212,19 @@ def aco_get_tau0(h):
     nn = C.c_int64()
     _check(load().aco_get_tau0(h, C.byref(t), C.byref(nn)), "aco_get_tau0")
     return float(np.float32(t.value)), nn.value
+
+
+def aco_set_mmas(h, p_best: float = 0.05, best_so_far: bool = False) -> None:
+    """Switch to the MAX-MIN Ant System update (before the first construction)."""
+    _check(load().aco_set_mmas(h, float(p_best), int(bool(best_so_far))), "aco_set_mmas")
+
+
+def aco_get_mmas_limits(h):
+    """(tau_min, tau_max) of a MAX-MIN handle."""
+    lo = C.c_float()
+    hi = C.c_float()
+    _check(load().aco_get_mmas_limits(h, C.byref(lo), C.byref(hi)), "aco_get_mmas_limits")
+    return float(np.float32(lo.value)), float(np.float32(hi.value))
 
 
 def aco_set_option(h, key: int, value: int) -> None:

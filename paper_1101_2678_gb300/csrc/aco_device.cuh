@@ -18,6 +18,8 @@ struct IterState {
   int deposit_shift;             // S of the fixed-point deposit
   float tau0;
   int status;                    // device error bits (kStatus*)
+  float tau_min, tau_max;        // MAX-MIN Ant System trail limits
+  float mmas_dtau;               // MAX-MIN Ant System deposit of this iteration
 };
 
 constexpr int kStatusTimeout = 1;
@@ -50,7 +52,16 @@ struct Instance {
   int nn;
   int32_t* nnlist;              // [n][kNnStride]
   float* nnchoice;              // [n][kNnStride]
+  // Update rule: kVariantAs (Eqs. 2-4) or kVariantMmas (the MAX-MIN Ant
+  // System: one depositing tour, trails clamped into [tau_min, tau_max]).
+  int variant;
+  int mmas_best_so_far;         // 1: the best-so-far tour deposits, 0: the iteration best
+  double mmas_f;                // tau_min / tau_max = (1 - p^(1/n)) / ((n/2 - 1) p^(1/n))
+  uint32_t* dep_nb;             // [n]  (pred << 16 | succ) of city i in the depositing tour
 };
+
+constexpr int kVariantAs = 0;
+constexpr int kVariantMmas = 1;
 
 constexpr int kNnStride = 32;   // longest supported list
 

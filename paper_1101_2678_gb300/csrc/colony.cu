@@ -214,12 +214,15 @@ static int enqueue_construct(aco_colony* h) {
 
 static int enqueue_update(aco_colony* h) {
   cudaError_t e;
-  if ((e = launch_deposit(h->I, h->deposit, h->sms, h->stream)) != cudaSuccess)
+  const int variant = h->I.variant;
+  if (variant == kVariantAs &&
+      (e = launch_deposit(h->I, h->deposit, h->sms, h->stream)) != cudaSuccess)
     return cuda_fail(e, "deposit");
   if (h->profile && (e = record_event(h, h->ev[3], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
-  if ((e = launch_update(h->I, h->deposit, h->sms, h->stream)) != cudaSuccess)
-    return cuda_fail(e, "update");
+  e = variant == kVariantMmas ? launch_mmas_update(h->I, h->sms, h->stream)
+                              : launch_update(h->I, h->deposit, h->sms, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "update");
   if (h->I.nn > 0 && (e = launch_nn_choice(h->I, h->stream)) != cudaSuccess)
     return cuda_fail(e, "nn choice");
   if (h->profile && (e = record_event(h, h->ev[4], h->stream)) != cudaSuccess)
@@ -319,7 +322,7 @@ static int create_common(int32_t n, const int32_t* dist, const int32_t* xy, floa
                o_q = take((size_t)m * 8), o_delta = take((size_t)m * 4),
                o_acc = take(mat * 8), o_best = take(((size_t)n + 1) * 4),
                o_st = take(sizeof(IterState)), o_nnl = take((size_t)n * kNnStride * 4),
-               o_nnc = take((size_t)n * kNnStride * 4);
+               o_nnc = take((size_t)n * kNnStride * 4), o_depnb = take((size_t)n * 4);
   h->arena_bytes = off;
   cudaError_t e = cudaMalloc(&h->arena, off);
   if (e != cudaSuccess) {
@@ -342,6 +345,8 @@ static int create_common(int32_t n, const int32_t* dist, const int32_t* xy, floa
   I.nnlist = (int32_t*)(b + o_nnl);
   I.nnchoice = (float*)(b + o_nnc);
   I.nn = 0;
+  I.dep_nb = (uint32_t*)(b + o_depnb);
+  I.variant = kVariantAs;
   h->sms = device_sms();
   rc = ACO_OK;
   do {
@@ -546,6 +551,37 @@ int aco_get_tau0(aco_handle h, float* tau0, int64_t* nn_len) {
   return rc;
 }
 
+int aco_set_mmas(aco_handle h, double p_best, int32_t best_so_far) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  if (!(p_best > 0.0 && p_best < 1.0)) return fail(ACO_EINVAL, "p_best must lie in (0, 1)");
+  if (best_so_far != 0 && best_so_far != 1) return fail(ACO_EINVAL, "best_so_far must be 0 or 1");
+  if (h->constructed || h->host_iteration != 0 || h->I.variant != kVariantAs)
+    return fail(ACO_ESTATE, "the update rule is chosen once, before the first construction");
+  const int n = h->I.n;
+  // f = tau_min / tau_max before the tau_min <= tau_max cap, in double.
+  const double root = std::pow(p_best, 1.0 / (double)n);
+  h->I.mmas_f = (1.0 - root) / (((double)n / 2.0 - 1.0) * root);
+  h->I.mmas_best_so_far = best_so_far;
+  h->I.variant = kVariantMmas;
+  drop_graph(h);
+  cudaError_t e = launch_mmas_init(h->I, h->sms, h->stream);
+  if (e == cudaSuccess && h->I.nn > 0) e = launch_nn_choice(h->I, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mmas init");
+  return check_status(h);
+}
+
+int aco_get_mmas_limits(aco_handle h, float* tau_min, float* tau_max) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  if (h->I.variant != kVariantMmas) return fail(ACO_ESTATE, "the handle runs the Ant System");
+  IterState st{};
+  cudaError_t e = cudaMemcpyAsync(&st, h->I.st, sizeof st, cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy state");
+  int rc = check_status(h);
+  if (tau_min) *tau_min = st.tau_min;
+  if (tau_max) *tau_max = st.tau_max;
+  return rc;
+}
+
 int aco_set_option(aco_handle h, int32_t key, int64_t value) {
   if (!h) return fail(ACO_EINVAL, "NULL handle");
   switch (key) {
@@ -676,7 +712,8 @@ int aco_synchronize(aco_handle h) {
 
 int aco_kernel_launches_per_iteration(aco_handle h, int32_t* count) {
   if (!h || !count) return fail(ACO_EINVAL, "NULL argument");
-  *count = launches_for_variant(h->deposit) + (h->I.nn > 0 ? 1 : 0);
+  *count = (h->I.variant != kVariantAs ? 3 : launches_for_variant(h->deposit)) +
+           (h->I.nn > 0 ? 1 : 0);
   return ACO_OK;
 }
 

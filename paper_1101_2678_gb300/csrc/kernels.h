@@ -37,6 +37,10 @@ cudaError_t launch_best(const Instance& I, cudaStream_t st);
 cudaError_t launch_deposit(const Instance& I, int variant, int sms, cudaStream_t st);
 cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t st);
 int launches_for_variant(int variant);
+// MAX-MIN Ant System: trails to tau_max(C_nn); one update (evaporation, the
+// depositing tour's dtau, clamp, choice_info).
+cudaError_t launch_mmas_init(const Instance& I, int sms, cudaStream_t st);
+cudaError_t launch_mmas_update(const Instance& I, int sms, cudaStream_t st);
 int gather_warps_per_cta(int ld);
 
 // Per-(G, H) dispatchers (one translation unit each, compiled in parallel).

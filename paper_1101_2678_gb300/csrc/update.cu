@@ -260,6 +260,63 @@ __global__ void __launch_bounds__(256) apply_symmetric_kernel(Instance I, int bu
   }
 }
 
+// MAX-MIN Ant System update (the variant of Stutzle and Hoos, cited by the
+// paper in Section II-B): tau' = clamp(fl(fl((1-rho) tau) + [ij on the
+// depositing tour] dtau), tau_min, tau_max) off the diagonal, then
+// choice_info; one streaming pass of 16-byte accesses.  Every city has
+// exactly two neighbours on the depositing tour (dep_nb), so the deposit
+// needs no atomics and no accumulator.
+__global__ void mmas_update_kernel(Instance I, int bump_iteration) {
+  const int n = I.n, ld = I.ld;
+  const size_t total4 = (size_t)n * ld / 4;
+  const float keep = __fsub_rn(1.0f, I.rho);
+  const float dtau = I.st->mmas_dtau, lo = I.st->tau_min, hi = I.st->tau_max;
+  const float alpha = I.alpha;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total4;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(4 * e / ld), j0 = (int)(4 * e % ld);
+    const uint32_t nb = I.dep_nb[i];
+    const int pred = (int)(nb >> 16), succ = (int)(nb & 0xffffu);
+    float4 t4 = reinterpret_cast<const float4*>(I.tau)[e];
+    const float4 h4 = reinterpret_cast<const float4*>(I.heta)[e];
+    float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+    const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+    float cv[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + c;
+      float t = __fmul_rn(keep, tv[c]);
+      if (j == pred || j == succ) t = __fadd_rn(t, dtau);
+      if (j != i && j < n) t = fminf(fmaxf(t, lo), hi);
+      tv[c] = t;
+      cv[c] = choice_of(t, hv[c], alpha);
+    }
+    reinterpret_cast<float4*>(I.tau)[e] = make_float4(tv[0], tv[1], tv[2], tv[3]);
+    reinterpret_cast<float4*>(I.choice)[e] = make_float4(cv[0], cv[1], cv[2], cv[3]);
+  }
+  if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
+}
+
+// MAX-MIN Ant System start: tau = tau_max computed from C_nn off the
+// diagonal, the limits stored, choice_info recomputed.
+__global__ void mmas_init_kernel(Instance I) {
+  float lo, hi;
+  mmas_limits(I, I.st->nn_len, &lo, &hi);
+  const int n = I.n, ld = I.ld;
+  const size_t total = (size_t)n * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    const float t = (j != i && j < n) ? hi : 0.0f;
+    I.tau[e] = t;
+    I.choice[e] = choice_of(t, I.heta[e], I.alpha);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    I.st->tau_min = lo;
+    I.st->tau_max = hi;
+  }
+}
+
 // The paper's atomic kernel: evaporation first (Eq. 2) ...
 __global__ void evaporate_kernel(Instance I) {
   const size_t total4 = (size_t)I.n * I.ld / 4;
@@ -432,6 +489,16 @@ cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t 
   } else {
     choice_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I, 1);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mmas_init(const Instance& I, int sms, cudaStream_t st) {
+  mmas_init_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mmas_update(const Instance& I, int sms, cudaStream_t st) {
+  mmas_update_kernel<<<grid_for((size_t)I.n * I.ld / 4, 256, sms), 256, 0, st>>>(I, 1);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,18 @@ namespace aco {
 // Block-wide (any blockDim multiple of 32, <= 1024): argmin of C^k (ties to
 // the lower ant), best-so-far update, deposit scale S and the per-ant dtau^k,
 // q_k of Eqs. 3-4.
+// MAX-MIN Ant System trail limits for best-so-far length c_gb, in double,
+// each rounded to float once: tau_max = 1 / (rho c_gb), tau_min = tau_max * f
+// (f precomputed on the host), tau_min = tau_max where that is larger.
+__device__ __forceinline__ void mmas_limits(const Instance& I, long long c_gb, float* tau_min,
+                                            float* tau_max) {
+  const double tmax = 1.0 / ((double)I.rho * (double)c_gb);
+  double tmin = tmax * I.mmas_f;
+  if (tmin > tmax) tmin = tmax;
+  *tau_max = (float)tmax;
+  *tau_min = (float)tmin;
+}
+
 __device__ __forceinline__ void best_body(const Instance& I) {
   __shared__ long long red_l[32];
   __shared__ int red_k[32];
@@ -67,6 +79,24 @@ __device__ __forceinline__ void best_body(const Instance& I) {
   if (s_improved) {
     const int32_t* src = I.tours + (size_t)s_best * I.ldt;
     for (int s = threadIdx.x; s <= n; s += blockDim.x) I.best_tour[s] = src[s];
+  }
+  if (I.variant == kVariantMmas) {
+    // The depositing tour (the iteration best, or the best-so-far tour,
+    // which is this iteration's best when it just improved), its neighbours
+    // per city, its deposit and the trail limits from the best-so-far length.
+    const int32_t* dep = (I.mmas_best_so_far && !s_improved)
+                             ? I.best_tour
+                             : I.tours + (size_t)s_best * I.ldt;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+      const uint32_t pred = (uint32_t)dep[s == 0 ? n - 1 : s - 1], succ = (uint32_t)dep[s + 1];
+      I.dep_nb[dep[s]] = (pred << 16) | succ;
+    }
+    if (threadIdx.x == 0) {
+      IterState* st = I.st;
+      const long long c_dep = I.mmas_best_so_far ? st->best_len : st->iter_best_len;
+      st->mmas_dtau = (float)(1.0 / (double)c_dep);
+      mmas_limits(I, st->best_len, &st->tau_min, &st->tau_max);
+    }
   }
 }
 
