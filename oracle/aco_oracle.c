@@ -82,6 +82,23 @@
  *     in double in this order and rounded to float once; the trails start at
  *     tau_max computed from C_nn.  tau' = clamp(fl(fl((1-rho) tau) + dtau)).
  *
+ *  R14 (optional variant) the Ant Colony System, which the paper names as
+ *     its next target (Section V); the variant is the one of Dorigo and
+ *     Gambardella, IEEE Trans. Evol. Comp. 1(1) (1997).  tau starts at
+ *     tau0 = (float)(1 / (n C_nn)).  At step s ant k draws x = Philox (s, k,
+ *     iteration, 0): it exploits when x2 < floor(q0 2^32) (compared as
+ *     64-bit integers), moving to the unvisited city of largest choice_info
+ *     (ties to the lower index), and otherwise samples Eq. 1 by the integer
+ *     roulette of R2 with r = x1 2^32 + x0.  The ants move in lockstep: all
+ *     ants choose their s-th city from the same state, then every edge
+ *     crossed at that step gets the local update tau <- fl(fl((1-xi) tau) +
+ *     fl(xi tau0)) in both directions, once per ant that crossed it (the
+ *     applications are identical, so their order does not matter), and its
+ *     choice_info is recomputed.  The closing edge back to the start is the
+ *     n-th such step.  After the tours, only the best-so-far tour's edges get
+ *     the global update tau <- fl(fl((1-rho) tau) + fl(rho dtau)), dtau =
+ *     (float)(1 / (double)C_bs), both directions; no other cell evaporates.
+ *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared -lm.
  * -ffp-contract=off matters: a fused multiply-add would change the rounding of
  * fl(fl(a*b)+c).
@@ -716,6 +733,151 @@ int orc_run_mmas(int n, const int32_t *d, float alpha, float beta, float rho, in
     }
     free(heta); free(tau); free(tau64); free(choice); free(tours); free(lens); free(gb);
     free(lists);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Ant Colony System (reading R14).                                           */
+/* ------------------------------------------------------------------------- */
+
+/* floor(q0 * 2^32): a step exploits when its Philox word x2 is below it. */
+uint64_t orc_acs_threshold(double q0)
+{
+    if (!(q0 > 0.0)) return 0;
+    if (q0 >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(q0 * 4294967296.0);
+}
+
+/* The pseudo-random proportional rule for one step (w: the row of the
+ * current city, visited: the tabu list).  Returns -1 if every city is
+ * visited. */
+int orc_acs_select(int n, const float *w, const uint8_t *visited, uint64_t r, uint32_t x2,
+                   uint64_t threshold)
+{
+    if ((uint64_t)x2 < threshold) {
+        int best = -1;
+        for (int j = 0; j < n; ++j)
+            if (!visited[j] && (best < 0 || w[j] > w[best])) best = j;
+        return best;
+    }
+    return orc_roulette(n, w, visited, r);
+}
+
+/* One local update of one cell. */
+float orc_acs_local(float tau, float xi, float tau0)
+{
+    float keep = 1.0f - xi;
+    float add = xi * tau0;
+    return keep * tau + add;
+}
+
+static float choice_cell(float tau, float heta, float alpha)
+{
+    if (alpha == 1.0f) return tau * heta;
+    if (alpha == 0.0f) return heta;
+    return powf(tau, alpha) * heta;
+}
+
+static void acs_cross(int n, int a, int b, float xi, float tau0, float alpha, const float *heta,
+                      float *tau, float *choice)
+{
+    size_t ab = (size_t)a * n + b, ba = (size_t)b * n + a;
+    tau[ab] = orc_acs_local(tau[ab], xi, tau0);
+    tau[ba] = orc_acs_local(tau[ba], xi, tau0);
+    choice[ab] = choice_cell(tau[ab], heta[ab], alpha);
+    choice[ba] = choice_cell(tau[ba], heta[ba], alpha);
+}
+
+/* A whole ACS run.  tau_out (n*n) is the final pheromone; the others as in
+ * orc_run_nn. */
+int orc_run_acs(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+                uint64_t seed, int iterations, double q0, float xi, int32_t *best_tour,
+                int64_t *best_len, float *tau_out, int32_t *last_tours, int64_t *last_lens,
+                int64_t *iter_best)
+{
+    if (n < 3 || m < 1) return -1;
+    size_t cells = (size_t)n * n;
+    float *heta = (float *)malloc(cells * sizeof(float));
+    float *tau = (float *)malloc(cells * sizeof(float));
+    float *choice = (float *)malloc(cells * sizeof(float));
+    int32_t *tours = (int32_t *)malloc((size_t)m * (n + 1) * sizeof(int32_t));
+    int64_t *lens = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    int32_t *gb = (int32_t *)malloc((size_t)(n + 1) * sizeof(int32_t));
+    uint8_t *visited = (uint8_t *)malloc((size_t)m * n);
+    int *cur = (int *)malloc((size_t)m * sizeof(int));
+    int *next = (int *)malloc((size_t)m * sizeof(int));
+    if (!heta || !tau || !choice || !tours || !lens || !gb || !visited || !cur || !next)
+        return -2;
+
+    orc_heta(n, d, (double)beta, heta);
+    int64_t cnn = orc_nn_tour_length(n, d);
+    float tau0 = (float)(1.0 / ((double)n * (double)cnn));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) tau[(size_t)i * n + j] = (i == j) ? 0.0f : tau0;
+    orc_choice(n, tau, heta, alpha, choice);
+    uint64_t thr = orc_acs_threshold(q0);
+    float keep = 1.0f - rho;
+
+    int64_t best = INT64_MAX;
+    for (int it = 0; it < iterations; ++it) {
+        uint32_t x[4];
+        memset(visited, 0, (size_t)m * n);
+        for (int k = 0; k < m; ++k) {
+            draw(seed, 0u, (uint32_t)k, (uint32_t)it, x);
+            int start = (int)(((uint64_t)x[0] * (uint64_t)n) >> 32);
+            tours[(size_t)k * (n + 1)] = start;
+            visited[(size_t)k * n + start] = 1;
+            cur[k] = start;
+        }
+        for (int s = 1; s < n; ++s) {
+            for (int k = 0; k < m; ++k) {
+                draw(seed, (uint32_t)s, (uint32_t)k, (uint32_t)it, x);
+                uint64_t r = ((uint64_t)x[1] << 32) | (uint64_t)x[0];
+                next[k] = orc_acs_select(n, choice + (size_t)cur[k] * n, visited + (size_t)k * n,
+                                         r, x[2], thr);
+            }
+            for (int k = 0; k < m; ++k) {
+                acs_cross(n, cur[k], next[k], xi, tau0, alpha, heta, tau, choice);
+                tours[(size_t)k * (n + 1) + s] = next[k];
+                visited[(size_t)k * n + next[k]] = 1;
+                cur[k] = next[k];
+            }
+        }
+        for (int k = 0; k < m; ++k) {
+            int start = tours[(size_t)k * (n + 1)];
+            acs_cross(n, cur[k], start, xi, tau0, alpha, heta, tau, choice);
+            tours[(size_t)k * (n + 1) + n] = start;
+            int64_t len = 0;
+            for (int s = 0; s < n; ++s)
+                len += d[(size_t)tours[(size_t)k * (n + 1) + s] * n +
+                         tours[(size_t)k * (n + 1) + s + 1]];
+            lens[k] = len;
+        }
+        int kbest = 0;
+        for (int k = 1; k < m; ++k)
+            if (lens[k] < lens[kbest]) kbest = k;
+        if (iter_best) iter_best[it] = lens[kbest];
+        if (lens[kbest] < best) {
+            best = lens[kbest];
+            memcpy(gb, tours + (size_t)kbest * (n + 1), (size_t)(n + 1) * sizeof(int32_t));
+        }
+        float dep = rho * (float)(1.0 / (double)best);
+        for (int s = 0; s < n; ++s) {
+            int a = gb[s], b = gb[s + 1];
+            size_t ab = (size_t)a * n + b, ba = (size_t)b * n + a;
+            tau[ab] = keep * tau[ab] + dep;
+            tau[ba] = keep * tau[ba] + dep;
+            choice[ab] = choice_cell(tau[ab], heta[ab], alpha);
+            choice[ba] = choice_cell(tau[ba], heta[ba], alpha);
+        }
+    }
+    if (best_len) *best_len = best;
+    if (best_tour && iterations > 0) memcpy(best_tour, gb, (size_t)(n + 1) * sizeof(int32_t));
+    if (tau_out) memcpy(tau_out, tau, cells * sizeof(float));
+    if (last_tours) memcpy(last_tours, tours, (size_t)m * (n + 1) * sizeof(int32_t));
+    if (last_lens) memcpy(last_lens, lens, (size_t)m * sizeof(int64_t));
+    free(heta); free(tau); free(choice); free(tours); free(lens); free(gb); free(visited);
+    free(cur); free(next);
     return 0;
 }
 

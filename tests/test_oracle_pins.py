@@ -577,3 +577,108 @@ def test_mmas_reaches_brute_force_optimum(orc, n, seed):
     opt, _ = orc.brute_force(inst.dist)
     r = orc.run_mmas(inst.dist, n, 60, seed, rho=0.1)
     assert r["best_len"] == opt
+
+
+# --------------------------------------------------------------------------
+# Ant Colony System (reading R14: Dorigo and Gambardella 1997)
+# --------------------------------------------------------------------------
+
+def _greedy_tour(dist, start):
+    n = dist.shape[0]
+    tour, seen = [start], {start}
+    while len(tour) < n:
+        row = [(dist[tour[-1], j], j) for j in range(n) if j not in seen]
+        j = min(row)[1]
+        tour.append(j)
+        seen.add(j)
+    return tour + [start]
+
+
+def test_acs_exploitation_only_is_the_greedy_tour(orc):
+    # q0 = 1: every step takes the largest tau * eta^2.  The trails start
+    # uniform and the local update moves them by at most an ulp, so on an
+    # instance with no equal distances in any row each ant walks the
+    # nearest-neighbour tour from its start.
+    inst = I.uniform_instance(25, 100000, seed=8)
+    d = inst.dist
+    for i in range(25):
+        row = np.delete(d[i], i)
+        assert len(np.unique(row)) == 24
+    r = orc.run_acs(d, 6, 1, 3, q0=1.0, xi=0.1)
+    for k in range(6):
+        assert r["tours"][k].tolist() == _greedy_tour(d, int(r["tours"][k, 0]))
+
+
+def test_acs_without_exploitation_or_local_update_is_eq1(orc):
+    # q0 = 0 and xi = 0: the local update is the identity and every step
+    # samples Eq. 1, so the first iteration equals the Ant System's
+    # construction on choice_info = tau0 * eta^2.
+    inst = I.uniform_instance(40, 1000, seed=4)
+    n, m = 40, 12
+    r = orc.run_acs(inst.dist, m, 1, 7, q0=0.0, xi=0.0)
+    tau0 = np.float32(1.0 / (n * orc.nn_tour_length(inst.dist)))
+    tau = np.where(np.eye(n) > 0, 0, tau0).astype(np.float32)
+    ch = orc.choice(tau, orc.heta(inst.dist, 2.0), 1.0)
+    tours, lens = orc.construct(ch, inst.dist, m, seed=7, iteration=0)
+    assert np.array_equal(r["tours"], tours) and np.array_equal(r["lens"], lens)
+
+
+def test_acs_local_update_closed_form_and_counts(orc):
+    # One application with xi = 1/2, tau0 = 1 on tau = 4: 2 + 1/2 = 2.5; a
+    # second: 1.25 + 0.5 = 1.75 (all exact in float).
+    assert orc.acs_local(4.0, 0.5, 1.0) == 2.5
+    assert orc.acs_local(2.5, 0.5, 1.0) == 1.75
+    # Over a greedy iteration (q0 = 1) an edge crossed c times (by any ants,
+    # at any steps) carries f^c(tau0); the best-so-far tour's edges then get
+    # the global update (1 - rho) tau + rho / C_bs.
+    inst = I.uniform_instance(7, 100000, seed=3)
+    n, m, xi, rho = 7, 20, 0.25, 0.1
+    r = orc.run_acs(inst.dist, m, 1, 11, q0=1.0, xi=xi, rho=rho)
+    tau0 = np.float32(1.0 / (n * orc.nn_tour_length(inst.dist)))
+    count = np.zeros((n, n), int)
+    for t in r["tours"]:
+        for a, b in zip(t[:-1], t[1:]):
+            count[a, b] += 1
+            count[b, a] += 1
+    expect = np.where(np.eye(n) > 0, 0, tau0).astype(np.float32)
+    for a in range(n):
+        for b in range(n):
+            for _ in range(count[a, b]):
+                expect[a, b] = orc.acs_local(expect[a, b], xi, tau0)
+    on = np.zeros((n, n), bool)
+    bt = r["best_tour"]
+    for a, b in zip(bt[:-1], bt[1:]):
+        on[a, b] = on[b, a] = True
+    assert np.array_equal(r["tau32"][~on], expect[~on])
+    dep = np.float32(np.float32(rho) * np.float32(1.0 / r["best_len"]))
+    glob = (np.float32(1 - np.float32(rho)) * expect + dep).astype(np.float32)
+    assert np.array_equal(r["tau32"][on], glob[on])
+    assert r["best_len"] == min(r["lens"])
+
+
+def test_acs_exploitation_frequency(orc):
+    # Weights 5, 1, 1, 1: exploitation always takes city 0, the roulette with
+    # probability 5/8, so P(0) = q0 + (1 - q0) 5/8.
+    from scipy.stats import binomtest
+    w = np.array([5.0, 1.0, 1.0, 1.0], np.float32)
+    vis = np.zeros(4, np.uint8)
+    for q0 in (0.3, 0.8):
+        hits, trials = 0, 20000
+        for i in range(trials):
+            x = orc.philox4x32_10([i, 1, 2, 0], [99, 0])
+            r = (int(x[1]) << 32) | int(x[0])
+            hits += orc.acs_select(w, vis, r, int(x[2]), q0) == 0
+        assert binomtest(hits, trials, q0 + (1 - q0) * 5 / 8).pvalue > 0.01
+    # ties in exploitation go to the lower index; visited cities never win
+    w2 = np.array([9.0, 2.0, 7.0, 7.0], np.float32)
+    assert orc.acs_select(w2, np.array([1, 0, 0, 0], np.uint8), 0, 0, 1.0) == 2
+    assert orc.acs_threshold(0.0) == 0 and orc.acs_threshold(1.0) == 2 ** 32
+    assert orc.acs_threshold(0.5) == 2 ** 31
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (9, 2), (10, 3)])
+def test_acs_reaches_brute_force_optimum(orc, n, seed):
+    inst = I.uniform_instance(n, 1000, seed=seed)
+    opt, _ = orc.brute_force(inst.dist)
+    r = orc.run_acs(inst.dist, 10, 60, seed)
+    assert r["best_len"] == opt
