@@ -56,9 +56,10 @@ def parse():
     ap.add_argument("--lanes-per-ant", type=int, default=0, help="0 = library default (32)")
     ap.add_argument("--nn", type=int, default=0,
                     help="nearest-neighbour list length (0 = every unvisited city)")
-    ap.add_argument("--variant", default="as", choices=["as", "mmas"],
+    ap.add_argument("--variant", default="as", choices=["as", "mmas", "acs"],
                     help="as: the Ant System update (Eqs. 2-4); mmas: the MAX-MIN Ant System "
-                         "update (p_best 0.05, iteration-best deposit)")
+                         "update (p_best 0.05, iteration-best deposit); acs: the Ant Colony "
+                         "System (q0 0.9, xi 0.1; m = min(m, 10))")
     ap.add_argument("--selection", default="eq1", choices=["eq1", "data-parallel"],
                     help="eq1: Eq. 1 (default); data-parallel: the paper's product-argmax kernel")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -69,6 +70,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=20.0,
                     help="length of the Poisson arrival window for --workload served")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-loop-sample", type=int, default=16,
+                    help="requests solved one at a time for the loop comparison")
     return ap.parse_args()
 
 
@@ -313,6 +316,8 @@ def run_ours(args, w, rank, world, local):
     aco.load()
     d = w["inst"].dist
     n, m = d.shape[0], w["m"]
+    if args.variant == "acs":
+        m = min(m, 10)  # the Ant Colony System's usual colony (one CTA, m <= 32)
     dep = {"gather": aco.ACO_DEPOSIT_GATHER, "u64": aco.ACO_DEPOSIT_ATOMIC_U64,
            "f32": aco.ACO_DEPOSIT_ATOMIC_F32, "sym": aco.ACO_DEPOSIT_SYMMETRIC}[args.deposit]
     stream = torch.cuda.Stream()
@@ -330,6 +335,8 @@ def run_ours(args, w, rank, world, local):
         aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, args.nn)
     if args.variant == "mmas":
         aco.aco_set_mmas(h, 0.05, False)
+    elif args.variant == "acs":
+        aco.aco_set_acs(h, 0.9, 0.1)
     if args.lanes_per_ant:
         aco.aco_set_option(h, aco.ACO_OPT_LANES_PER_ANT, args.lanes_per_ant)
     if args.ants_per_cta:
@@ -519,6 +526,17 @@ def run_batched(args, rank, world, local):
     barrier(world)
     b = aco.aco_batch_create(dists, ms, seeds)
     aco.aco_pool_synchronize(b)
+    # choose each class's construction tiling before the timed run (the
+    # choice does not change any result); reported in config
+    t_tune = time.perf_counter()
+    aco.aco_pool_autotune(b)
+    aco.aco_pool_synchronize(b)
+    t_tune = time.perf_counter() - t_tune
+    tilings = {}
+    for i, x in enumerate(insts):
+        g, hh, c = aco.aco_pool_tiling(b, i)
+        tilings.setdefault(f"G{g}H{hh}C{c}", 0)
+        tilings[f"G{g}H{hh}C{c}"] += 1
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -553,7 +571,8 @@ def run_batched(args, rank, world, local):
         "data": "synthetic",
         "config": {"workload": w["name"], "instances": len(insts), "n_min": min(x.n for x in insts),
                    "n_max": max(x.n for x in insts), "iterations": iters,
-                   "l2": "not flushed (one continuous 100-step run)"},
+                   "l2": "not flushed (one continuous 100-step run)",
+                   "autotuned_tilings": tilings, "autotune_seconds": t_tune},
         "per_instance_loop_solves_per_s": len(insts) / t_loop if t_loop else None,
         "speedup_vs_loop": t_loop / t_batch if t_loop else None,
         "identical_best_lengths": best_batch == best_loop,
@@ -586,6 +605,21 @@ def run_served(args, rank, world, local):
         arr2 = instances.poisson_arrivals(rate, args.serve_seconds, seed=6)
         reqs2 = [reqs[i % len(reqs)] for i in range(len(arr2))]
         outs2, st2 = srv.run(reqs2, arr2, deadline=3 * args.serve_seconds)
+    # the same requests one at a time through the single-instance API (the plain
+    # per-request loop) against the server on the same sample, all admitted at once
+    sample = reqs[:args.serve_loop_sample]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loop_lens = []
+    for r in sample:
+        h = aco.aco_create_coords(r.coords, r.alpha, r.beta, r.rho, r.m, r.seed)
+        aco.aco_iterate(h, r.iterations)
+        loop_lens.append(aco.aco_best_tour(h, r.n)[1])
+        aco.aco_destroy(h)
+    t_loop = time.perf_counter() - t0
+    with serve.Server(budget_bytes=64 << 30, max_slots=4096, max_step_work=1 << 62) as srv:
+        outs3, st3 = srv.run(sample, np.zeros(len(sample)), realtime=False)
+    same = sorted((o.index, o.best_len) for o in outs3) == list(enumerate(loop_lens))
     if rank != 0:
         return
     line = {
@@ -597,6 +631,14 @@ def run_served(args, rank, world, local):
                    "window_s": args.serve_seconds, "budget_gb": 64, "iterations": 200},
         "configured_stream": st,
         "sustainable_stream": dict(st2, rate_per_s=rate),
+        "loop_comparison": {
+            "requests": len(sample), "per_request_loop_solves_per_s": len(sample) / t_loop,
+            "server_solves_per_s": st3["solves_per_s"],
+            "speedup_vs_loop": st3["solves_per_s"] * t_loop / len(sample),
+            "identical_best_lengths": same,
+            "what": "the first requests of the stream solved one at a time (aco_create_coords "
+                    "+ aco_iterate(200) + aco_best_tour) vs the server with all of them "
+                    "admitted at once"},
     }
     print(json.dumps(line), flush=True)
 

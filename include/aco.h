@@ -236,6 +236,32 @@ int aco_get_tau0(aco_handle h, float *tau0, int64_t *nn_len);
 int aco_set_mmas(aco_handle h, double p_best, int32_t best_so_far);
 
 /*
+ * aco_set_acs - switch the handle to the Ant Colony System, the ACO variant
+ * the paper names as its next target (Section V); the paper does not define
+ * it, so this follows Dorigo and Gambardella, IEEE Trans. Evol. Comp. 1(1)
+ * (1997), with choice_info = tau^alpha * eta^beta as in the Ant System:
+ *  - tau starts at tau0 = (float)(1 / (n C_nn)) off the diagonal;
+ *  - at step s ant k draws Philox (s, k, iteration, 0); it exploits when
+ *    word x2 < floor(q0 * 2^32), moving to the unvisited city of largest
+ *    choice_info (ties to the lower index), and otherwise samples Eq. 1 by
+ *    the integer roulette;
+ *  - the ants move in lockstep: all choose their s-th city from the same
+ *    state, then every edge crossed at that step gets the local update
+ *    tau <- fl(fl((1-xi) tau) + fl(xi tau0)) in both directions, once per
+ *    ant that crossed it, with its choice_info; the closing edge back to the
+ *    start is the n-th step;
+ *  - after the tours only the best-so-far tour's edges get the global update
+ *    tau <- fl(fl((1-rho) tau) + fl(rho / C_bs)) (rho as given to create);
+ *    no other cell evaporates.
+ * The colony runs in one CTA, so m <= 32 (the variant's usual m is 10).
+ * Because construction changes tau, construction calls are not idempotent
+ * under this rule.  Nearest-neighbour lists and ACO_OPT_SELECTION do not
+ * apply.  Call once, before the first construction (ACO_ESTATE otherwise);
+ * q0 and xi must lie in [0, 1] and m <= 32 (ACO_EINVAL).
+ */
+int aco_set_acs(aco_handle h, double q0, float xi);
+
+/*
  * aco_get_mmas_limits - the current trail limits tau_min and tau_max of a
  * MAX-MIN handle (either output may be NULL); ACO_ESTATE for an Ant System
  * handle.
@@ -344,6 +370,29 @@ int aco_pool_release(aco_pool_handle p, int32_t slot);
  */
 int aco_pool_stats(aco_pool_handle p, int32_t *live, int32_t *finished, uint64_t *bytes_in_use,
                    int32_t *launches_last_step);
+
+/*
+ * Construction tiling of pooled instances.  Live instances are grouped into
+ * classes by their default tiling (whole warps, C cities per lane); each
+ * class is one construction launch per step.  With autotuning on (the
+ * default), the first step that sees a class times each candidate tiling on
+ * it (1, 2 or 4 warps per ant, or 8- or 16-lane segments with 4 or 2 ants per
+ * warp; the second of two runs) and keeps the fastest for that class from
+ * then on.  Every tiling builds the same tours, so tuning never changes a
+ * result.
+ *   aco_pool_set_autotune: on = 1 (default) or 0 (the default tiling always;
+ *     forgets earlier choices).
+ *   aco_pool_autotune: run the tuner now for classes of the current live
+ *     set not tuned yet (otherwise it runs inside the next aco_pool_step);
+ *     it builds tours but advances no iteration.
+ *   aco_pool_tiling: the tiling the class of live `slot` uses: warps per ant,
+ *     lanes per ant and cities per lane (any output may be NULL);
+ *     ACO_ESTATE before the first step after the live set changed.
+ */
+int aco_pool_set_autotune(aco_pool_handle p, int32_t on);
+int aco_pool_autotune(aco_pool_handle p);
+int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t *warps_per_ant,
+                    int32_t *lanes_per_ant, int32_t *cities_per_lane);
 
 /* aco_pool_synchronize - wait for all pool work and report device-side errors. */
 int aco_pool_synchronize(aco_pool_handle p);

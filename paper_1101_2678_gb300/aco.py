@@ -70,6 +70,7 @@ SIGNATURES = [
     ("aco_get_tau0", C.c_int, [_vp, _f32p, _i64p]),
     ("aco_set_mmas", C.c_int, [_vp, C.c_double, C.c_int32]),
     ("aco_get_mmas_limits", C.c_int, [_vp, _f32p, _f32p]),
+    ("aco_set_acs", C.c_int, [_vp, C.c_double, C.c_float]),
     ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
     ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
     ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
@@ -91,6 +92,9 @@ SIGNATURES = [
     ("aco_pool_release", C.c_int, [_vp, C.c_int32]),
     ("aco_pool_stats", C.c_int, [_vp, _i32p, _i32p, C.POINTER(C.c_uint64), _i32p]),
     ("aco_pool_synchronize", C.c_int, [_vp]),
+    ("aco_pool_set_autotune", C.c_int, [_vp, C.c_int32]),
+    ("aco_pool_autotune", C.c_int, [_vp]),
+    ("aco_pool_tiling", C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p]),
     ("aco_batch_create", C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     ("aco_batch_iterate", C.c_int, [_vp, C.c_int32]),
     ("aco_batch_best", C.c_int, [_vp, C.c_int32, _vp, _vp]),
@@ -219,6 +223,11 @@ def aco_set_mmas(h, p_best: float = 0.05, best_so_far: bool = False) -> None:
     _check(load().aco_set_mmas(h, float(p_best), int(bool(best_so_far))), "aco_set_mmas")
 
 
+def aco_set_acs(h, q0: float = 0.9, xi: float = 0.1) -> None:
+    """Switch to the Ant Colony System (before the first construction; m <= 32)."""
+    _check(load().aco_set_acs(h, float(q0), float(xi)), "aco_set_acs")
+
+
 def aco_get_mmas_limits(h):
     """(tau_min, tau_max) of a MAX-MIN handle."""
     lo = C.c_float()
@@ -344,6 +353,22 @@ def aco_pool_stats(p) -> dict:
 
 def aco_pool_synchronize(p) -> None:
     _check(load().aco_pool_synchronize(p), "aco_pool_synchronize")
+
+
+def aco_pool_set_autotune(p, on: bool) -> None:
+    _check(load().aco_pool_set_autotune(p, int(bool(on))), "aco_pool_set_autotune")
+
+
+def aco_pool_autotune(p) -> None:
+    """Tune the construction tiling of the live set's new classes now."""
+    _check(load().aco_pool_autotune(p), "aco_pool_autotune")
+
+
+def aco_pool_tiling(p, slot: int):
+    """(warps per ant, lanes per ant, cities per lane) of the class of live `slot`."""
+    g, h, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().aco_pool_tiling(p, slot, C.byref(g), C.byref(h), C.byref(c)), "aco_pool_tiling")
+    return g.value, h.value, c.value
 
 
 def aco_batch_create(dists, ms, seeds, alpha=1.0, beta=2.0, rho=0.5):

@@ -20,6 +20,7 @@ struct IterState {
   int status;                    // device error bits (kStatus*)
   float tau_min, tau_max;        // MAX-MIN Ant System trail limits
   float mmas_dtau;               // MAX-MIN Ant System deposit of this iteration
+  float acs_tau0;                // Ant Colony System tau0 = 1 / (n C_nn)
 };
 
 constexpr int kStatusTimeout = 1;
@@ -58,10 +59,15 @@ struct Instance {
   int mmas_best_so_far;         // 1: the best-so-far tour deposits, 0: the iteration best
   double mmas_f;                // tau_min / tau_max = (1 - p^(1/n)) / ((n/2 - 1) p^(1/n))
   uint32_t* dep_nb;             // [n]  (pred << 16 | succ) of city i in the depositing tour
+  // Ant Colony System: a step exploits when its Philox word x2 is below
+  // acs_threshold = floor(q0 2^32); local evaporation xi.
+  unsigned long long acs_threshold;
+  float acs_xi;
 };
 
 constexpr int kVariantAs = 0;
 constexpr int kVariantMmas = 1;
+constexpr int kVariantAcs = 2;
 
 constexpr int kNnStride = 32;   // longest supported list
 

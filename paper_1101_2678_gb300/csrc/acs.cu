@@ -1,0 +1,265 @@
+// Ant Colony System (Dorigo and Gambardella, IEEE Trans. Evol. Comp. 1(1),
+// 1997), the ACO variant the paper names as its next target (Section V), on
+// the same data layout as the Ant System:
+//  - the pseudo-random proportional rule: at step s ant k draws Philox
+//    (s, k, iteration, 0); it exploits when word x2 < floor(q0 2^32), taking
+//    the unvisited city of largest choice_info (ties to the lower index), and
+//    otherwise samples Eq. 1 by the exact integer roulette;
+//  - the local update: the ants move in lockstep, all choosing their s-th
+//    city from the same state; then every edge crossed at that step gets
+//    tau <- fl(fl((1-xi) tau) + fl(xi tau0)) once per ant that crossed it,
+//    in both directions, with its choice_info; the closing edge is the n-th
+//    such step;
+//  - the global update: only the best-so-far tour's edges get
+//    tau <- fl(fl((1-rho) tau) + fl(rho dtau)), dtau = 1/C_bs.
+// The colony (m <= 32 ants, the variant's usual m = 10) runs in one CTA, one
+// warp per ant, so the per-step lockstep is a CTA barrier.
+#include "aco_device.cuh"
+#include "kernels.h"
+
+namespace aco {
+
+// floor(w * 2^sc) for a non-negative float given by its bits, exactly, with
+// integer shifts of the significand (sc is such that the result is < 2^46).
+__device__ __forceinline__ unsigned long long acs_quant(uint32_t b, int sc) {
+  if (b == 0u) return 0ull;
+  const uint32_t e = b >> 23;
+  const uint32_t mant = e ? ((b & 0x7fffffu) | 0x800000u) : b;
+  const int shift = (e ? (int)e - 150 : -149) + sc;
+  if (shift >= 0) return (unsigned long long)mant << shift;
+  if (shift <= -24) return 0ull;
+  return (unsigned long long)(mant >> (-shift));
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(FULL, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long w = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += w;
+  }
+  return v;
+}
+
+// One local update of one cell.
+__device__ __forceinline__ float acs_local(float tau, float keep, float add) {
+  return __fadd_rn(__fmul_rn(keep, tau), add);
+}
+
+__global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
+  extern __shared__ uint32_t acs_seen[];          // m tabu bitmaps of `words` words
+  __shared__ uint32_t s_edge[32];                 // (min << 16 | max) crossed by ant k
+  const int n = I.n, ld = I.ld, m = I.m;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int words = (n + 31) >> 5;
+  uint32_t* seen = acs_seen + (size_t)k * words;
+  const uint32_t it = (uint32_t)I.st->iteration;
+  const float tau0 = I.st->acs_tau0;
+  const float keep = __fsub_rn(1.0f, I.acs_xi), add = __fmul_rn(I.acs_xi, tau0);
+  int32_t* tour = I.tours + (size_t)k * I.ldt;
+
+  for (int w = lane; w < words; w += 32) seen[w] = 0u;
+  __syncwarp();
+  const Philox4 x0 = step_draw(I.seed, 0u, (uint32_t)k, it);
+  const int start = (int)__umulhi(x0.x0, (uint32_t)n);
+  if (lane == 0) {
+    seen[start >> 5] |= 1u << (start & 31);
+    tour[0] = start;
+  }
+  __syncwarp();
+  int cur = start;
+  for (int s = 1; s <= n; ++s) {
+    int next = start;
+    if (s < n) {
+      const Philox4 x = step_draw(I.seed, (uint32_t)s, (uint32_t)k, it);
+      const float* row = I.choice + (size_t)cur * ld;
+      // Lane l reads cities 4l..4l+3 of every 128 with one 16-byte load (ld
+      // is a multiple of 4, so the load stays inside the row); the three
+      // passes read the same lines, the later two from L1.  Loads after the
+      // CTA barrier see the local updates of the previous step.
+      // Pass 1: the largest unvisited weight, ties to the lower index: max of
+      // (bits(w) << 32 | ~j); the bits of non-negative floats order like
+      // their values.
+      unsigned long long key = 0ull;
+#pragma unroll 4
+      for (int j0 = 4 * lane; j0 < n; j0 += 128) {
+        const uint4 w4 = *reinterpret_cast<const uint4*>(row + j0);
+        const uint32_t fr = ~seen[j0 >> 5] >> (j0 & 31);  // 4 free bits (j0 % 4 == 0)
+        const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const unsigned long long kk =
+              ((unsigned long long)wv[e] << 32) | (0xffffffffu - (uint32_t)(j0 + e));
+          if (((fr >> e) & 1u) && j0 + e < n && kk > key) key = kk;
+        }
+      }
+      key = warp_max_u64(key);
+      const uint32_t mbits = (uint32_t)(key >> 32);
+      next = (int)(0xffffffffu - (uint32_t)key);
+      const bool exploit = (unsigned long long)x.x2 < I.acs_threshold;
+      if (!exploit && mbits != 0u) {
+        // Eq. 1 by the integer roulette: q_j = floor(w_j 2^(45 - ilogb M)),
+        // T = floor(r Q / 2^64), the first j whose prefix sum exceeds T.
+        const int sc = 45 - exponent_of_bits(mbits);
+        unsigned long long part = 0ull;
+#pragma unroll 4
+        for (int j0 = 4 * lane; j0 < n; j0 += 128) {
+          const uint4 w4 = *reinterpret_cast<const uint4*>(row + j0);
+          const uint32_t fr = ~seen[j0 >> 5] >> (j0 & 31);
+          const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (((fr >> e) & 1u) && j0 + e < n) part += acs_quant(wv[e], sc);
+        }
+        const unsigned long long Q = warp_sum_u64(part);
+        const unsigned long long r = ((unsigned long long)x.x1 << 32) | x.x0;
+        const unsigned long long T = __umul64hi(r, Q);
+        // Pass 3: 128 cities at a time in ascending order; a warp scan of the
+        // lanes' four-city sums finds the lane, the lane its city.
+        unsigned long long running = 0ull;
+        for (int c0 = 0; c0 < n; c0 += 128) {
+          const int j0 = c0 + 4 * lane;
+          unsigned long long q[4] = {0ull, 0ull, 0ull, 0ull};
+          if (j0 < n) {
+            const uint4 w4 = *reinterpret_cast<const uint4*>(row + j0);
+            const uint32_t fr = ~seen[j0 >> 5] >> (j0 & 31);
+            const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (((fr >> e) & 1u) && j0 + e < n) q[e] = acs_quant(wv[e], sc);
+          }
+          const unsigned long long mine = q[0] + q[1] + q[2] + q[3];
+          const unsigned long long incl = warp_incl_scan_u64(mine, lane);
+          const unsigned long long total = __shfl_sync(FULL, incl, 31);
+          if (running + total > T) {
+            const unsigned hit = __ballot_sync(FULL, running + incl > T);
+            const int L = __ffs(hit) - 1;
+            int pick = 0;
+            if (lane == L) {
+              unsigned long long c = running + incl - mine;
+              c += q[0];
+              if (c > T) {
+                pick = 0;
+              } else {
+                c += q[1];
+                if (c > T) {
+                  pick = 1;
+                } else {
+                  c += q[2];
+                  pick = c > T ? 2 : 3;
+                }
+              }
+            }
+            next = c0 + 4 * L + __shfl_sync(FULL, pick, L);
+            break;
+          }
+          running += total;
+        }
+      }
+      if ((unsigned)next >= (unsigned)n) {  // cannot happen while a city is unvisited
+        if (lane == 0) atomicOr(&I.st->status, kStatusBadTour);
+        next = start;
+      }
+    }
+    // lockstep: every ant has chosen from the same state; then the local
+    // updates of this step, one writer per distinct edge applying it once
+    // per ant that crossed the edge
+    const uint32_t lo = (uint32_t)min(cur, next), hi = (uint32_t)max(cur, next);
+    if (lane == 0) s_edge[k] = (lo << 16) | hi;
+    __syncthreads();
+    const uint32_t e = s_edge[k];
+    const unsigned same = __ballot_sync(FULL, lane < m && s_edge[lane < m ? lane : 0] == e);
+    if (lane == 0 && __ffs(same) - 1 == k) {
+      const size_t ab = (size_t)lo * ld + hi, ba = (size_t)hi * ld + lo;
+      float t = __ldcg(I.tau + ab);
+      for (int c = __popc(same); c > 0; --c) t = acs_local(t, keep, add);
+      const float ch = choice_of(t, I.heta[ab], I.alpha);
+      I.tau[ab] = t;
+      I.tau[ba] = t;
+      I.choice[ab] = ch;
+      I.choice[ba] = ch;
+    }
+    if (lane == 0 && s < n) {
+      seen[next >> 5] |= 1u << (next & 31);
+      tour[s] = next;
+    }
+    __syncthreads();
+    cur = next;
+  }
+  if (lane == 0) tour[n] = start;
+  __syncwarp();
+  long long len = 0;
+  for (int s = lane; s < n; s += 32) len += I.dist[(size_t)tour[s] * ld + tour[s + 1]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
+  if (lane == 0) I.lens[k] = len;
+}
+
+// Global update on the best-so-far tour: one thread per edge (each edge of
+// a closed tour of n >= 3 cities occurs once).
+__global__ void acs_global_kernel(Instance I, int bump_iteration) {
+  const int n = I.n, ld = I.ld;
+  const float keep = __fsub_rn(1.0f, I.rho);
+  const float dep = __fmul_rn(I.rho, (float)(1.0 / (double)I.st->best_len));
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int a = I.best_tour[s], b = I.best_tour[s + 1];
+    const size_t ab = (size_t)a * ld + b, ba = (size_t)b * ld + a;
+    const float t = __fadd_rn(__fmul_rn(keep, I.tau[ab]), dep);
+    const float ch = choice_of(t, I.heta[ab], I.alpha);
+    I.tau[ab] = t;
+    I.tau[ba] = t;
+    I.choice[ab] = ch;
+    I.choice[ba] = ch;
+  }
+  if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
+}
+
+// Start: tau = tau0 = (float)(1 / (n C_nn)) off the diagonal, choice_info.
+__global__ void acs_init_kernel(Instance I) {
+  const float tau0 = (float)(1.0 / ((double)I.n * (double)I.st->nn_len));
+  const int n = I.n, ld = I.ld;
+  const size_t total = (size_t)n * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ld), j = (int)(e % ld);
+    const float t = (j != i && j < n) ? tau0 : 0.0f;
+    I.tau[e] = t;
+    I.choice[e] = choice_of(t, I.heta[e], I.alpha);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) I.st->acs_tau0 = tau0;
+}
+
+cudaError_t launch_acs_init(const Instance& I, int sms, cudaStream_t st) {
+  size_t blocks = ((size_t)I.n * I.ld + 255) / 256;
+  if (blocks > (size_t)sms * 8) blocks = (size_t)sms * 8;
+  acs_init_kernel<<<(int)blocks, 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_acs_construct(const Instance& I, cudaStream_t st) {
+  if (I.m < 1 || I.m > kAcsMaxAnts) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)I.m * ((I.n + 31) / 32) * sizeof(uint32_t);
+  acs_construct_kernel<<<1, 32 * I.m, smem, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_acs_global(const Instance& I, cudaStream_t st) {
+  acs_global_kernel<<<(I.n + 255) / 256, 256, 0, st>>>(I, 1);
+  return cudaGetLastError();
+}
+
+}  // namespace aco

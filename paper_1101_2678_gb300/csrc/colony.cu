@@ -202,7 +202,9 @@ static int enqueue_construct(aco_colony* h) {
   cudaError_t e;
   if (h->profile && (e = record_event(h, h->ev[0], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
-  e = h->I.nn > 0 ? launch_construct_nn(h->I, h->stream) : launch_construct(h->I, t, h->stream);
+  e = h->I.variant == kVariantAcs ? launch_acs_construct(h->I, h->stream)
+      : h->I.nn > 0               ? launch_construct_nn(h->I, h->stream)
+                                  : launch_construct(h->I, t, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "construct");
   if (h->profile && (e = record_event(h, h->ev[1], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
@@ -221,7 +223,8 @@ static int enqueue_update(aco_colony* h) {
   if (h->profile && (e = record_event(h, h->ev[3], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
   e = variant == kVariantMmas ? launch_mmas_update(h->I, h->sms, h->stream)
-                              : launch_update(h->I, h->deposit, h->sms, h->stream);
+      : variant == kVariantAcs ? launch_acs_global(h->I, h->stream)
+                               : launch_update(h->I, h->deposit, h->sms, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "update");
   if (h->I.nn > 0 && (e = launch_nn_choice(h->I, h->stream)) != cudaSuccess)
     return cuda_fail(e, "nn choice");
@@ -570,6 +573,29 @@ int aco_set_mmas(aco_handle h, double p_best, int32_t best_so_far) {
   return check_status(h);
 }
 
+int aco_set_acs(aco_handle h, double q0, float xi) {
+  if (!h) return fail(ACO_EINVAL, "NULL handle");
+  if (!(q0 >= 0.0 && q0 <= 1.0)) return fail(ACO_EINVAL, "q0 must lie in [0, 1]");
+  if (!(xi >= 0.0f && xi <= 1.0f)) return fail(ACO_EINVAL, "xi must lie in [0, 1]");
+  if (h->I.m > kAcsMaxAnts)
+    return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants (m=%d)", kAcsMaxAnts,
+                h->I.m);
+  if (h->I.nn > 0 || h->I.rule != 0)
+    return fail(ACO_EINVAL, "the Ant Colony System uses its own rule (no lists, no selection option)");
+  if (h->constructed || h->host_iteration != 0 || h->I.variant != kVariantAs)
+    return fail(ACO_ESTATE, "the update rule is chosen once, before the first construction");
+  // floor(q0 2^32); q0 = 1 gives 2^32 (every step exploits).
+  h->I.acs_threshold = q0 >= 1.0 ? (1ull << 32)
+                       : q0 > 0.0 ? (unsigned long long)std::floor(q0 * 4294967296.0)
+                                  : 0ull;
+  h->I.acs_xi = xi;
+  h->I.variant = kVariantAcs;
+  drop_graph(h);
+  cudaError_t e = launch_acs_init(h->I, h->sms, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "acs init");
+  return check_status(h);
+}
+
 int aco_get_mmas_limits(aco_handle h, float* tau_min, float* tau_max) {
   if (!h) return fail(ACO_EINVAL, "NULL handle");
   if (h->I.variant != kVariantMmas) return fail(ACO_ESTATE, "the handle runs the Ant System");
@@ -601,6 +627,8 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
         return fail(ACO_EINVAL, "nearest-neighbour list length must be in [0, %d]", most);
       if (value > 0 && h->I.rule != 0)
         return fail(ACO_EINVAL, "nearest-neighbour lists use Eq. 1 (ACO_SELECT_EQ1)");
+      if (value > 0 && h->I.variant == kVariantAcs)
+        return fail(ACO_EINVAL, "the Ant Colony System uses its own construction");
       cudaError_t e = cudaSuccess;
       if (value > 0 && !h->nn_lists_built) {
         e = launch_nn_lists(h->I, most, h->stream);
@@ -617,6 +645,8 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
         return fail(ACO_EINVAL, "selection rule %lld", (long long)value);
       if (value != ACO_SELECT_EQ1 && h->I.nn > 0)
         return fail(ACO_EINVAL, "nearest-neighbour lists use Eq. 1 (ACO_SELECT_EQ1)");
+      if (value != ACO_SELECT_EQ1 && h->I.variant == kVariantAcs)
+        return fail(ACO_EINVAL, "the Ant Colony System uses its own construction");
       const int old = h->I.rule;
       h->I.rule = (int)value;
       if (!tiling_ok(tiling_of(h), h->I.rule)) {

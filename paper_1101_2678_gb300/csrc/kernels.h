@@ -41,6 +41,12 @@ int launches_for_variant(int variant);
 // depositing tour's dtau, clamp, choice_info).
 cudaError_t launch_mmas_init(const Instance& I, int sms, cudaStream_t st);
 cudaError_t launch_mmas_update(const Instance& I, int sms, cudaStream_t st);
+// Ant Colony System: trails to 1/(n C_nn); construction with the local
+// update (one CTA, m <= kAcsMaxAnts); the global update on the best tour.
+constexpr int kAcsMaxAnts = 32;
+cudaError_t launch_acs_init(const Instance& I, int sms, cudaStream_t st);
+cudaError_t launch_acs_construct(const Instance& I, cudaStream_t st);
+cudaError_t launch_acs_global(const Instance& I, cudaStream_t st);
 int gather_warps_per_cta(int ld);
 
 // Per-(G, H) dispatchers (one translation unit each, compiled in parallel).

@@ -117,8 +117,15 @@ struct aco_pool {
   struct Class {
     ConstructTiling t;
     int begin, count;
+    std::tuple<int, int, int> key;  // the default tiling's (G, H, C)
+    int max_n;
   };
   std::vector<Class> classes;
+  // Autotuner: for each default class, the (G, H, ants per CTA) that measured
+  // fastest on the first live set that contained the class.
+  bool autotune = true;
+  bool tuned_pending = false;
+  std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;
   int max_ld = 4;
   bool dirty = true;
   cudaGraphExec_t exec = nullptr;
@@ -210,7 +217,19 @@ static int pool_rebuild(aco_pool* p) {
   }
   for (const auto& key : class_order) {
     aco_pool::Class c;
-    c.t = batched_construct_tiling(p->slots[(size_t)by_class[key][0]].n);
+    c.key = key;
+    c.max_n = p->slots[(size_t)by_class[key][0]].n;
+    c.t = batched_construct_tiling(c.max_n);
+    if (p->autotune) {
+      auto it = p->tuned.find(key);
+      if (it == p->tuned.end()) {
+        p->tuned_pending = true;
+      } else {
+        const ConstructTiling t = construct_tiling(c.max_n, std::get<0>(it->second),
+                                                   std::get<1>(it->second), std::get<2>(it->second));
+        if (t.C != 0) c.t = t;
+      }
+    }
     c.begin = (int)p->h_items.size();
     for (int s : by_class[key])
       for (int k = 0; k < p->slots[(size_t)s].m; ++k) p->h_items.push_back(make_int2(s, k));
@@ -240,6 +259,64 @@ static int pool_rebuild(aco_pool* p) {
   if (e != cudaSuccess) return cuda_fail(e, "pool lists");
   pool_drop_graph(p);
   p->dirty = false;
+  return ACO_OK;
+}
+
+// The autotuner.  For every class not tuned yet, each candidate tiling
+// (whole warps with 1, 2 or 4 warps per ant; 8- or 16-lane segments) builds
+// the class's tours twice on the pool stream and the second run is timed;
+// the fastest is kept for the class from then on.  Every tiling builds the
+// same tours (the selection is exact integer arithmetic), so the trial runs
+// change nothing: the step that follows rebuilds the same tours.
+static int pool_autotune(aco_pool* p) {
+  static const int kCand[][3] = {{1, 32, 4}, {2, 32, 2}, {4, 32, 1}, {1, 16, 8}, {1, 8, 16}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (auto& c : p->classes) {
+    if (e != cudaSuccess) break;
+    if (p->tuned.count(c.key)) continue;
+    float best_ms = 0.0f;
+    int bi = -1;
+    for (int i = 0; i < (int)(sizeof kCand / sizeof kCand[0]) && e == cudaSuccess; ++i) {
+      const ConstructTiling t = construct_tiling(c.max_n, kCand[i][0], kCand[i][1], kCand[i][2]);
+      if (t.C == 0 || t.W < 1 || t.W > 8 || ants_per_cta(t) < 1) continue;
+      float ms = 0.0f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        if (rep == 1) e = cudaEventRecord(e0, p->stream);
+        if (e == cudaSuccess)
+          e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, t, p->stream);
+        if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e1, p->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (bi < 0 || ms < best_ms)) {
+        best_ms = ms;
+        bi = i;
+      }
+    }
+    if (e == cudaSuccess && bi >= 0) {
+      p->tuned[c.key] = std::make_tuple(kCand[bi][0], kCand[bi][1], kCand[bi][2]);
+      c.t = construct_tiling(c.max_n, kCand[bi][0], kCand[bi][1], kCand[bi][2]);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  p->tuned_pending = false;
+  if (e != cudaSuccess) return cuda_fail(e, "pool autotune");
+  return ACO_OK;
+}
+
+// Order the pool stream after the setup of newly admitted instances.
+static int pool_wait_ready(aco_pool* p) {
+  for (int s : p->h_live) {
+    PoolSlot& sl = p->slots[(size_t)s];
+    if (sl.wait_ready) {
+      const cudaError_t e = cudaStreamWaitEvent(p->stream, sl.ready, 0);
+      if (e != cudaSuccess) return cuda_fail(e, "wait setup");
+      sl.wait_ready = false;
+    }
+  }
   return ACO_OK;
 }
 
@@ -476,14 +553,8 @@ int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
   if (p->dirty && (rc = pool_rebuild(p)) != ACO_OK) return rc;
   cudaError_t e;
   if (!p->h_live.empty()) {
-    for (int s : p->h_live) {
-      PoolSlot& sl = p->slots[(size_t)s];
-      if (sl.wait_ready) {
-        if ((e = cudaStreamWaitEvent(p->stream, sl.ready, 0)) != cudaSuccess)
-          return cuda_fail(e, "wait setup");
-        sl.wait_ready = false;
-      }
-    }
+    if ((rc = pool_wait_ready(p)) != ACO_OK) return rc;
+    if (p->tuned_pending && (rc = pool_autotune(p)) != ACO_OK) return rc;
     if (!p->exec) {
       cudaGraph_t g = nullptr;
       if ((e = cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
@@ -544,6 +615,44 @@ int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t* tour, int64_t* len
     e = cudaMemcpyAsync(len, &sl.I.st->best_len, 8, cudaMemcpyDeviceToHost, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "pool result");
   return pool_check_status(p, slot);
+}
+
+int aco_pool_set_autotune(aco_pool_handle p, int32_t on) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (on != 0 && on != 1) return fail(ACO_EINVAL, "on must be 0 or 1");
+  p->autotune = on != 0;
+  if (!p->autotune) p->tuned.clear();
+  p->dirty = true;
+  return ACO_OK;
+}
+
+int aco_pool_autotune(aco_pool_handle p) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  int rc;
+  if (p->dirty && (rc = pool_rebuild(p)) != ACO_OK) return rc;
+  if (p->h_live.empty() || !p->tuned_pending) return ACO_OK;
+  if ((rc = pool_wait_ready(p)) != ACO_OK) return rc;
+  if ((rc = pool_autotune(p)) != ACO_OK) return rc;
+  pool_drop_graph(p);
+  return ACO_OK;
+}
+
+int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t* warps_per_ant,
+                    int32_t* lanes_per_ant, int32_t* cities_per_lane) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
+    return fail(ACO_EINVAL, "slot %d is not live", slot);
+  if (p->dirty) return fail(ACO_ESTATE, "no step has run since the live set changed");
+  const int n = p->slots[(size_t)slot].n;
+  for (const auto& c : p->classes)
+    if (c.key == std::make_tuple(batched_construct_tiling(n).G, batched_construct_tiling(n).H,
+                                 batched_construct_tiling(n).C)) {
+      if (warps_per_ant) *warps_per_ant = c.t.G;
+      if (lanes_per_ant) *lanes_per_ant = c.t.H;
+      if (cities_per_lane) *cities_per_lane = c.t.C;
+      return ACO_OK;
+    }
+  return fail(ACO_ESTATE, "slot %d has no class", slot);
 }
 
 int aco_pool_pheromone(aco_pool_handle p, int32_t slot, float* tau) {

@@ -164,3 +164,31 @@ def test_server_results_equal_alone(aco):
             aco.aco_iterate(c.h, r.iterations)
             tour, length = aco.aco_best_tour(c.h, r.n)
         assert o.best_len == length and np.array_equal(o.best_tour, tour), o.index
+
+
+def test_autotuned_tilings_give_identical_results(aco):
+    # The tuner picks per class among tilings that all build the same tours;
+    # a batch with tuning on and one with it off end in the same state.
+    ns = [48, 130, 300, 700, 1000]
+    insts = [I.uniform_instance(n, 1000, seed=900 + n) for n in ns]
+    ms = ns
+    seeds = [31 + i for i in range(len(ns))]
+    out = {}
+    for on in (True, False):
+        b = aco.aco_batch_create([x.dist for x in insts], ms, seeds)
+        try:
+            aco.aco_pool_set_autotune(b, on)
+            aco.aco_pool_autotune(b)
+            tilings = [aco.aco_pool_tiling(b, i) for i in range(len(ns))]
+            for (g, h, c), n in zip(tilings, ns):
+                assert g in (1, 2, 4) and h in (8, 16, 32) and (h == 32 or g == 1)
+                assert g * h * c >= n
+                if not on:
+                    assert (g, h) == (1, 32)
+            aco.aco_batch_iterate(b, 4)
+            out[on] = [(aco.aco_pool_pheromone(b, i, n), aco.aco_batch_best(b, i, n))
+                       for i, n in enumerate(ns)]
+        finally:
+            aco.aco_batch_destroy(b)
+    for (ta, (tra, la)), (tb, (trb, lb)) in zip(out[True], out[False]):
+        assert np.array_equal(ta, tb) and la == lb and np.array_equal(tra, trb)
