@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--warps-per-ant", type=int, default=0, help="0 = library default")
     ap.add_argument("--ants-per-cta", type=int, default=0, help="0 = library default")
     ap.add_argument("--lanes-per-ant", type=int, default=0, help="0 = library default (32)")
+    ap.add_argument("--staging", type=int, default=-1,
+                    help="row staging of the construction kernel: 0 bulk copy (TMA), "
+                         "1 lane copies; -1 = library default")
     ap.add_argument("--nn", type=int, default=0,
                     help="nearest-neighbour list length (0 = every unvisited city)")
     ap.add_argument("--variant", default="as", choices=["as", "mmas", "acs"],
@@ -333,6 +336,8 @@ def run_ours(args, w, rank, world, local):
         aco.aco_set_option(h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
     if args.nn:
         aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, args.nn)
+    if args.staging >= 0:
+        aco.aco_set_option(h, aco.ACO_OPT_STAGING, args.staging)
     if args.variant == "mmas":
         aco.aco_set_mmas(h, 0.05, False)
     elif args.variant == "acs":
@@ -345,6 +350,7 @@ def run_ours(args, w, rank, world, local):
               aco.aco_get_option(h, aco.ACO_OPT_ANTS_PER_CTA),
               aco.aco_get_option(h, aco.ACO_OPT_LANES_PER_ANT))
     launches = aco.aco_kernel_launches_per_iteration(h)
+    staging = aco.aco_get_option(h, aco.ACO_OPT_STAGING)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -412,6 +418,7 @@ def run_ours(args, w, rank, world, local):
                    "warps_per_ant": tiling[0], "ants_per_cta": tiling[1],
                    "lanes_per_ant": tiling[2], "selection": args.selection, "nn_list": args.nn,
                    "variant": args.variant,
+                   "staging": staging,
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "flushed between steps (256 MB write)"},
         "construct_ant_steps_per_s": m * (n - 1) / (con_ms / 1e3),

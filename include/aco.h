@@ -81,6 +81,13 @@ extern "C" {
 #define ACO_OPT_LANES_PER_ANT 7 /* 0 (default) = 32; 8 or 16: 32/H ants share a
                                   warp (one warp per ant group)                */
 #define ACO_OPT_SELECTION 8    /* ACO_SELECT_* below; default ACO_SELECT_EQ1     */
+#define ACO_OPT_STAGING 10     /* how the construction kernel brings row
+                                  choice[cur] into shared memory at each step:
+                                  0 one bulk copy (TMA engine, cp.async.bulk)
+                                  completing on an mbarrier; 1 coalesced
+                                  16-byte loads by the ant's threads.  Default:
+                                  1 for n <= 64, else 0 (the faster measured
+                                  on GB300).  Results are identical.          */
 #define ACO_OPT_NN_LIST 9      /* 0 (default): every unvisited city is a
                                   candidate.  k in [1, min(32, n-1)]: the
                                   nearest-neighbour-list construction (Section
@@ -377,7 +384,8 @@ int aco_pool_stats(aco_pool_handle p, int32_t *live, int32_t *finished, uint64_t
  * class is one construction launch per step.  With autotuning on (the
  * default), the first step that sees a class times each candidate tiling on
  * it (1, 2 or 4 warps per ant, or 8- or 16-lane segments with 4 or 2 ants per
- * warp; the second of two runs) and keeps the fastest for that class from
+ * warp, leaving out tilings with more than twice the default's city slots per
+ * ant; the second of two runs) and keeps the fastest for that class from
  * then on.  Every tiling builds the same tours, so tuning never changes a
  * result.
  *   aco_pool_set_autotune: on = 1 (default) or 0 (the default tiling always;

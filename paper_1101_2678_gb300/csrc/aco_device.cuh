@@ -35,6 +35,7 @@ struct Instance {
   float alpha, beta, rho;
   int rule;                     // 0: Eq. 1 (integer roulette); 1: product of a uniform and the
                                 // weight, highest wins (the paper's data-parallel kernel)
+  int stage;                    // row staging: 0 bulk copy (TMA) + mbarrier, 1 lane copies
   unsigned long long seed;
   const int32_t* dist;          // [n][ld]
   float* heta;                  // [n][ld]  eta^beta

@@ -283,9 +283,16 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   }
   group_wait();
 
+  const bool lane_copy = I.stage != 0;
   for (int s = 1; s < n; ++s) {
     // Everyone is done with the previous row (the group agreed on `cur`).
-    if (tg == 0) {
+    if (lane_copy) {
+      // The group copies the row with coalesced 16-byte loads (through L1,
+      // so a row another group of this SM read recently may hit there).
+      const float4* src = reinterpret_cast<const float4*>(I.choice + (size_t)cur * ld);
+      float4* dst = reinterpret_cast<float4*>(srow);
+      for (int i = tg; i < (ld >> 2); i += NT) dst[i] = src[i];
+    } else if (tg == 0) {
       fence_proxy_async_smem();
       bulk_load(srow_a, I.choice + (size_t)cur * ld, row_bytes, bar);
     }
@@ -295,11 +302,15 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       rwin = ((unsigned long long)x.x1 << 32) | x.x0;
     }
     const unsigned long long r = seg.shfl(rwin, off);
-    if (waits_ok && !mbar_wait_bounded(bar, phase)) {
-      waits_ok = false;  // stale data from here on; the status word says so
-      if (tg == 0) atomicOr(&I.st->status, kStatusTimeout);
+    if (lane_copy) {
+      group_wait();
+    } else {
+      if (waits_ok && !mbar_wait_bounded(bar, phase)) {
+        waits_ok = false;  // stale data from here on; the status word says so
+        if (tg == 0) atomicOr(&I.st->status, kStatusTimeout);
+      }
+      phase ^= 1u;
     }
-    phase ^= 1u;
     const float* row = srow;
 
     uint32_t v[C];  // weight bits; w >= 0 orders like its bit pattern

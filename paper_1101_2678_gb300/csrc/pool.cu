@@ -278,9 +278,13 @@ static int pool_autotune(aco_pool* p) {
     if (p->tuned.count(c.key)) continue;
     float best_ms = 0.0f;
     int bi = -1;
+    const ConstructTiling d = batched_construct_tiling(c.max_n);
     for (int i = 0; i < (int)(sizeof kCand / sizeof kCand[0]) && e == cudaSuccess; ++i) {
       const ConstructTiling t = construct_tiling(c.max_n, kCand[i][0], kCand[i][1], kCand[i][2]);
       if (t.C == 0 || t.W < 1 || t.W > 8 || ants_per_cta(t) < 1) continue;
+      // a tiling with more than twice the default's city slots per ant only
+      // adds masked-off work: not worth a trial
+      if (t.G * t.H * t.C > 2 * d.G * d.H * d.C) continue;
       float ms = 0.0f;
       for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
         if (rep == 1) e = cudaEventRecord(e0, p->stream);

@@ -85,9 +85,12 @@ def test_first_iteration_tours_match_oracle(aco, orc, n):
                     aco.aco_set_option(c.h, aco.ACO_OPT_ANTS_PER_CTA, A)
                 except aco.AcoError:
                     continue  # no tiling for this n with these options
-            tours, lens = aco.aco_construct_tours(c.h, n, m)
-            assert np.array_equal(tours, otours), (G, H, A)
-            assert np.array_equal(lens, olens), (G, H, A)
+            for stage in (0, 1):
+                aco.aco_set_option(c.h, aco.ACO_OPT_STAGING, stage)
+                tours, lens = aco.aco_construct_tours(c.h, n, m)
+                assert np.array_equal(tours, otours), (G, H, A, stage)
+                assert np.array_equal(lens, olens), (G, H, A, stage)
+            aco.aco_set_option(c.h, aco.ACO_OPT_STAGING, 0)
 
 
 @pytest.mark.parametrize("wl,ants", [("n1002", 12), ("n2392", 6)])
