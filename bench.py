@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="n1002", choices=sorted(WORKLOADS))
-    ap.add_argument("--deposit", default="sym", choices=["gather", "u64", "f32", "sym"])
+    ap.add_argument("--deposit", default="sym", choices=["gather", "u64", "f32", "sym", "sort"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -322,7 +322,8 @@ def run_ours(args, w, rank, world, local):
     if args.variant == "acs":
         m = min(m, 10)  # the Ant Colony System's usual colony (one CTA, m <= 32)
     dep = {"gather": aco.ACO_DEPOSIT_GATHER, "u64": aco.ACO_DEPOSIT_ATOMIC_U64,
-           "f32": aco.ACO_DEPOSIT_ATOMIC_F32, "sym": aco.ACO_DEPOSIT_SYMMETRIC}[args.deposit]
+           "f32": aco.ACO_DEPOSIT_ATOMIC_F32, "sym": aco.ACO_DEPOSIT_SYMMETRIC,
+           "sort": aco.ACO_DEPOSIT_SORT}[args.deposit]
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     col = aco.Colony(d, m, seed=w["seed"] + rank, alpha=w["alpha"], beta=w["beta"], rho=w["rho"])
@@ -541,9 +542,9 @@ def run_batched(args, rank, world, local):
     t_tune = time.perf_counter() - t_tune
     tilings = {}
     for i, x in enumerate(insts):
-        g, hh, c = aco.aco_pool_tiling(b, i)
-        tilings.setdefault(f"G{g}H{hh}C{c}", 0)
-        tilings[f"G{g}H{hh}C{c}"] += 1
+        g, hh, c, sg = aco.aco_pool_tiling(b, i)
+        key = f"G{g}H{hh}C{c}S{sg}"
+        tilings[key] = tilings.get(key, 0) + 1
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.start()

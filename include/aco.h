@@ -121,6 +121,17 @@ extern "C" {
                                   evaporation (the paper's atomic kernel; the
                                   order of additions, hence the last bits of
                                   tau, is not deterministic)                   */
+#define ACO_DEPOSIT_SORT 4     /* atomic-free scatter-to-gather by sorting
+                                  (Section III-B's idea without its n^4
+                                  loads): each tour edge becomes the key
+                                  min(a,b)*n + max(a,b) with its ant as value,
+                                  a stable LSD radix sort (8-bit digits) groups
+                                  equal edges, one thread per run of equal
+                                  keys sums q_k exactly, and the symmetric
+                                  apply pass finishes the update.  Bit-exact
+                                  with the other deterministic variants.
+                                  Allocates 16 bytes per (ant, city) of
+                                  scratch when first selected.                */
 #define ACO_DEPOSIT_SYMMETRIC 3  /* the paper's "Reduction" version (Section
                                   III-B): for the symmetric TSP the edge (a,b)
                                   adds q_k once, to the upper-triangle cell
@@ -385,8 +396,8 @@ int aco_pool_stats(aco_pool_handle p, int32_t *live, int32_t *finished, uint64_t
  * default), the first step that sees a class times each candidate tiling on
  * it (1, 2 or 4 warps per ant, or 8- or 16-lane segments with 4 or 2 ants per
  * warp, leaving out tilings with more than twice the default's city slots per
- * ant; the second of two runs) and keeps the fastest for that class from
- * then on.  Every tiling builds the same tours, so tuning never changes a
+ * ant; each with either row staging of ACO_OPT_STAGING; the second of two
+ * runs) and keeps the fastest for that class from then on.  Every tiling builds the same tours, so tuning never changes a
  * result.
  *   aco_pool_set_autotune: on = 1 (default) or 0 (the default tiling always;
  *     forgets earlier choices).
@@ -394,13 +405,14 @@ int aco_pool_stats(aco_pool_handle p, int32_t *live, int32_t *finished, uint64_t
  *     set not tuned yet (otherwise it runs inside the next aco_pool_step);
  *     it builds tours but advances no iteration.
  *   aco_pool_tiling: the tiling the class of live `slot` uses: warps per ant,
- *     lanes per ant and cities per lane (any output may be NULL);
+ *     lanes per ant, cities per lane and row staging (0 bulk copy, 1 lane
+ *     copies); any output may be NULL;
  *     ACO_ESTATE before the first step after the live set changed.
  */
 int aco_pool_set_autotune(aco_pool_handle p, int32_t on);
 int aco_pool_autotune(aco_pool_handle p);
 int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t *warps_per_ant,
-                    int32_t *lanes_per_ant, int32_t *cities_per_lane);
+                    int32_t *lanes_per_ant, int32_t *cities_per_lane, int32_t *staging);
 
 /* aco_pool_synchronize - wait for all pool work and report device-side errors. */
 int aco_pool_synchronize(aco_pool_handle p);

@@ -42,6 +42,7 @@ ACO_DEPOSIT_GATHER = 0
 ACO_DEPOSIT_ATOMIC_U64 = 1
 ACO_DEPOSIT_ATOMIC_F32 = 2
 ACO_DEPOSIT_SYMMETRIC = 3
+ACO_DEPOSIT_SORT = 4
 
 ACO_PHASE_CONSTRUCT = 0
 ACO_PHASE_BEST = 1
@@ -95,7 +96,7 @@ SIGNATURES = [
     ("aco_pool_synchronize", C.c_int, [_vp]),
     ("aco_pool_set_autotune", C.c_int, [_vp, C.c_int32]),
     ("aco_pool_autotune", C.c_int, [_vp]),
-    ("aco_pool_tiling", C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p]),
+    ("aco_pool_tiling", C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p, _i32p]),
     ("aco_batch_create", C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     ("aco_batch_iterate", C.c_int, [_vp, C.c_int32]),
     ("aco_batch_best", C.c_int, [_vp, C.c_int32, _vp, _vp]),
@@ -366,10 +367,11 @@ def aco_pool_autotune(p) -> None:
 
 
 def aco_pool_tiling(p, slot: int):
-    """(warps per ant, lanes per ant, cities per lane) of the class of live `slot`."""
-    g, h, c = C.c_int32(), C.c_int32(), C.c_int32()
-    _check(load().aco_pool_tiling(p, slot, C.byref(g), C.byref(h), C.byref(c)), "aco_pool_tiling")
-    return g.value, h.value, c.value
+    """(warps per ant, lanes per ant, cities per lane, staging) of the class of live `slot`."""
+    g, h, c, s = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().aco_pool_tiling(p, slot, C.byref(g), C.byref(h), C.byref(c), C.byref(s)),
+           "aco_pool_tiling")
+    return g.value, h.value, c.value, s.value
 
 
 def aco_batch_create(dists, ms, seeds, alpha=1.0, beta=2.0, rho=0.5):

@@ -27,6 +27,10 @@ int fail(int code, const char* fmt, ...) {
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
+  // Clear the runtime's last-error state so that a later, unrelated launch
+  // check does not report this error again (a failed allocation is not
+  // sticky).
+  (void)cudaGetLastError();
   return fail(e == cudaErrorMemoryAllocation ? ACO_ENOMEM : ACO_ECUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
@@ -100,11 +104,11 @@ cudaError_t launch_construct(const Instance& I, ConstructTiling t, cudaStream_t 
 cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
                                    ConstructTiling t, cudaStream_t st) {
   if (t.W < 1 || t.W > 8) return cudaErrorInvalidValue;
-  if (t.G == 1 && t.H == 8) return launch_construct_items_g1h8(insts, items, count, t.C, t.W, st);
-  if (t.G == 1 && t.H == 16) return launch_construct_items_g1h16(insts, items, count, t.C, t.W, st);
-  if (t.G == 1 && t.H == 32) return launch_construct_items_g1h32(insts, items, count, t.C, t.W, st);
-  if (t.G == 2 && t.H == 32) return launch_construct_items_g2h32(insts, items, count, t.C, t.W, st);
-  if (t.G == 4 && t.H == 32) return launch_construct_items_g4h32(insts, items, count, t.C, t.W, st);
+  if (t.G == 1 && t.H == 8) return launch_construct_items_g1h8(insts, items, count, t.C, t.W, t.S, st);
+  if (t.G == 1 && t.H == 16) return launch_construct_items_g1h16(insts, items, count, t.C, t.W, t.S, st);
+  if (t.G == 1 && t.H == 32) return launch_construct_items_g1h32(insts, items, count, t.C, t.W, t.S, st);
+  if (t.G == 2 && t.H == 32) return launch_construct_items_g2h32(insts, items, count, t.C, t.W, t.S, st);
+  if (t.G == 4 && t.H == 32) return launch_construct_items_g4h32(insts, items, count, t.C, t.W, t.S, st);
   return cudaErrorInvalidValue;
 }
 
@@ -160,6 +164,7 @@ struct aco_colony {
   long long host_iteration = 0;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[ACO_NUM_PHASES + 1] = {};
+  void* sort_scratch = nullptr;  // keys, values and digit counts of the sort deposit
 };
 
 static ConstructTiling tiling_of(const aco_colony* h) {
@@ -217,14 +222,19 @@ static int enqueue_construct(aco_colony* h) {
 static int enqueue_update(aco_colony* h) {
   cudaError_t e;
   const int variant = h->I.variant;
-  if (variant == kVariantAs &&
-      (e = launch_deposit(h->I, h->deposit, h->sms, h->stream)) != cudaSuccess)
-    return cuda_fail(e, "deposit");
+  if (variant == kVariantAs) {
+    e = h->deposit == kDepositSort ? launch_sort_deposit(h->I, h->sort_scratch, h->sms, h->stream)
+                                   : launch_deposit(h->I, h->deposit, h->sms, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "deposit");
+  }
   if (h->profile && (e = record_event(h, h->ev[3], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
   e = variant == kVariantMmas ? launch_mmas_update(h->I, h->sms, h->stream)
       : variant == kVariantAcs ? launch_acs_global(h->I, h->stream)
-                               : launch_update(h->I, h->deposit, h->sms, h->stream);
+                               : launch_update(h->I,
+                                               h->deposit == kDepositSort ? kDepositSymmetric
+                                                                          : h->deposit,
+                                               h->sms, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "update");
   if (h->I.nn > 0 && (e = launch_nn_choice(h->I, h->stream)) != cudaSuccess)
     return cuda_fail(e, "nn choice");
@@ -417,6 +427,7 @@ int aco_destroy(aco_handle h) {
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   if (h->arena) cudaFree(h->arena);
+  if (h->sort_scratch) cudaFree(h->sort_scratch);
   delete h;
   return ACO_OK;
 }
@@ -616,7 +627,14 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
   if (!h) return fail(ACO_EINVAL, "NULL handle");
   switch (key) {
     case ACO_OPT_DEPOSIT:
-      if (value < 0 || value > 3) return fail(ACO_EINVAL, "deposit variant %lld", (long long)value);
+      if (value < 0 || value > 4) return fail(ACO_EINVAL, "deposit variant %lld", (long long)value);
+      if (value == kDepositSort && !h->sort_scratch) {
+        const cudaError_t e = cudaMalloc(&h->sort_scratch, sort_deposit_bytes(h->I.n, h->I.m));
+        if (e != cudaSuccess) {
+          h->sort_scratch = nullptr;
+          return cuda_fail(e, "sort deposit scratch");
+        }
+      }
       h->deposit = (int)value;
       break;
     case ACO_OPT_STREAM:
@@ -753,7 +771,9 @@ int aco_synchronize(aco_handle h) {
 
 int aco_kernel_launches_per_iteration(aco_handle h, int32_t* count) {
   if (!h || !count) return fail(ACO_EINVAL, "NULL argument");
-  *count = (h->I.variant != kVariantAs ? 3 : launches_for_variant(h->deposit)) +
+  *count = (h->I.variant != kVariantAs     ? 3
+            : h->deposit == kDepositSort ? 3 + sort_deposit_launches(h->I.n)
+                                         : launches_for_variant(h->deposit)) +
            (h->I.nn > 0 ? 1 : 0);
   return ACO_OK;
 }

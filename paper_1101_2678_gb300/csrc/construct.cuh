@@ -217,7 +217,7 @@ __host__ __device__ constexpr int groups_per_cta(int warps) {
 template <int C, int G, int H, int R = 0>
 __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, const int tg,
                                               const Seg<H> seg, GroupSmem* gs, const int bar_id,
-                                              float* srow) {
+                                              float* srow, const bool lane_copy) {
   static_assert(C % 4 == 0 && C >= 4 && C <= 128, "C must be a multiple of 4 in [4,128]");
   static_assert((C / 4) % 2 == 1, "C/4 must be odd: lanes then read their chunks from shared "
                                   "memory without bank conflicts");
@@ -283,7 +283,6 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   }
   group_wait();
 
-  const bool lane_copy = I.stage != 0;
   for (int s = 1; s < n; ++s) {
     // Everyone is done with the previous row (the group agreed on `cur`).
     if (lane_copy) {
@@ -561,15 +560,17 @@ __global__ void __launch_bounds__(256) construct_kernel(Instance I) {
   const int ant = blockIdx.x * groups_per_cta<G, H>(blockDim.x >> 5) + grp;
   if (ant >= I.m) return;
   construct_ant<C, G, H, R>(I, ant, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
-                            reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes));
+                            reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes),
+                            I.stage != 0);
 }
 
 // Batched form: group g of block b builds ant items[b*A + g].y of instance
-// insts[items[b*A + g].x].  Items are listed longest instance first.
+// insts[items[b*A + g].x].  Items are listed longest instance first.  The
+// row staging is chosen per launch (`lane_copy`), not per instance.
 template <int C, int G, int H>
 __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __restrict__ insts,
                                                               const int2* __restrict__ items,
-                                                              int count) {
+                                                              int count, int lane_copy) {
   __shared__ GroupSmem gs[kMaxGroupsPerCta];
   extern __shared__ __align__(16) unsigned char stage[];
   int grp, tg;
@@ -581,7 +582,8 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
   // a register copy of the whole descriptor, which cost ~40 registers.
   const Instance& I = insts[it.x];
   construct_ant<C, G, H>(I, it.y, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
-                         reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes));
+                         reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes),
+                         lane_copy != 0);
 }
 
 // Dynamic shared memory for a CTA of `warps` warps, with the opt-in above

@@ -66,7 +66,7 @@ cudaError_t launch_construct_g1h32(const Instance& I, int C, int warps, cudaStre
 }
 
 cudaError_t launch_construct_items_g1h32(const Instance* insts, const int2* items, int count,
-                                          int C, int warps, cudaStream_t st) {
+                                          int C, int warps, int lane_copy, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   const int per_cta = groups_per_cta<1, 32>(warps);
   const int grid = (count + per_cta - 1) / per_cta;
@@ -74,52 +74,52 @@ cudaError_t launch_construct_items_g1h32(const Instance* insts, const int2* item
   switch (C) {
     case 4: {
       const size_t smem = construct_smem_setup<4, 1, 32, true>(warps);
-      construct_items_kernel<4, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<4, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 12: {
       const size_t smem = construct_smem_setup<12, 1, 32, true>(warps);
-      construct_items_kernel<12, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<12, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 20: {
       const size_t smem = construct_smem_setup<20, 1, 32, true>(warps);
-      construct_items_kernel<20, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<20, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 28: {
       const size_t smem = construct_smem_setup<28, 1, 32, true>(warps);
-      construct_items_kernel<28, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<28, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 36: {
       const size_t smem = construct_smem_setup<36, 1, 32, true>(warps);
-      construct_items_kernel<36, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<36, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 44: {
       const size_t smem = construct_smem_setup<44, 1, 32, true>(warps);
-      construct_items_kernel<44, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<44, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 52: {
       const size_t smem = construct_smem_setup<52, 1, 32, true>(warps);
-      construct_items_kernel<52, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<52, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 60: {
       const size_t smem = construct_smem_setup<60, 1, 32, true>(warps);
-      construct_items_kernel<60, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<60, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 68: {
       const size_t smem = construct_smem_setup<68, 1, 32, true>(warps);
-      construct_items_kernel<68, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<68, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 76: {
       const size_t smem = construct_smem_setup<76, 1, 32, true>(warps);
-      construct_items_kernel<76, 1, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<76, 1, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     default:

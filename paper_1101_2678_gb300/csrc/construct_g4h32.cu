@@ -41,7 +41,7 @@ cudaError_t launch_construct_g4h32(const Instance& I, int C, int warps, cudaStre
 }
 
 cudaError_t launch_construct_items_g4h32(const Instance* insts, const int2* items, int count,
-                                          int C, int warps, cudaStream_t st) {
+                                          int C, int warps, int lane_copy, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   const int per_cta = groups_per_cta<4, 32>(warps);
   const int grid = (count + per_cta - 1) / per_cta;
@@ -49,27 +49,27 @@ cudaError_t launch_construct_items_g4h32(const Instance* insts, const int2* item
   switch (C) {
     case 4: {
       const size_t smem = construct_smem_setup<4, 4, 32, true>(warps);
-      construct_items_kernel<4, 4, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<4, 4, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 12: {
       const size_t smem = construct_smem_setup<12, 4, 32, true>(warps);
-      construct_items_kernel<12, 4, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<12, 4, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 20: {
       const size_t smem = construct_smem_setup<20, 4, 32, true>(warps);
-      construct_items_kernel<20, 4, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<20, 4, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 28: {
       const size_t smem = construct_smem_setup<28, 4, 32, true>(warps);
-      construct_items_kernel<28, 4, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<28, 4, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     case 36: {
       const size_t smem = construct_smem_setup<36, 4, 32, true>(warps);
-      construct_items_kernel<36, 4, 32><<<grid, threads, smem, st>>>(insts, items, count);
+      construct_items_kernel<36, 4, 32><<<grid, threads, smem, st>>>(insts, items, count, lane_copy);
       break;
     }
     default:

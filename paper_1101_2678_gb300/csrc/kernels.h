@@ -11,12 +11,14 @@ constexpr int kDepositGather = 0;
 constexpr int kDepositAtomicU64 = 1;
 constexpr int kDepositAtomicF32 = 2;
 constexpr int kDepositSymmetric = 3;
+constexpr int kDepositSort = 4;
 
 // Tiling of the construction kernel: C cities per thread, G warps per ant
 // group, H lanes per ant (H < 32: 32/H ants share a warp, G = 1), W warps
 // per CTA.
 struct ConstructTiling {
   int C, G, H, W;
+  int S = 0;  // row staging of batched launches: 0 bulk copy, 1 lane copies
 };
 
 // Smallest supported C for n cities with G warps and H lanes per ant, and
@@ -48,12 +50,18 @@ cudaError_t launch_acs_init(const Instance& I, int sms, cudaStream_t st);
 cudaError_t launch_acs_construct(const Instance& I, cudaStream_t st);
 cudaError_t launch_acs_global(const Instance& I, cudaStream_t st);
 int gather_warps_per_cta(int ld);
+// Atomic-free deposit by a radix sort of the tour edges (sort_deposit.cu):
+// scratch bytes for n cities and m ants, the deposit into the upper-triangle
+// accumulator (apply with the symmetric update), and its kernel launches.
+size_t sort_deposit_bytes(int n, int m);
+cudaError_t launch_sort_deposit(const Instance& I, void* scratch, int sms, cudaStream_t st);
+int sort_deposit_launches(int n);
 
 // Per-(G, H) dispatchers (one translation unit each, compiled in parallel).
 #define ACO_DECLARE_CONSTRUCT(tag)                                                              \
   cudaError_t launch_construct_##tag(const Instance& I, int C, int warps, cudaStream_t st);     \
   cudaError_t launch_construct_items_##tag(const Instance* insts, const int2* items, int count, \
-                                           int C, int warps, cudaStream_t st);
+                                           int C, int warps, int lane_copy, cudaStream_t st);
 ACO_DECLARE_CONSTRUCT(g1h8)
 ACO_DECLARE_CONSTRUCT(g1h16)
 ACO_DECLARE_CONSTRUCT(g1h32)

@@ -125,7 +125,7 @@ struct aco_pool {
   // fastest on the first live set that contained the class.
   bool autotune = true;
   bool tuned_pending = false;
-  std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;
+  std::map<std::tuple<int, int, int>, std::tuple<int, int, int, int>> tuned;
   int max_ld = 4;
   bool dirty = true;
   cudaGraphExec_t exec = nullptr;
@@ -225,8 +225,9 @@ static int pool_rebuild(aco_pool* p) {
       if (it == p->tuned.end()) {
         p->tuned_pending = true;
       } else {
-        const ConstructTiling t = construct_tiling(c.max_n, std::get<0>(it->second),
-                                                   std::get<1>(it->second), std::get<2>(it->second));
+        ConstructTiling t = construct_tiling(c.max_n, std::get<0>(it->second),
+                                             std::get<1>(it->second), std::get<2>(it->second));
+        t.S = std::get<3>(it->second);
         if (t.C != 0) c.t = t;
       }
     }
@@ -279,8 +280,11 @@ static int pool_autotune(aco_pool* p) {
     float best_ms = 0.0f;
     int bi = -1;
     const ConstructTiling d = batched_construct_tiling(c.max_n);
-    for (int i = 0; i < (int)(sizeof kCand / sizeof kCand[0]) && e == cudaSuccess; ++i) {
-      const ConstructTiling t = construct_tiling(c.max_n, kCand[i][0], kCand[i][1], kCand[i][2]);
+    const int ncand = (int)(sizeof kCand / sizeof kCand[0]);
+    for (int i = 0; i < 2 * ncand && e == cudaSuccess; ++i) {
+      ConstructTiling t = construct_tiling(c.max_n, kCand[i % ncand][0], kCand[i % ncand][1],
+                                           kCand[i % ncand][2]);
+      t.S = i / ncand;  // row staging: bulk copy, then lane copies
       if (t.C == 0 || t.W < 1 || t.W > 8 || ants_per_cta(t) < 1) continue;
       // a tiling with more than twice the default's city slots per ant only
       // adds masked-off work: not worth a trial
@@ -300,8 +304,10 @@ static int pool_autotune(aco_pool* p) {
       }
     }
     if (e == cudaSuccess && bi >= 0) {
-      p->tuned[c.key] = std::make_tuple(kCand[bi][0], kCand[bi][1], kCand[bi][2]);
-      c.t = construct_tiling(c.max_n, kCand[bi][0], kCand[bi][1], kCand[bi][2]);
+      const int* k = kCand[bi % ncand];
+      p->tuned[c.key] = std::make_tuple(k[0], k[1], k[2], bi / ncand);
+      c.t = construct_tiling(c.max_n, k[0], k[1], k[2]);
+      c.t.S = bi / ncand;
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -642,7 +648,7 @@ int aco_pool_autotune(aco_pool_handle p) {
 }
 
 int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t* warps_per_ant,
-                    int32_t* lanes_per_ant, int32_t* cities_per_lane) {
+                    int32_t* lanes_per_ant, int32_t* cities_per_lane, int32_t* staging) {
   if (!p) return fail(ACO_EINVAL, "NULL pool");
   if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
     return fail(ACO_EINVAL, "slot %d is not live", slot);
@@ -654,6 +660,7 @@ int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t* warps_per_ant,
       if (warps_per_ant) *warps_per_ant = c.t.G;
       if (lanes_per_ant) *lanes_per_ant = c.t.H;
       if (cities_per_lane) *cities_per_lane = c.t.C;
+      if (staging) *staging = c.t.S;
       return ACO_OK;
     }
   return fail(ACO_ESTATE, "slot %d has no class", slot);

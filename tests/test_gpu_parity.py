@@ -157,7 +157,7 @@ def test_chi_squared_first_move_on_gpu(aco, orc):
 # Pheromone update (Eqs. 2-4) and whole runs
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("deposit", ["GATHER", "ATOMIC_U64", "SYMMETRIC"])
+@pytest.mark.parametrize("deposit", ["GATHER", "ATOMIC_U64", "SYMMETRIC", "SORT"])
 def test_n48_hundred_iterations_bit_exact(aco, orc, deposit):
     w = I.workload_n48()
     d = w["inst"].dist
@@ -218,27 +218,29 @@ def test_float_atomic_deposit_within_rounding_bound(aco, orc):
 def test_deposit_variants_agree(aco):
     inst = I.uniform_instance(333, 1000, seed=8)
     out = {}
-    for v in ["GATHER", "ATOMIC_U64", "SYMMETRIC"]:
+    for v in ["GATHER", "ATOMIC_U64", "SYMMETRIC", "SORT"]:
         with aco.Colony(inst.dist, 333, seed=9) as c:
             aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, getattr(aco, "ACO_DEPOSIT_" + v))
             aco.aco_iterate(c.h, 8)
             out[v] = (aco.aco_get_pheromone(c.h, 333), aco.aco_best_tour(c.h, 333),
                       aco.aco_choice_info(c.h, 333))
-    for v in ["ATOMIC_U64", "SYMMETRIC"]:
+    for v in ["ATOMIC_U64", "SYMMETRIC", "SORT"]:
         assert np.array_equal(out["GATHER"][0], out[v][0]), v
         assert np.array_equal(out["GATHER"][2], out[v][2]), v
         assert out["GATHER"][1][1] == out[v][1][1], v
 
 
-# The upper-triangle update works on 32 x 32 tiles: sizes below, at and
-# around tile multiples, and a few iterations against the oracle.
-@pytest.mark.parametrize("n,m,iters", [(3, 2, 3), (31, 31, 5), (32, 20, 5), (33, 33, 5),
+# The upper-triangle update works on 32 x 32 tiles and the sort deposit on
+# tiles of 1024 keys: sizes below, at and around tile multiples (m n = 1024
+# at n = 32, m = 32 is one exact sort tile), a few iterations each.
+@pytest.mark.parametrize("n,m,iters", [(3, 2, 3), (31, 31, 5), (32, 32, 5), (33, 33, 5),
                                        (64, 64, 4), (97, 50, 4), (257, 100, 3)])
-def test_symmetric_update_bit_exact(aco, orc, n, m, iters):
+@pytest.mark.parametrize("deposit", ["SYMMETRIC", "SORT"])
+def test_symmetric_update_bit_exact(aco, orc, n, m, iters, deposit):
     inst = I.uniform_instance(n, 1000, seed=600 + n)
     ref = orc.run(inst.dist, m, iters, 13)
     with aco.Colony(inst.dist, m, seed=13) as c:
-        aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, aco.ACO_DEPOSIT_SYMMETRIC)
+        aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, getattr(aco, "ACO_DEPOSIT_" + deposit))
         aco.aco_iterate(c.h, iters)
         tau = aco.aco_get_pheromone(c.h, n)
         ch = aco.aco_choice_info(c.h, n)
@@ -257,13 +259,14 @@ def test_symmetric_update_full_size_equals_gather(aco, wl):
     d, m = w["inst"].dist, w["m"]
     n = d.shape[0]
     out = {}
-    for v in ["GATHER", "SYMMETRIC"]:
+    for v in ["GATHER", "SYMMETRIC", "SORT"]:
         with aco.Colony(d, m, seed=w["seed"]) as c:
             aco.aco_set_option(c.h, aco.ACO_OPT_DEPOSIT, getattr(aco, "ACO_DEPOSIT_" + v))
             aco.aco_iterate(c.h, 2)
             out[v] = (aco.aco_get_pheromone(c.h, n), aco.aco_choice_info(c.h, n))
-    assert np.array_equal(out["GATHER"][0], out["SYMMETRIC"][0])
-    assert np.array_equal(out["GATHER"][1], out["SYMMETRIC"][1])
+    for v in ["SYMMETRIC", "SORT"]:
+        assert np.array_equal(out["GATHER"][0], out[v][0]), v
+        assert np.array_equal(out["GATHER"][1], out[v][1]), v
 
 
 def test_update_invariants_at_full_size(aco):

@@ -180,11 +180,11 @@ def test_autotuned_tilings_give_identical_results(aco):
             aco.aco_pool_set_autotune(b, on)
             aco.aco_pool_autotune(b)
             tilings = [aco.aco_pool_tiling(b, i) for i in range(len(ns))]
-            for (g, h, c), n in zip(tilings, ns):
+            for (g, h, c, sg), n in zip(tilings, ns):
                 assert g in (1, 2, 4) and h in (8, 16, 32) and (h == 32 or g == 1)
-                assert g * h * c >= n
+                assert g * h * c >= n and sg in (0, 1)
                 if not on:
-                    assert (g, h) == (1, 32)
+                    assert (g, h, sg) == (1, 32, 0)
             aco.aco_batch_iterate(b, 4)
             out[on] = [(aco.aco_pool_pheromone(b, i, n), aco.aco_batch_best(b, i, n))
                        for i, n in enumerate(ns)]
@@ -192,3 +192,33 @@ def test_autotuned_tilings_give_identical_results(aco):
             aco.aco_batch_destroy(b)
     for (ta, (tra, la)), (tb, (trb, lb)) in zip(out[True], out[False]):
         assert np.array_equal(ta, tb) and la == lb and np.array_equal(tra, trb)
+
+
+def test_cancel_mid_flight_and_allocation_failure(aco):
+    # A request released while still live (cancelled) frees its memory and
+    # leaves the others' results unchanged; a budget the device cannot
+    # allocate fails cleanly with ACO_ENOMEM.
+    a = I.uniform_instance(120, 1000, seed=61)
+    b = I.uniform_instance(90, 1000, seed=62)
+    p = aco.aco_pool_create(4, 1 << 28)
+    try:
+        sa = aco.aco_pool_admit_coords(p, a.coords, 1.0, 2.0, 0.5, 60, 5, 6)
+        sb = aco.aco_pool_admit_coords(p, b.coords, 1.0, 2.0, 0.5, 40, 6, 6)
+        aco.aco_pool_step(p)
+        aco.aco_pool_step(p)
+        aco.aco_pool_release(p, sb)  # cancelled after two of its six iterations
+        assert aco.aco_pool_stats(p)["live"] == 1
+        while aco.aco_pool_step(p) > 0:
+            pass
+        assert aco.aco_pool_finished(p) == [sa]
+        tau_a, (tour_a, len_a) = alone(aco, a.dist, 60, 5, 6)
+        tour_p, len_p = aco.aco_pool_result(p, sa, a.n)
+        assert len_p == len_a and np.array_equal(tour_p, tour_a)
+        assert np.array_equal(aco.aco_pool_pheromone(p, sa, a.n), tau_a)
+        aco.aco_pool_release(p, sa)
+        assert aco.aco_pool_stats(p)["bytes_in_use"] == 0
+    finally:
+        aco.aco_pool_destroy(p)
+    with pytest.raises(aco.AcoError) as e:
+        aco.aco_pool_create(4, 1 << 50)
+    assert e.value.code == aco.ACO_ENOMEM
