@@ -396,13 +396,21 @@ def run_ours(args, w, rank, world, local):
     if rank != 0:
         return
     peaks, peak_kind = measured_peaks()
-    roof = construct_roofline(n, m, con_ms, peaks, peak_kind)
+    if args.variant == "acs":
+        kernel = "acs_construct_kernel"
+    elif args.nn:
+        kernel = "construct_nn_kernel"
+    else:
+        kernel = "construct_kernel"
+    roof = construct_roofline(n, m, con_ms, peaks, peak_kind, kernel=kernel, nn=args.nn)
     if not (args.nn or args.selection != "eq1" or args.lanes_per_ant or args.warps_per_ant
             or args.ants_per_cta or args.variant != "as"):
         roof["traffic"], roof["traffic_source"] = recorded_traffic(w["name"])
     l2_gbs = measure_l2_copy_gbs()
     algo = roof["algorithmic_bytes_per_launch"]
-    dense = 4.0 * m * (n - 1) * n
+    # bytes the kernel stages per launch: whole rows for the Eq. 1 kernels,
+    # one 128-byte line of list values plus the list for the NN-list kernel
+    dense = 4.0 * m * (n - 1) * n if not args.nn else 256.0 * m * (n - 1)
     roof_l2 = {"bound": "l2", "peak": l2_gbs, "unit": "GB/s",
                "peak_kind": "L2 copy bandwidth measured in this run (64 graph-replayed torch copies, 2 x 24 MiB)",
                "achieved_algorithmic": algo / (con_ms / 1e3) / 1e9,
@@ -474,19 +482,24 @@ def recorded_traffic(workload: str):
     return None, None
 
 
-def construct_roofline(n, m, con_ms, peaks, peak_kind):
+def construct_roofline(n, m, con_ms, peaks, peak_kind, kernel="construct_kernel", nn=0):
     """Roofline entry for the construction kernel (the dominant kernel).
 
     Algorithmic bytes per launch: every ant reads, at each of its n-1 steps,
     the 4-byte choice_info entries of the cities it has not visited yet:
-    4 * m * sum_{s=1}^{n-1} (n - s) = 4 m n (n-1) / 2."""
-    algo = 4.0 * m * n * (n - 1) / 2.0
+    4 * m * sum_{s=1}^{n-1} (n - s) = 4 m n (n-1) / 2.  With nearest-neighbour
+    lists a step needs the current city's nn list entries and their
+    list-ordered choice_info values: 8 * nn bytes, m (n-1) steps."""
+    if nn:
+        algo = 8.0 * nn * m * (n - 1)
+    else:
+        algo = 4.0 * m * n * (n - 1) / 2.0
     achieved = algo / (con_ms / 1e3) / 1e9
     peak = float(peaks["hbm_gbs"])
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
             "peak_kind": f"{peak_kind} HBM copy bandwidth",
-            "kernel": "construct_kernel", "algorithmic_bytes_per_launch": algo,
+            "kernel": kernel, "algorithmic_bytes_per_launch": algo,
             "avg_launch_ms": con_ms}
 
 
