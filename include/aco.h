@@ -474,6 +474,17 @@ int aco_update_pheromone_noalloc(int32_t n, int32_t m, const int32_t *tours, con
                                  const float *heta, float *tau, float *choice, float alpha,
                                  float rho, int64_t stream);
 
+/*
+ * aco_selftest_bounded_wait - exercise the library's bounded device-side
+ * wait (no counterpart in the paper).  A one-warp kernel expects 16 bytes on
+ * an mbarrier and waits with the loop the construction kernel uses, giving
+ * up after `polls` polls (1 <= polls <= 2^20).  complete = 1: a 16-byte bulk
+ * copy delivers the bytes, the wait succeeds, ACO_OK.  complete = 0: nothing
+ * completes the phase, the wait gives up and the call returns ACO_ETIMEOUT;
+ * the kernel still ends normally and the context stays usable.
+ */
+int aco_selftest_bounded_wait(int32_t polls, int32_t complete);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("aco_set_mmas", C.c_int, [_vp, C.c_double, C.c_int32]),
     ("aco_get_mmas_limits", C.c_int, [_vp, _f32p, _f32p]),
     ("aco_set_acs", C.c_int, [_vp, C.c_double, C.c_float]),
+    ("aco_selftest_bounded_wait", C.c_int, [C.c_int32, C.c_int32]),
     ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
     ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
     ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
@@ -223,6 +224,11 @@ def aco_get_tau0(h):
 def aco_set_mmas(h, p_best: float = 0.05, best_so_far: bool = False) -> None:
     """Switch to the MAX-MIN Ant System update (before the first construction)."""
     _check(load().aco_set_mmas(h, float(p_best), int(bool(best_so_far))), "aco_set_mmas")
+
+
+def aco_selftest_bounded_wait(polls: int, complete: bool) -> int:
+    """Return code of the bounded-wait self-test (ACO_OK or ACO_ETIMEOUT)."""
+    return int(load().aco_selftest_bounded_wait(int(polls), int(bool(complete))))
 
 
 def aco_set_acs(h, q0: float = 0.9, xi: float = 0.1) -> None:

@@ -96,3 +96,13 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.aco_best_tour(None, None, None) == aco.ACO_EINVAL
     h = C.c_void_p()
     assert lib.aco_create(3, None, 1.0, 2.0, 0.5, 3, 1, C.byref(h)) == aco.ACO_EINVAL
+    assert lib.aco_set_mmas(None, 0.05, 0) == aco.ACO_EINVAL
+    assert lib.aco_set_acs(None, 0.9, 0.1) == aco.ACO_EINVAL
+    assert lib.aco_pool_autotune(None) == aco.ACO_EINVAL
+
+
+def test_selftest_rejects_bad_arguments_before_touching_the_gpu(lib):
+    from paper_1101_2678_gb300 import aco
+    assert lib.aco_selftest_bounded_wait(0, 1) == aco.ACO_EINVAL
+    assert lib.aco_selftest_bounded_wait((1 << 20) + 1, 1) == aco.ACO_EINVAL
+    assert lib.aco_selftest_bounded_wait(100, 2) == aco.ACO_EINVAL

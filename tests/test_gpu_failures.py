@@ -1,0 +1,34 @@
+"""Failure detection on the GPU without a GPU fault.
+
+The library's only device-side spin waits are the bounded mbarrier waits of
+the bulk row copies.  The self-test kernel runs the same bounded loop on a
+phase that nothing completes: the wait must give up, the call must return
+ACO_ETIMEOUT, and the context must stay usable.
+"""
+import numpy as np
+import pytest
+
+from paper_1101_2678_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aco():
+    from paper_1101_2678_gb300 import build
+    build.build()
+    from paper_1101_2678_gb300 import aco as a
+    a.load()
+    return a
+
+
+def test_bounded_wait_gives_up_and_context_survives(aco, orc):
+    assert aco.aco_selftest_bounded_wait(1000, True) == aco.ACO_OK
+    assert aco.aco_selftest_bounded_wait(1000, False) == aco.ACO_ETIMEOUT
+    assert aco.aco_selftest_bounded_wait(1000, True) == aco.ACO_OK
+    # a normal run afterwards still matches the oracle
+    inst = I.uniform_instance(40, 1000, seed=2)
+    ref = orc.run(inst.dist, 20, 3, 4)
+    with aco.Colony(inst.dist, 20, seed=4) as c:
+        aco.aco_iterate(c.h, 3)
+        assert np.array_equal(aco.aco_get_pheromone(c.h, 40), ref["tau32"])

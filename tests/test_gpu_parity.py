@@ -424,3 +424,40 @@ def test_nn_list_run_bit_exact_and_option_rules(aco, orc):
             aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 33)
         aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 0)
         assert aco.aco_get_option(c.h, aco.ACO_OPT_NN_LIST) == 0
+
+
+# ---------------------------------------------------------------------------
+# Other exponents (R3, R6): alpha = 0 is exact; non-integer beta and alpha go
+# through pow/powf, where the device and host libraries may differ in the last
+# place, so those are held to one and two units in the last place.
+# ---------------------------------------------------------------------------
+
+def _ulps(a, b):
+    a = np.asarray(a, np.float32).view(np.int32).astype(np.int64)
+    b = np.asarray(b, np.float32).view(np.int32).astype(np.int64)
+    return np.abs(a - b)
+
+
+def test_alpha_zero_run_bit_exact(aco, orc):
+    inst = I.uniform_instance(97, 1000, seed=17)
+    ref = orc.run(inst.dist, 40, 5, 3, alpha=0.0)
+    with aco.Colony(inst.dist, 40, seed=3, alpha=0.0) as c:
+        aco.aco_iterate(c.h, 5)
+        tau = aco.aco_get_pheromone(c.h, 97)
+        tour, best = aco.aco_best_tour(c.h, 97)
+    assert np.array_equal(tau, ref["tau32"]) and best == ref["best_len"]
+
+
+def test_non_integer_exponents_within_ulps(aco, orc):
+    n, m = 300, 50
+    inst = I.clustered_instance(n, seed=5, clusters=6, sigma=300, side=6000)
+    h_ref = orc.heta(inst.dist, 2.5)
+    tau = np.full((n, n), orc.tau0(inst.dist, m), np.float32)
+    np.fill_diagonal(tau, 0)
+    ch_ref = orc.choice(tau, h_ref, 1.5)
+    with aco.Colony(inst.dist, m, seed=8, alpha=1.5, beta=2.5) as c:
+        assert _ulps(aco.aco_get_heuristic(c.h, n), h_ref).max() <= 1
+        assert _ulps(aco.aco_choice_info(c.h, n), ch_ref).max() <= 2
+        aco.aco_iterate(c.h, 3)
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+    check_tours(tours, lens, inst.dist)
