@@ -15,21 +15,10 @@
 // The colony (m <= 32 ants, the variant's usual m = 10) runs in one CTA, one
 // warp per ant, so the per-step lockstep is a CTA barrier.
 #include "aco_device.cuh"
+#include "construct.cuh"
 #include "kernels.h"
 
 namespace aco {
-
-// floor(w * 2^sc) for a non-negative float given by its bits, exactly, with
-// integer shifts of the significand (sc is such that the result is < 2^46).
-__device__ __forceinline__ unsigned long long acs_quant(uint32_t b, int sc) {
-  if (b == 0u) return 0ull;
-  const uint32_t e = b >> 23;
-  const uint32_t mant = e ? ((b & 0x7fffffu) | 0x800000u) : b;
-  const int shift = (e ? (int)e - 150 : -149) + sc;
-  if (shift >= 0) return (unsigned long long)mant << shift;
-  if (shift <= -24) return 0ull;
-  return (unsigned long long)(mant >> (-shift));
-}
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
 #pragma unroll
@@ -114,7 +103,9 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
       if (!exploit && mbits != 0u) {
         // Eq. 1 by the integer roulette: q_j = floor(w_j 2^(45 - ilogb M)),
         // T = floor(r Q / 2^64), the first j whose prefix sum exceeds T.
-        const int sc = 45 - exponent_of_bits(mbits);
+        // (the three-FMA quantiser of the construction kernel: exact, branch-free)
+        float f1, f1s, f2;
+        quant_factors(kRouletteBits - 1 - exponent_of_bits(mbits), f1, f1s, f2);
         unsigned long long part = 0ull;
 #pragma unroll 4
         for (int j0 = 4 * lane; j0 < n; j0 += 128) {
@@ -123,26 +114,34 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
           const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e)
-            if (((fr >> e) & 1u) && j0 + e < n) part += acs_quant(wv[e], sc);
+            part += quant_value(((fr >> e) & 1u) && j0 + e < n ? wv[e] : 0u, f1, f1s, f2);
         }
         const unsigned long long Q = warp_sum_u64(part);
         const unsigned long long r = ((unsigned long long)x.x1 << 32) | x.x0;
         const unsigned long long T = __umul64hi(r, Q);
-        // Pass 3: 128 cities at a time in ascending order; a warp scan of the
-        // lanes' four-city sums finds the lane, the lane its city.
+        // Pass 3: 256 cities at a time in ascending order, lane l holding
+        // cities 8l..8l+7 of the chunk; a warp scan of the lanes' eight-city
+        // sums finds the lane, the lane its city.
         unsigned long long running = 0ull;
-        for (int c0 = 0; c0 < n; c0 += 128) {
-          const int j0 = c0 + 4 * lane;
-          unsigned long long q[4] = {0ull, 0ull, 0ull, 0ull};
-          if (j0 < n) {
-            const uint4 w4 = *reinterpret_cast<const uint4*>(row + j0);
-            const uint32_t fr = ~seen[j0 >> 5] >> (j0 & 31);
-            const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+        for (int c0 = 0; c0 < n; c0 += 256) {
+          const int j0 = c0 + 8 * lane;
+          unsigned long long q[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (((fr >> e) & 1u) && j0 + e < n) q[e] = acs_quant(wv[e], sc);
+          for (int e = 0; e < 8; ++e) q[e] = 0ull;
+          if (j0 < n) {
+            const uint32_t fr = ~seen[j0 >> 5] >> (j0 & 31);  // 8 free bits (j0 % 8 == 0)
+            const uint4 wa = *reinterpret_cast<const uint4*>(row + j0);
+            // the second half only if it starts inside the row (ld % 4 == 0)
+            const uint4 wb = j0 + 4 < n ? *reinterpret_cast<const uint4*>(row + j0 + 4)
+                                        : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              q[e] = quant_value(((fr >> e) & 1u) && j0 + e < n ? wv[e] : 0u, f1, f1s, f2);
           }
-          const unsigned long long mine = q[0] + q[1] + q[2] + q[3];
+          unsigned long long mine = 0ull;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) mine += q[e];
           const unsigned long long incl = warp_incl_scan_u64(mine, lane);
           const unsigned long long total = __shfl_sync(FULL, incl, 31);
           if (running + total > T) {
@@ -150,21 +149,16 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
             const int L = __ffs(hit) - 1;
             int pick = 0;
             if (lane == L) {
+              // the first e whose inclusive prefix exceeds T: count the
+              // prefixes that do not
               unsigned long long c = running + incl - mine;
-              c += q[0];
-              if (c > T) {
-                pick = 0;
-              } else {
-                c += q[1];
-                if (c > T) {
-                  pick = 1;
-                } else {
-                  c += q[2];
-                  pick = c > T ? 2 : 3;
-                }
+#pragma unroll
+              for (int e = 0; e < 7; ++e) {
+                c += q[e];
+                pick += c <= T ? 1 : 0;
               }
             }
-            next = c0 + 4 * L + __shfl_sync(FULL, pick, L);
+            next = c0 + 8 * L + __shfl_sync(FULL, pick, L);
             break;
           }
           running += total;
@@ -179,15 +173,23 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
     // updates of this step, one writer per distinct edge applying it once
     // per ant that crossed the edge
     const uint32_t lo = (uint32_t)min(cur, next), hi = (uint32_t)max(cur, next);
-    if (lane == 0) s_edge[k] = (lo << 16) | hi;
+    const size_t ab = (size_t)lo * ld + hi, ba = (size_t)hi * ld + lo;
+    // The crossed cell's tau and eta^beta, read before the barrier: only this
+    // step's writer of the edge stores to it, after the barrier, so the
+    // values read here are the current ones and the load latency overlaps
+    // the other ants' selection.
+    float t = 0.0f, h = 0.0f;
+    if (lane == 0) {
+      s_edge[k] = (lo << 16) | hi;
+      t = __ldcg(I.tau + ab);
+      h = I.heta[ab];
+    }
     __syncthreads();
     const uint32_t e = s_edge[k];
     const unsigned same = __ballot_sync(FULL, lane < m && s_edge[lane < m ? lane : 0] == e);
     if (lane == 0 && __ffs(same) - 1 == k) {
-      const size_t ab = (size_t)lo * ld + hi, ba = (size_t)hi * ld + lo;
-      float t = __ldcg(I.tau + ab);
       for (int c = __popc(same); c > 0; --c) t = acs_local(t, keep, add);
-      const float ch = choice_of(t, I.heta[ab], I.alpha);
+      const float ch = choice_of(t, h, I.alpha);
       I.tau[ab] = t;
       I.tau[ba] = t;
       I.choice[ab] = ch;
