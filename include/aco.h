@@ -81,13 +81,6 @@ extern "C" {
 #define ACO_OPT_LANES_PER_ANT 7 /* 0 (default) = 32; 8 or 16: 32/H ants share a
                                   warp (one warp per ant group)                */
 #define ACO_OPT_SELECTION 8    /* ACO_SELECT_* below; default ACO_SELECT_EQ1     */
-#define ACO_OPT_STAGING 10     /* how the construction kernel brings row
-                                  choice[cur] into shared memory at each step:
-                                  0 one bulk copy (TMA engine, cp.async.bulk)
-                                  completing on an mbarrier; 1 coalesced
-                                  16-byte loads by the ant's threads.  Default:
-                                  1 for n <= 64, else 0 (the faster measured
-                                  on GB300).  Results are identical.          */
 #define ACO_OPT_NN_LIST 9      /* 0 (default): every unvisited city is a
                                   candidate.  k in [1, min(32, n-1)]: the
                                   nearest-neighbour-list construction (Section
@@ -100,6 +93,13 @@ extern "C" {
                                   unvisited city with the largest choice_info
                                   value (ties to the lower index).  Needs
                                   ACO_SELECT_EQ1; not available in pools.      */
+#define ACO_OPT_STAGING 10     /* how the construction kernel brings row
+                                  choice[cur] into shared memory at each step:
+                                  0 one bulk copy (TMA engine, cp.async.bulk)
+                                  completing on an mbarrier; 1 coalesced
+                                  16-byte loads by the ant's threads.  Default:
+                                  1 for n <= 64, else 0 (the faster measured
+                                  on GB300).  Results are identical.          */
 
 #define ACO_SELECT_EQ1 0       /* Eq. 1 (random proportional rule), exact      */
 #define ACO_SELECT_DATA_PARALLEL 1 /* the paper's data-parallel kernel (Section
@@ -121,6 +121,16 @@ extern "C" {
                                   evaporation (the paper's atomic kernel; the
                                   order of additions, hence the last bits of
                                   tau, is not deterministic)                   */
+#define ACO_DEPOSIT_SYMMETRIC 3  /* the paper's "Reduction" version (Section
+                                  III-B): for the symmetric TSP the edge (a,b)
+                                  adds q_k once, to the upper-triangle cell
+                                  (min, max), with red.global.add.u64 (half the
+                                  atomics of ATOMIC_U64); the apply pass reads
+                                  tau, eta^beta and the accumulator in the
+                                  upper triangle only and writes both halves
+                                  of tau and choice_info through shared-memory
+                                  tiles.  Results equal GATHER and ATOMIC_U64
+                                  bit for bit.                                 */
 #define ACO_DEPOSIT_SORT 4     /* atomic-free scatter-to-gather by sorting
                                   (Section III-B's idea without its n^4
                                   loads): each tour edge becomes the key
@@ -132,16 +142,6 @@ extern "C" {
                                   with the other deterministic variants.
                                   Allocates 16 bytes per (ant, city) of
                                   scratch when first selected.                */
-#define ACO_DEPOSIT_SYMMETRIC 3  /* the paper's "Reduction" version (Section
-                                  III-B): for the symmetric TSP the edge (a,b)
-                                  adds q_k once, to the upper-triangle cell
-                                  (min, max), with red.global.add.u64 (half the
-                                  atomics of ATOMIC_U64); the apply pass reads
-                                  tau, eta^beta and the accumulator in the
-                                  upper triangle only and writes both halves
-                                  of tau and choice_info through shared-memory
-                                  tiles.  Results equal GATHER and ATOMIC_U64
-                                  bit for bit.                                 */
 
 /* ---- phases reported by aco_get_kernel_times ------------------------------ */
 #define ACO_PHASE_CONSTRUCT 0  /* tour construction kernel                      */
