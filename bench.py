@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-iterations", type=int, default=0,
                     help="0 = the workload's 100; fewer for profiling runs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched: default tiling for every class (profiling runs)")
     ap.add_argument("--no-loop-baseline", action="store_true",
                     help="skip the per-instance loop (profiling runs)")
     ap.add_argument("--serve-seconds", type=float, default=20.0,
@@ -541,12 +543,16 @@ def run_batched(args, rank, world, local):
     dists = [x.dist for x in insts]
     # warm-up (module load, graph code paths)
     b = aco.aco_batch_create(dists[:4], ms[:4], seeds[:4])
+    if args.no_autotune:
+        aco.aco_pool_set_autotune(b, False)
     aco.aco_batch_iterate(b, 3)
     aco.aco_pool_synchronize(b)
     aco.aco_batch_destroy(b)
     barrier(world)
     b = aco.aco_batch_create(dists, ms, seeds)
     aco.aco_pool_synchronize(b)
+    if args.no_autotune:
+        aco.aco_pool_set_autotune(b, False)
     # choose each class's construction tiling before the timed run (the
     # choice does not change any result); reported in config
     t_tune = time.perf_counter()
