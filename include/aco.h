@@ -414,6 +414,20 @@ int aco_pool_autotune(aco_pool_handle p);
 int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t *warps_per_ant,
                     int32_t *lanes_per_ant, int32_t *cities_per_lane, int32_t *staging);
 
+/*
+ * The tuner's table, to keep it across runs (the Python binding saves it as
+ * JSON).  One entry is 7 int32: the class's default (warps per ant, lanes
+ * per ant, cities per lane) and the chosen (warps per ant, lanes per ant,
+ * ants per CTA, staging).
+ *   aco_pool_get_tuning: *count = entries in the table; up to `capacity` of
+ *     them are written to `entries` (7 * capacity int32) when it is not NULL.
+ *   aco_pool_set_tuning: replace the table (count >= 0 entries); classes in
+ *     it are not timed again.  ACO_EINVAL if an entry names an unsupported
+ *     tiling (the table is then unchanged).  Turns autotuning on.
+ */
+int aco_pool_get_tuning(aco_pool_handle p, int32_t *entries, int32_t capacity, int32_t *count);
+int aco_pool_set_tuning(aco_pool_handle p, const int32_t *entries, int32_t count);
+
 /* aco_pool_synchronize - wait for all pool work and report device-side errors. */
 int aco_pool_synchronize(aco_pool_handle p);
 

@@ -98,6 +98,8 @@ SIGNATURES = [
     ("aco_pool_set_autotune", C.c_int, [_vp, C.c_int32]),
     ("aco_pool_autotune", C.c_int, [_vp]),
     ("aco_pool_tiling", C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p, _i32p]),
+    ("aco_pool_get_tuning", C.c_int, [_vp, _vp, C.c_int32, _i32p]),
+    ("aco_pool_set_tuning", C.c_int, [_vp, _vp, C.c_int32]),
     ("aco_batch_create", C.c_int, [C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     ("aco_batch_iterate", C.c_int, [_vp, C.c_int32]),
     ("aco_batch_best", C.c_int, [_vp, C.c_int32, _vp, _vp]),
@@ -370,6 +372,37 @@ def aco_pool_set_autotune(p, on: bool) -> None:
 def aco_pool_autotune(p) -> None:
     """Tune the construction tiling of the live set's new classes now."""
     _check(load().aco_pool_autotune(p), "aco_pool_autotune")
+
+
+def aco_pool_get_tuning(p) -> list:
+    """The tuner's table: [[default G, H, C], [chosen G, H, ants per CTA, staging]] entries."""
+    cnt = C.c_int32()
+    _check(load().aco_pool_get_tuning(p, None, 0, C.byref(cnt)), "aco_pool_get_tuning")
+    buf = np.zeros((max(cnt.value, 1), 7), np.int32)
+    _check(load().aco_pool_get_tuning(p, _ptr(buf), buf.shape[0], C.byref(cnt)),
+           "aco_pool_get_tuning")
+    return [[row[:3].tolist(), row[3:].tolist()] for row in buf[:cnt.value]]
+
+
+def aco_pool_set_tuning(p, table) -> None:
+    """Replace the tuner's table (entries as returned by aco_pool_get_tuning)."""
+    buf = np.array([list(k) + list(v) for k, v in table], np.int32).reshape(-1, 7)
+    _check(load().aco_pool_set_tuning(p, _ptr(np.ascontiguousarray(buf)), buf.shape[0]),
+           "aco_pool_set_tuning")
+
+
+def save_tuning(p, path: str) -> None:
+    """Write the pool's tuning table to a JSON file."""
+    import json
+    with open(path, "w") as f:
+        json.dump({"construct_tiling": aco_pool_get_tuning(p)}, f, indent=1)
+
+
+def load_tuning(p, path: str) -> None:
+    """Load a tuning table written by save_tuning into the pool."""
+    import json
+    with open(path) as f:
+        aco_pool_set_tuning(p, json.load(f)["construct_tiling"])
 
 
 def aco_pool_tiling(p, slot: int):

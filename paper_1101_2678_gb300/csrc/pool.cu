@@ -270,7 +270,9 @@ static int pool_rebuild(aco_pool* p) {
 // same tours (the selection is exact integer arithmetic), so the trial runs
 // change nothing: the step that follows rebuilds the same tours.
 static int pool_autotune(aco_pool* p) {
-  static const int kCand[][3] = {{1, 32, 4}, {2, 32, 2}, {4, 32, 1}, {1, 16, 8}, {1, 8, 16}};
+  // (warps per ant, lanes per ant, ants per CTA): CTA widths of 2-8 warps
+  static const int kCand[][3] = {{1, 32, 4}, {1, 32, 2}, {1, 32, 8}, {2, 32, 2},
+                                 {4, 32, 1}, {1, 16, 8}, {1, 8, 16}};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -644,6 +646,48 @@ int aco_pool_autotune(aco_pool_handle p) {
   if ((rc = pool_wait_ready(p)) != ACO_OK) return rc;
   if ((rc = pool_autotune(p)) != ACO_OK) return rc;
   pool_drop_graph(p);
+  return ACO_OK;
+}
+
+int aco_pool_get_tuning(aco_pool_handle p, int32_t* entries, int32_t capacity, int32_t* count) {
+  if (!p || !count) return fail(ACO_EINVAL, "NULL argument");
+  *count = (int32_t)p->tuned.size();
+  if (!entries) return ACO_OK;
+  int i = 0;
+  for (const auto& kv : p->tuned) {
+    if (i >= capacity) break;
+    int32_t* e = entries + 7 * i;
+    e[0] = std::get<0>(kv.first);
+    e[1] = std::get<1>(kv.first);
+    e[2] = std::get<2>(kv.first);
+    e[3] = std::get<0>(kv.second);
+    e[4] = std::get<1>(kv.second);
+    e[5] = std::get<2>(kv.second);
+    e[6] = std::get<3>(kv.second);
+    ++i;
+  }
+  return ACO_OK;
+}
+
+int aco_pool_set_tuning(aco_pool_handle p, const int32_t* entries, int32_t count) {
+  if (!p || (count > 0 && !entries)) return fail(ACO_EINVAL, "NULL argument");
+  if (count < 0) return fail(ACO_EINVAL, "count < 0");
+  std::map<std::tuple<int, int, int>, std::tuple<int, int, int, int>> table;
+  for (int i = 0; i < count; ++i) {
+    const int32_t* e = entries + 7 * i;
+    // the class key must be a supported (G, H, C) and the choice a supported
+    // (G, H, ants per CTA, staging)
+    const bool key_ok = construct_supported(e[2], e[0], e[1]);
+    const ConstructTiling t = construct_tiling(1, e[3], e[4], e[5]);
+    const bool choice_ok = t.C != 0 && t.W >= 1 && t.W <= 8 && ants_per_cta(t) >= 1 &&
+                           (e[4] == 32 || e[3] == 1) && (e[6] == 0 || e[6] == 1);
+    if (!key_ok || !choice_ok)
+      return fail(ACO_EINVAL, "tuning entry %d is not a supported tiling", i);
+    table[std::make_tuple(e[0], e[1], e[2])] = std::make_tuple(e[3], e[4], e[5], e[6]);
+  }
+  p->tuned = table;
+  p->autotune = true;
+  p->dirty = true;
   return ACO_OK;
 }
 

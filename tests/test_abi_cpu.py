@@ -99,6 +99,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.aco_set_mmas(None, 0.05, 0) == aco.ACO_EINVAL
     assert lib.aco_set_acs(None, 0.9, 0.1) == aco.ACO_EINVAL
     assert lib.aco_pool_autotune(None) == aco.ACO_EINVAL
+    assert lib.aco_pool_set_tuning(None, None, 0) == aco.ACO_EINVAL
 
 
 def test_selftest_rejects_bad_arguments_before_touching_the_gpu(lib):

@@ -222,3 +222,49 @@ def test_cancel_mid_flight_and_allocation_failure(aco):
     with pytest.raises(aco.AcoError) as e:
         aco.aco_pool_create(4, 1 << 50)
     assert e.value.code == aco.ACO_ENOMEM
+
+
+def test_large_instances_in_a_batch_equal_alone(aco):
+    # n > 2432 takes two warps per ant; mixed with small instances in one
+    # batch, each still ends exactly as when run alone.
+    insts = [I.clustered_instance(3000, seed=77, clusters=16, sigma=400, side=20000),
+             I.uniform_instance(150, 1000, seed=78), I.uniform_instance(4096, 30000, seed=79)]
+    ms, seeds = [48, 150, 32], [5, 6, 7]
+    b = aco.aco_batch_create([x.dist for x in insts], ms, seeds)
+    try:
+        aco.aco_batch_iterate(b, 2)
+        for i, x in enumerate(insts):
+            tau_a, (tour_a, len_a) = alone(aco, x.dist, ms[i], seeds[i], 2)
+            tour_b, len_b = aco.aco_batch_best(b, i, x.n)
+            assert len_b == len_a and np.array_equal(tour_b, tour_a), i
+            assert np.array_equal(aco.aco_pool_pheromone(b, i, x.n), tau_a), i
+    finally:
+        aco.aco_batch_destroy(b)
+
+
+def test_tuning_table_round_trips_through_json(aco, tmp_path):
+    ns = [60, 250, 700, 1000]
+    insts = [I.uniform_instance(n, 1000, seed=300 + n) for n in ns]
+    seeds = [1, 2, 3, 4]
+    b = aco.aco_batch_create([x.dist for x in insts], ns, seeds)
+    try:
+        aco.aco_pool_autotune(b)
+        chosen = [aco.aco_pool_tiling(b, i) for i in range(len(ns))]
+        table = aco.aco_pool_get_tuning(b)
+        assert len(table) == len({tuple(k) for k, _ in table}) >= 3
+        path = str(tmp_path / "tuning.json")
+        aco.save_tuning(b, path)
+    finally:
+        aco.aco_batch_destroy(b)
+    b = aco.aco_batch_create([x.dist for x in insts], ns, seeds)
+    try:
+        aco.load_tuning(b, path)
+        assert aco.aco_pool_get_tuning(b) == table
+        aco.aco_batch_iterate(b, 2)
+        assert [aco.aco_pool_tiling(b, i) for i in range(len(ns))] == chosen
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_set_tuning(b, [[[1, 32, 36], [3, 32, 4, 0]]])  # 3 warps per ant
+        assert e.value.code == aco.ACO_EINVAL
+        assert aco.aco_pool_get_tuning(b) == table
+    finally:
+        aco.aco_batch_destroy(b)
