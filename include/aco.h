@@ -499,6 +499,17 @@ int aco_update_pheromone_noalloc(int32_t n, int32_t m, const int32_t *tours, con
  */
 int aco_selftest_bounded_wait(int32_t polls, int32_t complete);
 
+/*
+ * aco_philox4x32_10 - the kernels' counter-based generator (Philox4x32-10,
+ * Salmon, Moraes, Dror and Shaw, SC'11), evaluated on the GPU for `count`
+ * counters: ctr and out are host arrays of 4 * count uint32 (c0..c3 and
+ * x0..x3 per entry), key holds (k0, k1).  The construction kernels draw
+ * counter (step, ant, iteration, 0) with key (seed low, seed high) for Eq. 1,
+ * and (step, ant, iteration, 1 + j/4) for the data-parallel rule.
+ * 1 <= count <= 2^24; ACO_EINVAL on NULL pointers.
+ */
+int aco_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int32_t count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,7 @@ SIGNATURES = [
     ("aco_get_mmas_limits", C.c_int, [_vp, _f32p, _f32p]),
     ("aco_set_acs", C.c_int, [_vp, C.c_double, C.c_float]),
     ("aco_selftest_bounded_wait", C.c_int, [C.c_int32, C.c_int32]),
+    ("aco_philox4x32_10", C.c_int, [_vp, _vp, _vp, C.c_int32]),
     ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
     ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
     ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
@@ -226,6 +227,15 @@ def aco_get_tau0(h):
 def aco_set_mmas(h, p_best: float = 0.05, best_so_far: bool = False) -> None:
     """Switch to the MAX-MIN Ant System update (before the first construction)."""
     _check(load().aco_set_mmas(h, float(p_best), int(bool(best_so_far))), "aco_set_mmas")
+
+
+def aco_philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 words computed on the GPU: ctr (count, 4) uint32, key (2,) uint32."""
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, np.uint32).reshape(2)
+    out = np.empty_like(c)
+    _check(load().aco_philox4x32_10(_ptr(c), _ptr(k), _ptr(out), c.shape[0]), "aco_philox4x32_10")
+    return out
 
 
 def aco_selftest_bounded_wait(polls: int, complete: bool) -> int:

@@ -57,3 +57,40 @@ extern "C" int aco_selftest_bounded_wait(int32_t polls, int32_t complete) {
   if (status == kStatusTimeout) return fail(ACO_ETIMEOUT, "the bounded wait gave up as expected");
   return status == 0 ? ACO_OK : fail(ACO_ECUDA, "selftest status %d", status);
 }
+
+namespace aco {
+
+// The device Philox4x32-10 (the generator of every kernel) on given counters.
+__global__ void philox_words_kernel(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                                    uint4* __restrict__ out, int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const uint4 c = ctr[i];
+    const Philox4 x = philox4x32_10(c.x, c.y, c.z, c.w, k0, k1);
+    out[i] = make_uint4(x.x0, x.x1, x.x2, x.x3);
+  }
+}
+
+}  // namespace aco
+
+extern "C" int aco_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                                 int32_t count) {
+  if (!ctr || !key || !out) return fail(ACO_EINVAL, "NULL argument");
+  if (count < 1 || count > (1 << 24)) return fail(ACO_EINVAL, "count outside [1, 2^24]");
+  const size_t bytes = (size_t)count * 16;
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 2 * bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "philox alloc");
+  uint4* dc = static_cast<uint4*>(d);
+  uint4* dout = dc + count;
+  e = cudaMemcpy(dc, ctr, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    int blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    philox_words_kernel<<<blocks, 256>>>(dc, key[0], key[1], dout, count);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "philox");
+  return ACO_OK;
+}

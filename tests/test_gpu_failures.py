@@ -32,3 +32,4 @@ def test_bounded_wait_gives_up_and_context_survives(aco, orc):
     with aco.Colony(inst.dist, 20, seed=4) as c:
         aco.aco_iterate(c.h, 3)
         assert np.array_equal(aco.aco_get_pheromone(c.h, 40), ref["tau32"])
+

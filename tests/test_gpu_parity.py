@@ -461,3 +461,33 @@ def test_non_integer_exponents_within_ulps(aco, orc):
         aco.aco_iterate(c.h, 3)
         tours, lens = aco.aco_construct_tours(c.h, n, m)
     check_tours(tours, lens, inst.dist)
+
+
+# ---------------------------------------------------------------------------
+# The generator (reading R1)
+# ---------------------------------------------------------------------------
+
+def _kat():
+    import os
+    rows = []
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x, 16) for x in line.split()]
+        rows.append((v[:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_device_philox_matches_published_vectors_and_oracle(aco, orc):
+    # The kernels' generator directly: the published known-answer vectors,
+    # then random counters and keys against the oracle's own implementation.
+    for ctr, key, out in _kat():
+        assert aco.aco_philox4x32_10([ctr], key)[0].tolist() == out
+    rng = np.random.default_rng(11)
+    ctr = rng.integers(0, 2 ** 32, size=(4000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xffffffff] * 4, [5, 7, 9, 1]]
+    for key in ([0, 0], [0xdeadbeef, 0x12345678], [1, 0]):
+        got = aco.aco_philox4x32_10(ctr, key)
+        for i in range(0, 4000, 7):
+            assert got[i].tolist() == list(orc.philox4x32_10(ctr[i].tolist(), key)), (i, key)
