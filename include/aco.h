@@ -280,6 +280,25 @@ int aco_set_mmas(aco_handle h, double p_best, int32_t best_so_far);
 int aco_set_acs(aco_handle h, double q0, float xi);
 
 /*
+ * Checkpoint and resume (library feature; the paper has no counterpart).
+ * The state of a run is tau, the best-so-far tour and length, the iteration
+ * counter and the update rule with its parameters.  The random numbers are
+ * counter-based on (seed, iteration, ant, step), so a run restored from a
+ * checkpoint continues exactly as the uninterrupted run would.
+ *   aco_save_state: *size = bytes of the checkpoint; with buf != NULL and
+ *     capacity >= *size it is written to buf (host memory).
+ *   aco_restore_state: load a checkpoint into a handle created with the same
+ *     n, distances, alpha, beta, rho, m and seed (the header checks all but
+ *     the distances; ACO_EINVAL on a mismatch, a truncated or foreign
+ *     buffer).  choice_info is recomputed from tau.  Options (deposit
+ *     variant, tiling, staging, lists, selection, stream) are not part of the
+ *     state: set them on the new handle as before; a checkpoint of an Ant
+ *     Colony System run needs a handle without lists and with Eq. 1.
+ */
+int aco_save_state(aco_handle h, void *buf, uint64_t capacity, uint64_t *size);
+int aco_restore_state(aco_handle h, const void *buf, uint64_t size);
+
+/*
  * aco_get_mmas_limits - the current trail limits tau_min and tau_max of a
  * MAX-MIN handle (either output may be NULL); ACO_ESTATE for an Ant System
  * handle.

@@ -74,6 +74,8 @@ SIGNATURES = [
     ("aco_get_mmas_limits", C.c_int, [_vp, _f32p, _f32p]),
     ("aco_set_acs", C.c_int, [_vp, C.c_double, C.c_float]),
     ("aco_selftest_bounded_wait", C.c_int, [C.c_int32, C.c_int32]),
+    ("aco_save_state", C.c_int, [_vp, _vp, C.c_uint64, C.POINTER(C.c_uint64)]),
+    ("aco_restore_state", C.c_int, [_vp, _vp, C.c_uint64]),
     ("aco_philox4x32_10", C.c_int, [_vp, _vp, _vp, C.c_int32]),
     ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
     ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
@@ -236,6 +238,21 @@ def aco_philox4x32_10(ctr, key) -> np.ndarray:
     out = np.empty_like(c)
     _check(load().aco_philox4x32_10(_ptr(c), _ptr(k), _ptr(out), c.shape[0]), "aco_philox4x32_10")
     return out
+
+
+def aco_save_state(h) -> bytes:
+    """A checkpoint of the run (tau, best tour, iteration counter, update rule)."""
+    size = C.c_uint64()
+    _check(load().aco_save_state(h, None, 0, C.byref(size)), "aco_save_state")
+    buf = np.empty(size.value, np.uint8)
+    _check(load().aco_save_state(h, _ptr(buf), size.value, C.byref(size)), "aco_save_state")
+    return buf.tobytes()
+
+
+def aco_restore_state(h, blob: bytes) -> None:
+    """Continue a run from a checkpoint written by aco_save_state."""
+    buf = np.frombuffer(blob, np.uint8)
+    _check(load().aco_restore_state(h, _ptr(buf), buf.size), "aco_restore_state")
 
 
 def aco_selftest_bounded_wait(polls: int, complete: bool) -> int:
