@@ -308,6 +308,7 @@ int aco_create_coords(int32_t n, const int32_t* xy, float alpha, float beta, flo
 
 static int create_common(int32_t n, const int32_t* dist, const int32_t* xy, float alpha,
                          float beta, float rho, int32_t m, uint64_t seed, aco_handle* out) {
+  NvtxRange nvtx_range("aco_create");
   int rc;
   aco_colony* h = new (std::nothrow) aco_colony();
   if (!h) return fail(ACO_ENOMEM, "host allocation");
@@ -448,6 +449,7 @@ int aco_choice_info(aco_handle h, float* out) {
 }
 
 int aco_construct_tours(aco_handle h, int32_t* tours, int64_t* lens) {
+  NvtxRange nvtx_range("aco_construct_tours");
   if (!h) return fail(ACO_EINVAL, "NULL handle");
   int rc = enqueue_construct(h);
   if (rc) return rc;
@@ -468,6 +470,7 @@ int aco_construct_tours(aco_handle h, int32_t* tours, int64_t* lens) {
 }
 
 int aco_update_pheromone(aco_handle h) {
+  NvtxRange nvtx_range("aco_update_pheromone");
   if (!h) return fail(ACO_EINVAL, "NULL handle");
   if (!h->tours_valid) return fail(ACO_ESTATE, "no tours constructed since the last update");
   int rc = enqueue_update(h);
@@ -478,6 +481,7 @@ int aco_update_pheromone(aco_handle h) {
 }
 
 int aco_iterate(aco_handle h, int32_t iterations) {
+  NvtxRange nvtx_range("aco_iterate");
   if (!h) return fail(ACO_EINVAL, "NULL handle");
   if (iterations < 0) return fail(ACO_EINVAL, "iterations < 0");
   if (iterations == 0) return ACO_OK;
@@ -636,6 +640,7 @@ static uint64_t checkpoint_bytes(int n) {
 }
 
 int aco_save_state(aco_handle h, void* buf, uint64_t capacity, uint64_t* size) {
+  NvtxRange nvtx_range("aco_save_state");
   if (!h || !size) return fail(ACO_EINVAL, "NULL argument");
   const int n = h->I.n;
   *size = checkpoint_bytes(n);
@@ -677,6 +682,7 @@ int aco_save_state(aco_handle h, void* buf, uint64_t capacity, uint64_t* size) {
 }
 
 int aco_restore_state(aco_handle h, const void* buf, uint64_t size) {
+  NvtxRange nvtx_range("aco_restore_state");
   if (!h || !buf) return fail(ACO_EINVAL, "NULL argument");
   CheckpointHeader hd{};
   if (size < sizeof hd) return fail(ACO_EINVAL, "checkpoint too short");

@@ -370,6 +370,7 @@ static int pool_enqueue_step(aco_pool* p) {
 static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const int32_t* xy,
                              float alpha, float beta, float rho, int32_t m, uint64_t seed,
                              int32_t iterations, int32_t* slot) {
+  NvtxRange nvtx_range("aco_pool_admit");
   if (!p || !slot) return fail(ACO_EINVAL, "NULL argument");
   if (!p->unlimited && iterations < 1) return fail(ACO_EINVAL, "iterations must be >= 1");
   int rc = dist ? validate_instance(n, dist, alpha, beta, rho, m)
@@ -560,6 +561,7 @@ int aco_pool_admit_coords(aco_pool_handle p, int32_t n, const int32_t* xy, float
 }
 
 int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
+  NvtxRange nvtx_range("aco_pool_step");
   if (!p) return fail(ACO_EINVAL, "NULL pool");
   int rc;
   if (p->dirty && (rc = pool_rebuild(p)) != ACO_OK) return rc;
@@ -639,6 +641,7 @@ int aco_pool_set_autotune(aco_pool_handle p, int32_t on) {
 }
 
 int aco_pool_autotune(aco_pool_handle p) {
+  NvtxRange nvtx_range("aco_pool_autotune");
   if (!p) return fail(ACO_EINVAL, "NULL pool");
   int rc;
   if (p->dirty && (rc = pool_rebuild(p)) != ACO_OK) return rc;

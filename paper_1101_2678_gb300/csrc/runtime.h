@@ -4,8 +4,18 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace aco {
+
+// NVTX range around a host API call (visible to Nsight tools; a no-op when
+// no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Record a message for aco_last_error_message() and return `code`.
 int fail(int code, const char* fmt, ...);

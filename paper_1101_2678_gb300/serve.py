@@ -99,6 +99,13 @@ class Server:
         nxt = 0
         steps = 0
         max_live = 0
+        # (time, queued, live, HBM bytes in use) about once a second, and
+        # per-step queue depth and arena use for the summary
+        timeline = []
+        next_sample = 0.0
+        depth_sum = 0
+        depth_max = 0
+        bytes_max = 0
         t0 = time.perf_counter()
         while len(outcomes) < total:
             now = time.perf_counter() - t0
@@ -123,6 +130,14 @@ class Server:
                     time.sleep(max(0.0, min(0.01, arrivals[order[nxt]] - now)))
                 continue
             max_live = max(max_live, len(live))
+            queued_now = len(queue)  # arrived and waiting for admission
+            in_use = aco.aco_pool_stats(pool)["bytes_in_use"]
+            depth_sum += queued_now
+            depth_max = max(depth_max, queued_now)
+            bytes_max = max(bytes_max, in_use)
+            if now >= next_sample:
+                timeline.append([round(now, 3), queued_now, len(live), round(in_use / 2 ** 30, 3)])
+                next_sample = now + 1.0
             aco.aco_pool_step(pool)
             steps += 1
             for slot in aco.aco_pool_finished(pool):
@@ -141,5 +156,7 @@ class Server:
             elapsed_s=elapsed, steps=steps, max_live=max_live,
             solves_per_s=len(outcomes) / elapsed if elapsed > 0 else 0.0,
             p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+            queue_depth_max=depth_max, queue_depth_mean=depth_sum / max(steps, 1),
+            hbm_in_use_max_gb=bytes_max / 2 ** 30, timeline=timeline,
         )
         return outcomes, stats
