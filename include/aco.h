@@ -70,6 +70,12 @@ extern "C" {
 #define ACO_MAX_M 16384   /* ants per instance                               */
 
 /* ---- options (aco_set_option / aco_get_option) --------------------------- */
+#define ACO_OPT_CHECK 11       /* 1: after every construction a kernel checks
+                                  each tour (every city once, closed, stored
+                                  length = summed distances) and a failure
+                                  makes the next synchronising call return
+                                  ACO_ECUDA; 0 (default): no check.  A debug
+                                  aid: one extra launch per iteration.       */
 #define ACO_OPT_DEPOSIT 1      /* ACO_DEPOSIT_* below; default SYMMETRIC (the
                                   fastest measured on GB300)                  */
 #define ACO_OPT_STREAM 2       /* cudaStream_t as int64; 0 = the handle's own   */

@@ -35,6 +35,7 @@ ACO_OPT_LANES_PER_ANT = 7
 ACO_OPT_SELECTION = 8
 ACO_OPT_NN_LIST = 9
 ACO_OPT_STAGING = 10
+ACO_OPT_CHECK = 11
 ACO_SELECT_EQ1 = 0
 ACO_SELECT_DATA_PARALLEL = 1
 

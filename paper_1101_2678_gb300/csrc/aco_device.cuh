@@ -25,6 +25,7 @@ struct IterState {
 
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusBadTour = 2;
+constexpr int kStatusCheckFailed = 4;  // a tour failed the optional check (ACO_OPT_CHECK)
 
 // Everything a kernel needs to know about one instance.  Matrices are n rows
 // of `ld` elements (ld = n rounded up to a multiple of 4, padding zero).

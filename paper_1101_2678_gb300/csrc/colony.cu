@@ -158,6 +158,7 @@ struct aco_colony {
   int warps_per_ant = 0;
   int lanes_per_ant = 0;
   int ants_per_cta = 0;
+  int check = 0;  // ACO_OPT_CHECK
   bool tours_valid = false;
   bool constructed = false;
   bool nn_lists_built = false;
@@ -213,6 +214,8 @@ static int enqueue_construct(aco_colony* h) {
   if (e != cudaSuccess) return cuda_fail(e, "construct");
   if (h->profile && (e = record_event(h, h->ev[1], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
+  if (h->check && (e = launch_check_tours(h->I, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "check tours");
   if ((e = launch_best(h->I, h->stream)) != cudaSuccess) return cuda_fail(e, "best");
   if (h->profile && (e = record_event(h, h->ev[2], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
@@ -250,6 +253,8 @@ static int check_status(aco_colony* h) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "synchronize");
   if (status & kStatusTimeout) return fail(ACO_ETIMEOUT, "a device-side wait gave up");
+  if (status & kStatusCheckFailed)
+    return fail(ACO_ECUDA, "a constructed tour failed the check (device status 0x%x)", status);
   if (status) return fail(ACO_ECUDA, "device status 0x%x", status);
   return ACO_OK;
 }
@@ -807,6 +812,10 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
       if (value != 0 && value != 1) return fail(ACO_EINVAL, "staging must be 0 or 1");
       h->I.stage = (int)value;
       break;
+    case ACO_OPT_CHECK:
+      if (value != 0 && value != 1) return fail(ACO_EINVAL, "check must be 0 or 1");
+      h->check = (int)value;
+      break;
     case ACO_OPT_WARPS_PER_ANT:
     case ACO_OPT_LANES_PER_ANT:
     case ACO_OPT_ANTS_PER_CTA: {
@@ -851,6 +860,9 @@ int aco_get_option(aco_handle h, int32_t key, int64_t* value) {
       break;
     case ACO_OPT_STAGING:
       *value = h->I.stage;
+      break;
+    case ACO_OPT_CHECK:
+      *value = h->check;
       break;
     case ACO_OPT_NN_LIST:
       *value = h->I.nn;
@@ -897,7 +909,7 @@ int aco_kernel_launches_per_iteration(aco_handle h, int32_t* count) {
   *count = (h->I.variant != kVariantAs     ? 3
             : h->deposit == kDepositSort ? 3 + sort_deposit_launches(h->I.n)
                                          : launches_for_variant(h->deposit)) +
-           (h->I.nn > 0 ? 1 : 0);
+           (h->I.nn > 0 ? 1 : 0) + (h->check ? 1 : 0);
   return ACO_OK;
 }
 

@@ -42,6 +42,8 @@ int launches_for_variant(int variant);
 // MAX-MIN Ant System: trails to tau_max(C_nn); one update (evaporation, the
 // depositing tour's dtau, clamp, choice_info).
 cudaError_t launch_mmas_init(const Instance& I, int sms, cudaStream_t st);
+// Optional check of the constructed tours (ACO_OPT_CHECK).
+cudaError_t launch_check_tours(const Instance& I, cudaStream_t st);
 cudaError_t launch_mmas_update(const Instance& I, int sms, cudaStream_t st);
 // Ant Colony System: trails to 1/(n C_nn); construction with the local
 // update (one CTA, m <= kAcsMaxAnts); the global update on the best tour.

@@ -390,6 +390,39 @@ __global__ void dist_from_coords_kernel(Instance I, const int32_t* __restrict__ 
   }
 }
 
+// Optional check of the constructed tours (ACO_OPT_CHECK): one warp per
+// ant; every city must occur exactly once among tour[0..n), tour[n] must be
+// tour[0], and the stored length must equal the sum of the distances.  The
+// visited cities are counted in a shared-memory bitmap per warp.
+__global__ void check_tours_kernel(Instance I) {
+  extern __shared__ uint32_t check_bits[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (k >= I.m) return;
+  const int n = I.n, ld = I.ld, words = (n + 31) >> 5;
+  uint32_t* bits = check_bits + (size_t)warp * words;
+  for (int w = lane; w < words; w += 32) bits[w] = 0u;
+  __syncwarp();
+  const int32_t* t = I.tours + (size_t)k * I.ldt;
+  bool ok = true;
+  long long len = 0;
+  for (int s = lane; s < n; s += 32) {
+    const int a = t[s], b = t[s + 1];
+    if ((unsigned)a >= (unsigned)n || (unsigned)b >= (unsigned)n) {
+      ok = false;
+      continue;
+    }
+    const uint32_t old = atomicOr(&bits[a >> 5], 1u << (a & 31));
+    if (old & (1u << (a & 31))) ok = false;  // a city twice
+    len += I.dist[(size_t)a * ld + b];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
+  ok = __all_sync(FULL, ok);
+  if (lane == 0 && (!ok || t[n] != t[0] || len != I.lens[k]))
+    atomicOr(&I.st->status, kStatusCheckFailed);
+}
+
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
@@ -489,6 +522,13 @@ cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t 
   } else {
     choice_kernel<<<grid_for((size_t)I.n * I.ld, 256, sms), 256, 0, st>>>(I, 1);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_tours(const Instance& I, cudaStream_t st) {
+  const int warps = 4;
+  const size_t smem = (size_t)warps * ((I.n + 31) / 32) * sizeof(uint32_t);
+  check_tours_kernel<<<(I.m + warps - 1) / warps, 32 * warps, smem, st>>>(I);
   return cudaGetLastError();
 }
 

@@ -33,3 +33,26 @@ def test_bounded_wait_gives_up_and_context_survives(aco, orc):
         aco.aco_iterate(c.h, 3)
         assert np.array_equal(aco.aco_get_pheromone(c.h, 40), ref["tau32"])
 
+
+
+def test_tour_check_option_passes_on_valid_runs(aco, orc):
+    # With the check on, every construction is verified on the device; valid
+    # runs (all rules) report nothing and end as without the check.
+    inst = I.uniform_instance(120, 1000, seed=9)
+    ref = orc.run(inst.dist, 40, 4, 2)
+    with aco.Colony(inst.dist, 40, seed=2) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_CHECK, 1)
+        assert aco.aco_get_option(c.h, aco.ACO_OPT_CHECK) == 1
+        n_launch = aco.aco_kernel_launches_per_iteration(c.h)
+        aco.aco_iterate(c.h, 4)
+        assert np.array_equal(aco.aco_get_pheromone(c.h, 120), ref["tau32"])
+        aco.aco_set_option(c.h, aco.ACO_OPT_CHECK, 0)
+        assert aco.aco_kernel_launches_per_iteration(c.h) == n_launch - 1
+    for setup in (lambda h: aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, 10),
+                  lambda h: aco.aco_set_acs(h, 0.9, 0.1),
+                  lambda h: aco.aco_set_option(h, aco.ACO_OPT_SELECTION, 1)):
+        with aco.Colony(inst.dist, 10, seed=3) as c:
+            setup(c.h)
+            aco.aco_set_option(c.h, aco.ACO_OPT_CHECK, 1)
+            aco.aco_iterate(c.h, 3)
+            aco.aco_synchronize(c.h)
