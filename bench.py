@@ -609,6 +609,86 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batched_acs(args, rank, world, local):
+    """The batched workload's instances as Ant Colony System colonies (m = 10,
+    q0 0.9, xi 0.1, rho 0.1): one pool, one launch for all colonies per step,
+    vs the plain per-instance loop over the single-colony kernel."""
+    import torch
+    from paper_1101_2678_gb300 import aco, instances
+    torch.cuda.set_device(local)
+    aco.load()
+    w = instances.workload_batched(args.batch_count)
+    insts, seeds, iters = w["insts"], w["seeds"], w["iterations"]
+    if args.batch_iterations:
+        iters = args.batch_iterations
+    m, rho, q0, xi = 10, 0.1, 0.9, 0.1
+
+    def pool_run(subset, iterations):
+        need = sum(aco.aco_pool_bytes_needed(x.n, m) for x in subset) + (1 << 20)
+        p = aco.aco_pool_create(len(subset), need)
+        slots = [aco.aco_pool_admit_acs(p, x.dist, 1.0, 2.0, rho, m, seeds[i], iterations, q0, xi)
+                 for i, x in enumerate(subset)]
+        aco.aco_pool_synchronize(p)
+        return p, slots
+
+    p, _ = pool_run(insts[:4], 3)  # warm-up (module load, graph code paths)
+    while aco.aco_pool_step(p) > 0:
+        pass
+    aco.aco_pool_synchronize(p)
+    aco.aco_pool_destroy(p)
+    barrier(world)
+    p, slots = pool_run(insts, iters)
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    t0 = time.perf_counter()
+    launches = steps = 0
+    while True:
+        live = aco.aco_pool_step(p)
+        launches += aco.aco_pool_stats(p)["launches_last_step"]
+        steps += 1
+        if live == 0:
+            break
+    aco.aco_pool_synchronize(p)
+    t_batch = time.perf_counter() - t0
+    clk = clocks.stop() if clocks else None
+    best_batch = [aco.aco_pool_result(p, s, x.n)[1] for s, x in zip(slots, insts)]
+    aco.aco_pool_destroy(p)
+    t_loop = 0.0
+    best_loop = []
+    for i, x in enumerate([] if args.no_loop_baseline else insts):
+        c = aco.Colony(x.dist, m, seed=seeds[i], rho=rho)
+        aco.aco_set_acs(c.h, q0, xi)
+        aco.aco_synchronize(c.h)
+        t0 = time.perf_counter()
+        aco.aco_iterate(c.h, iters)
+        aco.aco_synchronize(c.h)
+        t_loop += time.perf_counter() - t0
+        best_loop.append(aco.aco_best_tour(c.h, x.n)[1])
+        c.close()
+    t_batch = max_over_ranks(t_batch, world)
+    if rank != 0:
+        return
+    ant_steps = sum(m * (x.n - 1) for x in insts) * iters
+    line = {
+        "metric": "batched solves/s", "value": world * len(insts) / t_batch, "unit": "solves/s",
+        "n_gpus": world, "steps": iters, "warmup": 3, "ms_per_step": t_batch / iters * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w["name"].replace("as-", "acs-"), "variant": "acs",
+                   "instances": len(insts), "m": m, "q0": q0, "xi": xi, "rho": rho,
+                   "n_min": min(x.n for x in insts), "n_max": max(x.n for x in insts),
+                   "iterations": iters, "pool_steps": steps,
+                   "l2": "not flushed (one continuous run)"},
+        "per_instance_loop_solves_per_s": len(insts) / t_loop if t_loop else None,
+        "speedup_vs_loop": t_loop / t_batch if t_loop else None,
+        "identical_best_lengths": best_batch == best_loop if best_loop else None,
+        "ant_steps_per_s": ant_steps / t_batch,
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_served(args, rank, world, local):
     """Poisson arrivals (n log-uniform in [48, 4096], m = min(n, 1024), 200 iterations)
     through the continuous-batching server with a 64 GB HBM budget."""
@@ -674,6 +754,9 @@ def main():
     args = parse()
     rank, world, local = dist_init(args)
     from paper_1101_2678_gb300 import instances
+    if args.workload == "batched" and args.variant == "acs":
+        run_batched_acs(args, rank, world, local)
+        return
     if args.workload == "batched":
         run_batched(args, rank, world, local)
         return

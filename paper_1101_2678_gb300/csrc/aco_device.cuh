@@ -1,12 +1,28 @@
 // Device-side building blocks shared by the Ant System kernels (sm_103a).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace aco {
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// Host: run `set` (a kernel attribute setting, which holds per device) the
+// first time it succeeds on the current device.  `done` keeps one bit per
+// device ordinal (ordinals >= 64 run `set` every time); concurrent first
+// calls may both run it, which is harmless for an idempotent setting.
+template <class F>
+inline cudaError_t once_per_device(std::atomic<unsigned long long>& done, F set) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return set();
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  const cudaError_t e = set();
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // Per-instance iteration state, resident on the device.
 struct IterState {

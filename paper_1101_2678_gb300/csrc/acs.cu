@@ -13,7 +13,8 @@
 //  - the global update: only the best-so-far tour's edges get
 //    tau <- fl(fl((1-rho) tau) + fl(rho dtau)), dtau = 1/C_bs.
 // The colony (m <= 32 ants, the variant's usual m = 10) runs in one CTA, one
-// warp per ant, so the per-step lockstep is a CTA barrier.
+// warp per ant, so the per-step lockstep is a CTA barrier; many colonies (a
+// pool's Ant Colony System slots) run as one launch of one CTA per colony.
 #include "aco_device.cuh"
 #include "construct.cuh"
 #include "kernels.h"
@@ -49,11 +50,14 @@ __device__ __forceinline__ float acs_local(float tau, float keep, float add) {
   return __fadd_rn(__fmul_rn(keep, tau), add);
 }
 
-__global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
-  extern __shared__ uint32_t acs_seen[];          // m tabu bitmaps of `words` words
-  __shared__ uint32_t s_edge[32];                 // (min << 16 | max) crossed by ant k
+// One colony in one CTA.  Warp k < m builds ant k's tour; further warps (a
+// launch over colonies with different m sizes the CTA for the largest) take
+// part in the lockstep barriers only.
+__device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* acs_seen,
+                                                   uint32_t* s_edge) {
   const int n = I.n, ld = I.ld, m = I.m;
   const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool active = k < m;
   const int words = (n + 31) >> 5;
   uint32_t* seen = acs_seen + (size_t)k * words;
   const uint32_t it = (uint32_t)I.st->iteration;
@@ -61,19 +65,22 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
   const float keep = __fsub_rn(1.0f, I.acs_xi), add = __fmul_rn(I.acs_xi, tau0);
   int32_t* tour = I.tours + (size_t)k * I.ldt;
 
-  for (int w = lane; w < words; w += 32) seen[w] = 0u;
-  __syncwarp();
-  const Philox4 x0 = step_draw(I.seed, 0u, (uint32_t)k, it);
-  const int start = (int)__umulhi(x0.x0, (uint32_t)n);
-  if (lane == 0) {
-    seen[start >> 5] |= 1u << (start & 31);
-    tour[0] = start;
+  int start = 0;
+  if (active) {
+    for (int w = lane; w < words; w += 32) seen[w] = 0u;
+    __syncwarp();
+    const Philox4 x0 = step_draw(I.seed, 0u, (uint32_t)k, it);
+    start = (int)__umulhi(x0.x0, (uint32_t)n);
+    if (lane == 0) {
+      seen[start >> 5] |= 1u << (start & 31);
+      tour[0] = start;
+    }
+    __syncwarp();
   }
-  __syncwarp();
   int cur = start;
   for (int s = 1; s <= n; ++s) {
     int next = start;
-    if (s < n) {
+    if (active && s < n) {
       const Philox4 x = step_draw(I.seed, (uint32_t)s, (uint32_t)k, it);
       const float* row = I.choice + (size_t)cur * ld;
       // Lane l reads cities 4l..4l+3 of every 128 with one 16-byte load (ld
@@ -179,29 +186,32 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
     // values read here are the current ones and the load latency overlaps
     // the other ants' selection.
     float t = 0.0f, h = 0.0f;
-    if (lane == 0) {
+    if (active && lane == 0) {
       s_edge[k] = (lo << 16) | hi;
       t = __ldcg(I.tau + ab);
       h = I.heta[ab];
     }
     __syncthreads();
-    const uint32_t e = s_edge[k];
-    const unsigned same = __ballot_sync(FULL, lane < m && s_edge[lane < m ? lane : 0] == e);
-    if (lane == 0 && __ffs(same) - 1 == k) {
-      for (int c = __popc(same); c > 0; --c) t = acs_local(t, keep, add);
-      const float ch = choice_of(t, h, I.alpha);
-      I.tau[ab] = t;
-      I.tau[ba] = t;
-      I.choice[ab] = ch;
-      I.choice[ba] = ch;
-    }
-    if (lane == 0 && s < n) {
-      seen[next >> 5] |= 1u << (next & 31);
-      tour[s] = next;
+    if (active) {
+      const uint32_t e = s_edge[k];
+      const unsigned same = __ballot_sync(FULL, lane < m && s_edge[lane < m ? lane : 0] == e);
+      if (lane == 0 && __ffs(same) - 1 == k) {
+        for (int c = __popc(same); c > 0; --c) t = acs_local(t, keep, add);
+        const float ch = choice_of(t, h, I.alpha);
+        I.tau[ab] = t;
+        I.tau[ba] = t;
+        I.choice[ab] = ch;
+        I.choice[ba] = ch;
+      }
+      if (lane == 0 && s < n) {
+        seen[next >> 5] |= 1u << (next & 31);
+        tour[s] = next;
+      }
     }
     __syncthreads();
     cur = next;
   }
+  if (!active) return;
   if (lane == 0) tour[n] = start;
   __syncwarp();
   long long len = 0;
@@ -211,13 +221,29 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
   if (lane == 0) I.lens[k] = len;
 }
 
-// Global update on the best-so-far tour: one thread per edge (each edge of
-// a closed tour of n >= 3 cities occurs once).
-__global__ void acs_global_kernel(Instance I, int bump_iteration) {
+__global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
+  extern __shared__ uint32_t acs_seen[];  // m tabu bitmaps of (n + 31) / 32 words
+  __shared__ uint32_t s_edge[32];         // (min << 16 | max) crossed by ant k
+  acs_construct_body(I, acs_seen, s_edge);
+}
+
+// Many colonies per launch: CTA b runs the colony of slot slots[b].
+__global__ void __launch_bounds__(1024, 1)
+    acs_construct_slots_kernel(const Instance* __restrict__ insts, const int* __restrict__ slots) {
+  extern __shared__ uint32_t acs_seen[];
+  __shared__ uint32_t s_edge[32];
+  acs_construct_body(insts[slots[blockIdx.x]], acs_seen, s_edge);
+}
+
+// Global update on the best-so-far tour: edge s of the tour per thread from
+// `first` in steps of `stride` (each edge of a closed tour of n >= 3 cities
+// occurs once).
+__device__ __forceinline__ void acs_global_body(const Instance& I, int first, int stride,
+                                                bool bump_iteration) {
   const int n = I.n, ld = I.ld;
   const float keep = __fsub_rn(1.0f, I.rho);
   const float dep = __fmul_rn(I.rho, (float)(1.0 / (double)I.st->best_len));
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+  for (int s = first; s < n; s += stride) {
     const int a = I.best_tour[s], b = I.best_tour[s + 1];
     const size_t ab = (size_t)a * ld + b, ba = (size_t)b * ld + a;
     const float t = __fadd_rn(__fmul_rn(keep, I.tau[ab]), dep);
@@ -227,7 +253,17 @@ __global__ void acs_global_kernel(Instance I, int bump_iteration) {
     I.choice[ab] = ch;
     I.choice[ba] = ch;
   }
-  if (bump_iteration && blockIdx.x == 0 && threadIdx.x == 0) I.st->iteration += 1;
+  if (bump_iteration) I.st->iteration += 1;
+}
+
+__global__ void acs_global_kernel(Instance I) {
+  acs_global_body(I, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                  blockIdx.x == 0 && threadIdx.x == 0);
+}
+
+__global__ void acs_global_slots_kernel(const Instance* __restrict__ insts,
+                                        const int* __restrict__ slots) {
+  acs_global_body(insts[slots[blockIdx.x]], threadIdx.x, blockDim.x, threadIdx.x == 0);
 }
 
 // Start: tau = tau0 = (float)(1 / (n C_nn)) off the diagonal, choice_info.
@@ -260,7 +296,23 @@ cudaError_t launch_acs_construct(const Instance& I, cudaStream_t st) {
 }
 
 cudaError_t launch_acs_global(const Instance& I, cudaStream_t st) {
-  acs_global_kernel<<<(I.n + 255) / 256, 256, 0, st>>>(I, 1);
+  acs_global_kernel<<<(I.n + 255) / 256, 256, 0, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_acs_construct_slots(const Instance* insts, const int* slots, int count,
+                                       int max_m, int max_n, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  if (max_m < 1 || max_m > kAcsMaxAnts) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)max_m * ((max_n + 31) / 32) * sizeof(uint32_t);
+  acs_construct_slots_kernel<<<count, 32 * max_m, smem, st>>>(insts, slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_acs_global_slots(const Instance* insts, const int* slots, int count,
+                                    cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  acs_global_slots_kernel<<<count, 256, 0, st>>>(insts, slots);
   return cudaGetLastError();
 }
 

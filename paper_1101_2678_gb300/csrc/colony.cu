@@ -112,6 +112,13 @@ cudaError_t launch_construct_items(const Instance* insts, const int2* items, int
   return cudaErrorInvalidValue;
 }
 
+// floor(q0 2^32) for q0 in [0, 1]; q0 = 1 gives 2^32 (every step exploits).
+unsigned long long acs_threshold_of(double q0) {
+  return q0 >= 1.0  ? (1ull << 32)
+         : q0 > 0.0 ? (unsigned long long)std::floor(q0 * 4294967296.0)
+                    : 0ull;
+}
+
 int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -608,10 +615,7 @@ int aco_set_acs(aco_handle h, double q0, float xi) {
     return fail(ACO_EINVAL, "the Ant Colony System uses its own rule (no lists, no selection option)");
   if (h->constructed || h->host_iteration != 0 || h->I.variant != kVariantAs)
     return fail(ACO_ESTATE, "the update rule is chosen once, before the first construction");
-  // floor(q0 2^32); q0 = 1 gives 2^32 (every step exploits).
-  h->I.acs_threshold = q0 >= 1.0 ? (1ull << 32)
-                       : q0 > 0.0 ? (unsigned long long)std::floor(q0 * 4294967296.0)
-                                  : 0ull;
+  h->I.acs_threshold = acs_threshold_of(q0);
   h->I.acs_xi = xi;
   h->I.variant = kVariantAcs;
   drop_graph(h);

@@ -587,21 +587,20 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
 }
 
 // Dynamic shared memory for a CTA of `warps` warps, with the opt-in above
-// 48 KB set once per kernel.
+// 48 KB set once per kernel and device.
 template <int C, int G, int H, bool kItems, int R = 0>
 inline size_t construct_smem_setup(int warps) {
   const size_t bytes = (size_t)groups_per_cta<G, H>(warps) * StageLayout<C, G, H>::kBytes;
-  static bool done = false;
-  if (!done) {
+  static std::atomic<unsigned long long> done{0};
+  once_per_device(done, [] {
     const int most = groups_per_cta<G, H>(8) * StageLayout<C, G, H>::kBytes;
     if constexpr (kItems)
-      cudaFuncSetAttribute(construct_items_kernel<C, G, H>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      return cudaFuncSetAttribute(construct_items_kernel<C, G, H>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     else
-      cudaFuncSetAttribute(construct_kernel<C, G, H, R>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    done = true;
-  }
+      return cudaFuncSetAttribute(construct_kernel<C, G, H, R>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  });
   return bytes;
 }
 

@@ -51,6 +51,12 @@ constexpr int kAcsMaxAnts = 32;
 cudaError_t launch_acs_init(const Instance& I, int sms, cudaStream_t st);
 cudaError_t launch_acs_construct(const Instance& I, cudaStream_t st);
 cudaError_t launch_acs_global(const Instance& I, cudaStream_t st);
+// The same for `count` colonies insts[slots[b]] per launch (one CTA each,
+// sized for the largest m and n among them).
+cudaError_t launch_acs_construct_slots(const Instance* insts, const int* slots, int count,
+                                       int max_m, int max_n, cudaStream_t st);
+cudaError_t launch_acs_global_slots(const Instance* insts, const int* slots, int count,
+                                    cudaStream_t st);
 int gather_warps_per_cta(int ld);
 // Atomic-free deposit by a radix sort of the tour edges (sort_deposit.cu):
 // scratch bytes for n cities and m ants, the deposit into the upper-triangle

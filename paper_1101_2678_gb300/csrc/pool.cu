@@ -92,6 +92,7 @@ struct PoolSlot {
   Instance I{};
   cudaEvent_t ready = nullptr;  // setup done on the side stream
   bool wait_ready = false;
+  bool acs = false;  // Ant Colony System slot (otherwise the Ant System)
 };
 
 struct aco_pool {
@@ -110,9 +111,11 @@ struct aco_pool {
   int2* d_items = nullptr;
   int2* d_rows = nullptr;
   int* d_coords = nullptr;  // staging for aco_pool_admit_coords (n pairs)
+  int* d_acs = nullptr;     // live Ant Colony System slots
   size_t items_cap = 0, rows_cap = 0;
   // host mirrors of the lists
-  std::vector<int> h_live;
+  std::vector<int> h_live, h_acs;
+  int acs_max_m = 0, acs_max_n = 0;
   std::vector<int2> h_items, h_rows;
   struct Class {
     ConstructTiling t;
@@ -193,10 +196,12 @@ static int ensure_capacity(void** ptr, size_t* cap, size_t need, size_t elem) {
 // Rebuild the device work lists for the current live set.
 static int pool_rebuild(aco_pool* p) {
   p->h_live.clear();
+  p->h_acs.clear();
   p->h_items.clear();
   p->h_rows.clear();
   p->classes.clear();
   p->max_ld = 4;
+  p->acs_max_m = p->acs_max_n = 0;
   std::vector<int> live;
   for (int s = 0; s < p->max_slots; ++s)
     if (p->slots[(size_t)s].live) live.push_back(s);
@@ -206,10 +211,20 @@ static int pool_rebuild(aco_pool* p) {
     return na != nb ? na > nb : a < b;
   });
   p->h_live = live;
-  // group by tiling class, keeping the longest-first order inside a class
+  // Ant Colony System slots: one CTA per colony in one launch of their own
+  for (int s : live) {
+    const PoolSlot& sl = p->slots[(size_t)s];
+    if (!sl.acs) continue;
+    p->h_acs.push_back(s);
+    p->acs_max_m = std::max(p->acs_max_m, sl.m);
+    p->acs_max_n = std::max(p->acs_max_n, sl.n);
+  }
+  // group the Ant System slots by tiling class, keeping the longest-first
+  // order inside a class
   std::map<std::tuple<int, int, int>, std::vector<int>> by_class;
   std::vector<std::tuple<int, int, int>> class_order;
   for (int s : live) {
+    if (p->slots[(size_t)s].acs) continue;
     const ConstructTiling t = batched_construct_tiling(p->slots[(size_t)s].n);
     const auto key = std::make_tuple(t.G, t.H, t.C);
     if (!by_class.count(key)) class_order.push_back(key);
@@ -239,6 +254,7 @@ static int pool_rebuild(aco_pool* p) {
   }
   for (int s : live) {
     const PoolSlot& sl = p->slots[(size_t)s];
+    if (sl.acs) continue;
     p->max_ld = std::max(p->max_ld, sl.I.ld);
     for (int i = 0; i < sl.n; ++i) p->h_rows.push_back(make_int2(s, i));
   }
@@ -254,6 +270,9 @@ static int pool_rebuild(aco_pool* p) {
                         cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && !p->h_live.empty())
     e = cudaMemcpyAsync(p->d_live, p->h_live.data(), p->h_live.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && !p->h_acs.empty())
+    e = cudaMemcpyAsync(p->d_acs, p->h_acs.data(), p->h_acs.size() * sizeof(int),
                         cudaMemcpyHostToDevice, p->stream);
   // The host vectors must outlive the copies: synchronise before they change.
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -335,18 +354,28 @@ static int pool_wait_ready(aco_pool* p) {
 static int pool_enqueue_step(aco_pool* p) {
   cudaError_t e;
   int launches = 0;
-  // Fork: every tiling class gets its own stream so that the tail of one
-  // class overlaps the others; join before the best/update launches.
+  // Fork: every tiling class, and the Ant Colony System colonies, get their
+  // own stream so that the tail of one overlaps the others; join before the
+  // best/update launches.
   const int ncls = (int)p->classes.size();
-  const int nstreams = std::min(ncls, (int)aco_pool::kClassStreams);
+  const int nacs = (int)p->h_acs.size();
+  const int nstreams = std::min(ncls + (nacs > 0 ? 1 : 0), (int)aco_pool::kClassStreams);
   if (nstreams > 1 && (e = cudaEventRecord(p->fork_ev, p->stream)) != cudaSuccess)
     return cuda_fail(e, "pool fork");
   for (int i = 0; i < nstreams && nstreams > 1; ++i)
     if ((e = cudaStreamWaitEvent(p->class_stream[i], p->fork_ev, 0)) != cudaSuccess)
       return cuda_fail(e, "pool fork wait");
+  // The colonies (n lockstep steps each) go first, on the first stream.
+  const int first = nacs > 0 ? 1 : 0;
+  if (nacs > 0) {
+    cudaStream_t st = nstreams > 1 ? p->class_stream[0] : p->stream;
+    e = launch_acs_construct_slots(p->d_inst, p->d_acs, nacs, p->acs_max_m, p->acs_max_n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pool acs construct");
+    ++launches;
+  }
   for (int ci = 0; ci < ncls; ++ci) {
     const auto& c = p->classes[(size_t)ci];
-    cudaStream_t st = nstreams > 1 ? p->class_stream[ci % nstreams] : p->stream;
+    cudaStream_t st = nstreams > 1 ? p->class_stream[(ci + first) % nstreams] : p->stream;
     e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, st);
     if (e != cudaSuccess) return cuda_fail(e, "pool construct");
     ++launches;
@@ -360,19 +389,37 @@ static int pool_enqueue_step(aco_pool* p) {
   if ((e = launch_best_slots(p->d_inst, p->d_live, (int)p->h_live.size(), p->stream)) !=
       cudaSuccess)
     return cuda_fail(e, "pool best");
+  ++launches;
   if ((e = launch_update_rows(p->d_inst, p->d_rows, (int)p->h_rows.size(), p->max_ld,
                               p->stream)) != cudaSuccess)
     return cuda_fail(e, "pool update");
-  p->launches = launches + 2;
+  launches += p->h_rows.empty() ? 0 : 1;
+  if ((e = launch_acs_global_slots(p->d_inst, p->d_acs, nacs, p->stream)) != cudaSuccess)
+    return cuda_fail(e, "pool acs update");
+  launches += nacs > 0 ? 1 : 0;
+  p->launches = launches;
   return ACO_OK;
 }
 
+// Ant Colony System parameters of an admission (acs = false: the Ant System).
+struct AcsArgs {
+  bool acs = false;
+  double q0 = 0.0;
+  float xi = 0.0f;
+};
+
 static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const int32_t* xy,
                              float alpha, float beta, float rho, int32_t m, uint64_t seed,
-                             int32_t iterations, int32_t* slot) {
+                             int32_t iterations, int32_t* slot, AcsArgs acs = AcsArgs{}) {
   NvtxRange nvtx_range("aco_pool_admit");
   if (!p || !slot) return fail(ACO_EINVAL, "NULL argument");
   if (!p->unlimited && iterations < 1) return fail(ACO_EINVAL, "iterations must be >= 1");
+  if (acs.acs) {
+    if (!(acs.q0 >= 0.0 && acs.q0 <= 1.0)) return fail(ACO_EINVAL, "q0 must lie in [0, 1]");
+    if (!(acs.xi >= 0.0f && acs.xi <= 1.0f)) return fail(ACO_EINVAL, "xi must lie in [0, 1]");
+    if (m < 1 || m > kAcsMaxAnts)
+      return fail(ACO_EINVAL, "the Ant Colony System runs 1 to %d ants (m=%d)", kAcsMaxAnts, m);
+  }
   int rc = dist ? validate_instance(n, dist, alpha, beta, rho, m)
                 : validate_coords_public(n, xy);
   if (rc) return rc;
@@ -397,6 +444,7 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
   sl = PoolSlot{};
   sl.ready = ev;
   sl.used = true;
+  sl.acs = acs.acs;
   sl.n = n;
   sl.m = m;
   sl.iters_left = p->unlimited ? -1 : iterations;
@@ -412,6 +460,11 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
   I.beta = beta;
   I.rho = rho;
   I.seed = seed;
+  if (acs.acs) {
+    I.variant = kVariantAcs;
+    I.acs_threshold = acs_threshold_of(acs.q0);
+    I.acs_xi = acs.xi;
+  }
   char* b = (char*)p->arena + off;
   I.dist = (const int32_t*)(b + L.dist);
   I.heta = (float*)(b + L.heta);
@@ -453,6 +506,7 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
                              p->side)) != cudaSuccess)
       break;
     if ((e = launch_setup(I, p->sms, p->side)) != cudaSuccess) break;
+    if (acs.acs && (e = launch_acs_init(I, p->sms, p->side)) != cudaSuccess) break;
     e = cudaEventRecord(sl.ready, p->side);
   } while (0);
   if (e != cudaSuccess) {
@@ -505,6 +559,7 @@ int aco_pool_create(int32_t max_slots, uint64_t budget_bytes, aco_pool_handle* o
     if ((e = cudaMalloc(&p->arena, p->budget)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->d_inst, sizeof(Instance) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->d_live, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&p->d_acs, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess) break;
     for (int i = 0; i < aco_pool::kClassStreams && e == cudaSuccess; ++i) {
       e = cudaStreamCreateWithFlags(&p->class_stream[i], cudaStreamNonBlocking);
@@ -531,6 +586,7 @@ int aco_pool_destroy(aco_pool_handle p) {
   if (p->arena) cudaFree(p->arena);
   if (p->d_inst) cudaFree(p->d_inst);
   if (p->d_live) cudaFree(p->d_live);
+  if (p->d_acs) cudaFree(p->d_acs);
   if (p->d_items) cudaFree(p->d_items);
   if (p->d_rows) cudaFree(p->d_rows);
   for (int i = 0; i < aco_pool::kClassStreams; ++i) {
@@ -558,6 +614,29 @@ int aco_pool_admit_coords(aco_pool_handle p, int32_t n, const int32_t* xy, float
                           int32_t* slot) {
   if (!xy) return fail(ACO_EINVAL, "xy is NULL");
   return pool_admit_common(p, n, nullptr, xy, alpha, beta, rho, m, seed, iterations, slot);
+}
+
+int aco_pool_admit_acs(aco_pool_handle p, int32_t n, const int32_t* dist, float alpha,
+                       float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
+                       double q0, float xi, int32_t* slot) {
+  if (!dist) return fail(ACO_EINVAL, "dist is NULL");
+  AcsArgs acs;
+  acs.acs = true;
+  acs.q0 = q0;
+  acs.xi = xi;
+  return pool_admit_common(p, n, dist, nullptr, alpha, beta, rho, m, seed, iterations, slot,
+                           acs);
+}
+
+int aco_pool_admit_acs_coords(aco_pool_handle p, int32_t n, const int32_t* xy, float alpha,
+                              float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
+                              double q0, float xi, int32_t* slot) {
+  if (!xy) return fail(ACO_EINVAL, "xy is NULL");
+  AcsArgs acs;
+  acs.acs = true;
+  acs.q0 = q0;
+  acs.xi = xi;
+  return pool_admit_common(p, n, nullptr, xy, alpha, beta, rho, m, seed, iterations, slot, acs);
 }
 
 int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
@@ -700,6 +779,8 @@ int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t* warps_per_ant,
   if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
     return fail(ACO_EINVAL, "slot %d is not live", slot);
   if (p->dirty) return fail(ACO_ESTATE, "no step has run since the live set changed");
+  if (p->slots[(size_t)slot].acs)
+    return fail(ACO_EINVAL, "slot %d runs the Ant Colony System (one CTA per colony)", slot);
   const int n = p->slots[(size_t)slot].n;
   for (const auto& c : p->classes)
     if (c.key == std::make_tuple(batched_construct_tiling(n).G, batched_construct_tiling(n).H,

@@ -23,6 +23,8 @@ int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 // Streaming multiprocessors of the current device.
 int device_sms();
+// Ant Colony System exploitation threshold floor(q0 2^32), q0 in [0, 1].
+unsigned long long acs_threshold_of(double q0);
 // Argument checks shared by aco_create and the batch/pool admission.
 int validate_instance(int32_t n, const int32_t* dist, float alpha, float beta, float rho,
                       int32_t m);

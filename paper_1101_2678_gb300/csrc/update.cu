@@ -463,12 +463,11 @@ cudaError_t launch_update_rows(const Instance* insts, const int2* rows, int coun
   if (count <= 0) return cudaSuccess;
   const int w = gather_warps_per_cta(max_ld);
   const size_t smem = (size_t)w * max_ld * sizeof(unsigned long long);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(update_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         100 * 1024);
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_set{0};
+  once_per_device(attr_set, [] {
+    return cudaFuncSetAttribute(update_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                100 * 1024);
+  });
   update_rows_kernel<<<(count + w - 1) / w, 32 * w, smem, st>>>(insts, rows, count, max_ld);
   return cudaGetLastError();
 }
@@ -507,12 +506,11 @@ cudaError_t launch_update(const Instance& I, int variant, int sms, cudaStream_t 
   if (variant == kDepositGather) {
     const int w = gather_warps_per_cta(I.ld);
     const size_t smem = (size_t)w * I.ld * sizeof(unsigned long long);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(update_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           100 * 1024);
-      attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_set{0};
+    once_per_device(attr_set, [] {
+      return cudaFuncSetAttribute(update_gather_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    });
     update_gather_kernel<<<(I.n + w - 1) / w, 32 * w, smem, st>>>(I, 1);
   } else if (variant == kDepositAtomicU64) {
     apply_acc_kernel<<<grid_for((size_t)I.n * I.ld / 4, 256, sms), 256, 0, st>>>(I, 1);

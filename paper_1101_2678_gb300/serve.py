@@ -3,9 +3,9 @@
 Requests (TSP instances given by integer coordinates) arrive over time.  The
 server admits them in arrival order whenever the pool has a free slot and
 enough of its HBM budget, keeps every admitted instance's state resident on
-the device, and runs one Ant System iteration for all live instances per
-step, so work from requests that arrived at different times overlaps on the
-GPU.  A request finishes after its own number of iterations; its latency is
+the device, and runs one iteration for all live instances per step (Ant
+System and Ant Colony System requests side by side), so work from requests
+that arrived at different times overlaps on the GPU.  A request finishes after its own number of iterations; its latency is
 completion time minus arrival time (queueing included).
 
 All compute happens in the library's kernels (aco_pool_step); this module only
@@ -31,6 +31,11 @@ class Request:
     alpha: float = 1.0
     beta: float = 2.0
     rho: float = 0.5
+    # "as": the Ant System; "acs": the Ant Colony System with q0 and xi
+    # (m <= 32; rho is then its global-update rate)
+    variant: str = "as"
+    q0: float = 0.9
+    xi: float = 0.1
 
     @property
     def n(self) -> int:
@@ -119,8 +124,12 @@ class Server:
                 w = step_work(r)
                 if live and live_work + w > self.max_step_work:
                     break
-                slot = aco.aco_pool_admit_coords(pool, r.coords, r.alpha, r.beta, r.rho, r.m,
-                                                 r.seed, r.iterations)
+                if r.variant == "acs":
+                    slot = aco.aco_pool_admit_acs_coords(pool, r.coords, r.alpha, r.beta, r.rho,
+                                                         r.m, r.seed, r.iterations, r.q0, r.xi)
+                else:
+                    slot = aco.aco_pool_admit_coords(pool, r.coords, r.alpha, r.beta, r.rho,
+                                                     r.m, r.seed, r.iterations)
                 if slot is None:
                     break
                 live[slot] = (queue.popleft(), time.perf_counter() - t0)
