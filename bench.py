@@ -609,10 +609,13 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
-def run_batched_acs(args, rank, world, local):
-    """The batched workload's instances as Ant Colony System colonies (m = 10,
-    q0 0.9, xi 0.1, rho 0.1): one pool, one launch for all colonies per step,
-    vs the plain per-instance loop over the single-colony kernel."""
+def run_batched_rule(args, rank, world, local):
+    """The batched workload's instances under another update rule, in one pool
+    vs the plain per-instance loop over the single-handle kernels:
+    acs: Ant Colony System colonies (m = 10, q0 0.9, xi 0.1, rho 0.1), one
+    launch for all colonies per step; mmas: the MAX-MIN Ant System (m = n,
+    rho 0.02, p_best 0.05, iteration-best deposit), construction classes
+    shared with the Ant System path and its own row update."""
     import torch
     from paper_1101_2678_gb300 import aco, instances
     torch.cuda.set_device(local)
@@ -621,13 +624,24 @@ def run_batched_acs(args, rank, world, local):
     insts, seeds, iters = w["insts"], w["seeds"], w["iterations"]
     if args.batch_iterations:
         iters = args.batch_iterations
-    m, rho, q0, xi = 10, 0.1, 0.9, 0.1
+    acs = args.variant == "acs"
+    ms = [10] * len(insts) if acs else list(w["ms"])
+    rho = 0.1 if acs else 0.02
+    q0, xi, p_best = 0.9, 0.1, 0.05
+
+    def admit(p, i, x, iterations):
+        if acs:
+            return aco.aco_pool_admit_acs(p, x.dist, 1.0, 2.0, rho, ms[i], seeds[i], iterations,
+                                          q0, xi)
+        return aco.aco_pool_admit_mmas(p, x.dist, 1.0, 2.0, rho, ms[i], seeds[i], iterations,
+                                       p_best, False)
 
     def pool_run(subset, iterations):
-        need = sum(aco.aco_pool_bytes_needed(x.n, m) for x in subset) + (1 << 20)
-        p = aco.aco_pool_create(len(subset), need)
-        slots = [aco.aco_pool_admit_acs(p, x.dist, 1.0, 2.0, rho, m, seeds[i], iterations, q0, xi)
-                 for i, x in enumerate(subset)]
+        need = sum(aco.aco_pool_bytes_needed(x.n, ms[i]) for i, x in enumerate(subset))
+        p = aco.aco_pool_create(len(subset), need + (1 << 20))
+        if args.no_autotune:
+            aco.aco_pool_set_autotune(p, False)
+        slots = [admit(p, i, x, iterations) for i, x in enumerate(subset)]
         aco.aco_pool_synchronize(p)
         return p, slots
 
@@ -638,6 +652,12 @@ def run_batched_acs(args, rank, world, local):
     aco.aco_pool_destroy(p)
     barrier(world)
     p, slots = pool_run(insts, iters)
+    # the construction tilings of the MAX-MIN classes are chosen before the
+    # timed run (the choice changes no result)
+    t_tune = time.perf_counter()
+    aco.aco_pool_autotune(p)
+    aco.aco_pool_synchronize(p)
+    t_tune = time.perf_counter() - t_tune
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -657,8 +677,11 @@ def run_batched_acs(args, rank, world, local):
     t_loop = 0.0
     best_loop = []
     for i, x in enumerate([] if args.no_loop_baseline else insts):
-        c = aco.Colony(x.dist, m, seed=seeds[i], rho=rho)
-        aco.aco_set_acs(c.h, q0, xi)
+        c = aco.Colony(x.dist, ms[i], seed=seeds[i], rho=rho)
+        if acs:
+            aco.aco_set_acs(c.h, q0, xi)
+        else:
+            aco.aco_set_mmas(c.h, p_best, False)
         aco.aco_synchronize(c.h)
         t0 = time.perf_counter()
         aco.aco_iterate(c.h, iters)
@@ -669,16 +692,18 @@ def run_batched_acs(args, rank, world, local):
     t_batch = max_over_ranks(t_batch, world)
     if rank != 0:
         return
-    ant_steps = sum(m * (x.n - 1) for x in insts) * iters
+    ant_steps = sum(m * (x.n - 1) for m, x in zip(ms, insts)) * iters
+    rule = ({"variant": "acs", "m": 10, "q0": q0, "xi": xi, "rho": rho} if acs else
+            {"variant": "mmas", "m": "n", "p_best": p_best, "deposit": "iteration best",
+             "rho": rho, "autotune_seconds": t_tune})
     line = {
         "metric": "batched solves/s", "value": world * len(insts) / t_batch, "unit": "solves/s",
         "n_gpus": world, "steps": iters, "warmup": 3, "ms_per_step": t_batch / iters * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": w["name"].replace("as-", "acs-"), "variant": "acs",
-                   "instances": len(insts), "m": m, "q0": q0, "xi": xi, "rho": rho,
-                   "n_min": min(x.n for x in insts), "n_max": max(x.n for x in insts),
-                   "iterations": iters, "pool_steps": steps,
+        "config": {"workload": w["name"].replace("as-", args.variant + "-"), **rule,
+                   "instances": len(insts), "n_min": min(x.n for x in insts),
+                   "n_max": max(x.n for x in insts), "iterations": iters, "pool_steps": steps,
                    "l2": "not flushed (one continuous run)"},
         "per_instance_loop_solves_per_s": len(insts) / t_loop if t_loop else None,
         "speedup_vs_loop": t_loop / t_batch if t_loop else None,
@@ -754,8 +779,8 @@ def main():
     args = parse()
     rank, world, local = dist_init(args)
     from paper_1101_2678_gb300 import instances
-    if args.workload == "batched" and args.variant == "acs":
-        run_batched_acs(args, rank, world, local)
+    if args.workload == "batched" and args.variant != "as":
+        run_batched_rule(args, rank, world, local)
         return
     if args.workload == "batched":
         run_batched(args, rank, world, local)

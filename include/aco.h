@@ -347,11 +347,12 @@ int aco_create_coords(int32_t n, const int32_t *xy, float alpha, float beta, flo
  * A pool owns one HBM arena of `budget_bytes`; every admitted instance gets
  * its own dist / eta^beta / tau / choice_info / tours / best-tour block from
  * it and keeps it until released.  aco_pool_step() runs one iteration for
- * every live slot: one construction launch per tiling class (Ant System
- * instances of similar n), one launch for all Ant Colony System slots, one
- * best launch for all slots, one gather-update launch for the Ant System
- * slots and one global-update launch for the Ant Colony System slots,
- * captured as a CUDA graph while the live set is unchanged.  Random numbers use each instance's own seed and iteration
+ * every live slot: one construction launch per tiling class (Ant System and
+ * MAX-MIN Ant System instances of similar n), one launch for all Ant Colony
+ * System slots, one best launch for all slots, one row-update launch (the
+ * gather update, or the MAX-MIN update) and one global-update launch for the
+ * Ant Colony System slots, captured as a CUDA graph while the live set is
+ * unchanged.  Random numbers use each instance's own seed and iteration
  * counter, so an instance's results are identical alone and in any mix.
  * Pools use the deterministic gather deposit.  A pool is not thread-safe.
  * ======================================================================== */
@@ -384,23 +385,21 @@ int aco_pool_admit_coords(aco_pool_handle p, int32_t n, const int32_t *xy, float
                           int32_t *slot);
 
 /*
- * aco_pool_admit_acs / aco_pool_admit_acs_coords - as aco_pool_admit /
- * aco_pool_admit_coords, but the slot runs the Ant Colony
- * System of aco_set_acs (same rules: tau0 = 1/(n C_nn), the pseudo-random
- * proportional rule with q0, the lockstep local update with xi, the global
- * update with rho on the best-so-far tour).  1 <= m <= 32 and q0, xi in
- * [0, 1] (ACO_EINVAL otherwise).  Every aco_pool_step runs all live Ant
- * Colony System slots in one launch, one CTA per colony, beside the Ant
- * System classes; a slot's results are those of a handle created with the
- * same arguments and switched by aco_set_acs(q0, xi).  aco_pool_tiling
- * answers ACO_EINVAL for such a slot.
+ * aco_pool_set_acs / aco_pool_set_mmas - switch a live slot that has not yet
+ * taken part in a step to the Ant Colony System or the MAX-MIN Ant System,
+ * with the rules and argument ranges of aco_set_acs / aco_set_mmas (rho, as
+ * admitted, is then the rule's own rate).  The start trails are written on
+ * the side stream after the admission's setup.  A slot's results are those
+ * of a handle created with the same arguments and switched the same way.
+ * Every aco_pool_step runs all live Ant Colony System slots in one launch,
+ * one CTA per colony (m <= 32, ACO_EINVAL otherwise), beside the Ant System
+ * classes; MAX-MIN slots construct with the Ant System slots and take the
+ * rule's update in the row-update launch.  ACO_ESTATE once the slot has
+ * stepped or already switched; aco_pool_tiling answers ACO_EINVAL for an
+ * Ant Colony System slot.
  */
-int aco_pool_admit_acs(aco_pool_handle p, int32_t n, const int32_t *dist, float alpha,
-                       float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
-                       double q0, float xi, int32_t *slot);
-int aco_pool_admit_acs_coords(aco_pool_handle p, int32_t n, const int32_t *xy, float alpha,
-                              float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
-                              double q0, float xi, int32_t *slot);
+int aco_pool_set_acs(aco_pool_handle p, int32_t slot, double q0, float xi);
+int aco_pool_set_mmas(aco_pool_handle p, int32_t slot, double p_best, int32_t best_so_far);
 
 /*
  * aco_pool_step - one iteration for every live slot (asynchronous).  A slot

@@ -92,12 +92,8 @@ SIGNATURES = [
                                  C.c_uint64, C.c_int32, _i32p]),
     ("aco_pool_admit_coords", C.c_int, [_vp, C.c_int32, _vp, C.c_float, C.c_float, C.c_float,
                                         C.c_int32, C.c_uint64, C.c_int32, _i32p]),
-    ("aco_pool_admit_acs", C.c_int, [_vp, C.c_int32, _vp, C.c_float, C.c_float, C.c_float,
-                                     C.c_int32, C.c_uint64, C.c_int32, C.c_double, C.c_float,
-                                     _i32p]),
-    ("aco_pool_admit_acs_coords", C.c_int, [_vp, C.c_int32, _vp, C.c_float, C.c_float,
-                                            C.c_float, C.c_int32, C.c_uint64, C.c_int32,
-                                            C.c_double, C.c_float, _i32p]),
+    ("aco_pool_set_acs", C.c_int, [_vp, C.c_int32, C.c_double, C.c_float]),
+    ("aco_pool_set_mmas", C.c_int, [_vp, C.c_int32, C.c_double, C.c_int32]),
     ("aco_pool_step", C.c_int, [_vp, _i32p]),
     ("aco_pool_finished", C.c_int, [_vp, _vp, C.c_int32, _i32p]),
     ("aco_pool_result", C.c_int, [_vp, C.c_int32, _vp, _vp]),
@@ -343,26 +339,36 @@ def aco_pool_admit(p, dist, alpha, beta, rho, m, seed, iterations):
     return slot.value
 
 
+def aco_pool_set_acs(p, slot: int, q0: float, xi: float) -> None:
+    _check(load().aco_pool_set_acs(p, slot, q0, xi), "aco_pool_set_acs")
+
+
+def aco_pool_set_mmas(p, slot: int, p_best: float, best_so_far: bool) -> None:
+    _check(load().aco_pool_set_mmas(p, slot, p_best, int(best_so_far)), "aco_pool_set_mmas")
+
+
 def aco_pool_admit_acs(p, dist, alpha, beta, rho, m, seed, iterations, q0, xi):
-    """Admit an Ant Colony System instance (distance matrix); returns the slot (raises AcoError)."""
-    d = np.ascontiguousarray(dist, dtype=np.int32)
-    slot = C.c_int32()
-    _check(load().aco_pool_admit_acs(p, d.shape[0], _ptr(d), alpha, beta, rho, m, seed,
-                                     iterations, q0, xi, C.byref(slot)), "aco_pool_admit_acs")
-    return slot.value
+    """aco_pool_admit then aco_pool_set_acs; returns the slot (raises AcoError, and releases
+    the slot if the switch is refused)."""
+    slot = aco_pool_admit(p, dist, alpha, beta, rho, m, seed, iterations)
+    try:
+        aco_pool_set_acs(p, slot, q0, xi)
+    except AcoError:
+        aco_pool_release(p, slot)
+        raise
+    return slot
 
 
-def aco_pool_admit_acs_coords(p, xy, alpha, beta, rho, m, seed, iterations, q0, xi):
-    """Admit an Ant Colony System instance given by integer coordinates; returns the slot or
-    None if busy."""
-    c = np.ascontiguousarray(xy, dtype=np.int32)
-    slot = C.c_int32()
-    rc = load().aco_pool_admit_acs_coords(p, c.shape[0], _ptr(c), alpha, beta, rho, m, seed,
-                                          iterations, q0, xi, C.byref(slot))
-    if rc == ACO_EBUSY:
-        return None
-    _check(rc, "aco_pool_admit_acs_coords")
-    return slot.value
+def aco_pool_admit_mmas(p, dist, alpha, beta, rho, m, seed, iterations, p_best, best_so_far):
+    """aco_pool_admit then aco_pool_set_mmas; returns the slot (raises AcoError, and releases
+    the slot if the switch is refused)."""
+    slot = aco_pool_admit(p, dist, alpha, beta, rho, m, seed, iterations)
+    try:
+        aco_pool_set_mmas(p, slot, p_best, best_so_far)
+    except AcoError:
+        aco_pool_release(p, slot)
+        raise
+    return slot
 
 
 def aco_pool_admit_coords(p, xy, alpha, beta, rho, m, seed, iterations):

@@ -119,6 +119,13 @@ unsigned long long acs_threshold_of(double q0) {
                     : 0ull;
 }
 
+// MAX-MIN Ant System f = tau_min / tau_max before the tau_min <= tau_max cap:
+// (1 - p^(1/n)) / ((n/2 - 1) p^(1/n)), in double.
+double mmas_f_of(int n, double p_best) {
+  const double root = std::pow(p_best, 1.0 / (double)n);
+  return (1.0 - root) / (((double)n / 2.0 - 1.0) * root);
+}
+
 int device_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 148;
@@ -591,10 +598,7 @@ int aco_set_mmas(aco_handle h, double p_best, int32_t best_so_far) {
   if (best_so_far != 0 && best_so_far != 1) return fail(ACO_EINVAL, "best_so_far must be 0 or 1");
   if (h->constructed || h->host_iteration != 0 || h->I.variant != kVariantAs)
     return fail(ACO_ESTATE, "the update rule is chosen once, before the first construction");
-  const int n = h->I.n;
-  // f = tau_min / tau_max before the tau_min <= tau_max cap, in double.
-  const double root = std::pow(p_best, 1.0 / (double)n);
-  h->I.mmas_f = (1.0 - root) / (((double)n / 2.0 - 1.0) * root);
+  h->I.mmas_f = mmas_f_of(h->I.n, p_best);
   h->I.mmas_best_so_far = best_so_far;
   h->I.variant = kVariantMmas;
   drop_graph(h);

@@ -29,7 +29,7 @@ namespace aco {
 static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
-  size_t dist, heta, tau, choice, tours, lens, nbr, q, delta, best, st, total;
+  size_t dist, heta, tau, choice, tours, lens, nbr, q, delta, best, dep_nb, st, total;
 };
 
 static Layout layout_of(int n, int m) {
@@ -53,6 +53,7 @@ static Layout layout_of(int n, int m) {
   L.q = take((size_t)m * 8);
   L.delta = take((size_t)m * 4);
   L.best = take(((size_t)n + 1) * 4);
+  L.dep_nb = take((size_t)n * 4);
   L.st = take(sizeof(IterState));
   L.total = off;
   return L;
@@ -92,7 +93,7 @@ struct PoolSlot {
   Instance I{};
   cudaEvent_t ready = nullptr;  // setup done on the side stream
   bool wait_ready = false;
-  bool acs = false;  // Ant Colony System slot (otherwise the Ant System)
+  bool started = false;  // taken part in a step (the update rule is then fixed)
 };
 
 struct aco_pool {
@@ -212,9 +213,11 @@ static int pool_rebuild(aco_pool* p) {
   });
   p->h_live = live;
   // Ant Colony System slots: one CTA per colony in one launch of their own
+  // (MAX-MIN Ant System slots construct and update with the Ant System ones:
+  // the best and row-update kernels follow each slot's rule)
   for (int s : live) {
     const PoolSlot& sl = p->slots[(size_t)s];
-    if (!sl.acs) continue;
+    if (sl.I.variant != kVariantAcs) continue;
     p->h_acs.push_back(s);
     p->acs_max_m = std::max(p->acs_max_m, sl.m);
     p->acs_max_n = std::max(p->acs_max_n, sl.n);
@@ -224,7 +227,7 @@ static int pool_rebuild(aco_pool* p) {
   std::map<std::tuple<int, int, int>, std::vector<int>> by_class;
   std::vector<std::tuple<int, int, int>> class_order;
   for (int s : live) {
-    if (p->slots[(size_t)s].acs) continue;
+    if (p->slots[(size_t)s].I.variant == kVariantAcs) continue;
     const ConstructTiling t = batched_construct_tiling(p->slots[(size_t)s].n);
     const auto key = std::make_tuple(t.G, t.H, t.C);
     if (!by_class.count(key)) class_order.push_back(key);
@@ -254,7 +257,7 @@ static int pool_rebuild(aco_pool* p) {
   }
   for (int s : live) {
     const PoolSlot& sl = p->slots[(size_t)s];
-    if (sl.acs) continue;
+    if (sl.I.variant == kVariantAcs) continue;
     p->max_ld = std::max(p->max_ld, sl.I.ld);
     for (int i = 0; i < sl.n; ++i) p->h_rows.push_back(make_int2(s, i));
   }
@@ -401,25 +404,12 @@ static int pool_enqueue_step(aco_pool* p) {
   return ACO_OK;
 }
 
-// Ant Colony System parameters of an admission (acs = false: the Ant System).
-struct AcsArgs {
-  bool acs = false;
-  double q0 = 0.0;
-  float xi = 0.0f;
-};
-
 static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const int32_t* xy,
                              float alpha, float beta, float rho, int32_t m, uint64_t seed,
-                             int32_t iterations, int32_t* slot, AcsArgs acs = AcsArgs{}) {
+                             int32_t iterations, int32_t* slot) {
   NvtxRange nvtx_range("aco_pool_admit");
   if (!p || !slot) return fail(ACO_EINVAL, "NULL argument");
   if (!p->unlimited && iterations < 1) return fail(ACO_EINVAL, "iterations must be >= 1");
-  if (acs.acs) {
-    if (!(acs.q0 >= 0.0 && acs.q0 <= 1.0)) return fail(ACO_EINVAL, "q0 must lie in [0, 1]");
-    if (!(acs.xi >= 0.0f && acs.xi <= 1.0f)) return fail(ACO_EINVAL, "xi must lie in [0, 1]");
-    if (m < 1 || m > kAcsMaxAnts)
-      return fail(ACO_EINVAL, "the Ant Colony System runs 1 to %d ants (m=%d)", kAcsMaxAnts, m);
-  }
   int rc = dist ? validate_instance(n, dist, alpha, beta, rho, m)
                 : validate_coords_public(n, xy);
   if (rc) return rc;
@@ -444,7 +434,6 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
   sl = PoolSlot{};
   sl.ready = ev;
   sl.used = true;
-  sl.acs = acs.acs;
   sl.n = n;
   sl.m = m;
   sl.iters_left = p->unlimited ? -1 : iterations;
@@ -460,11 +449,6 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
   I.beta = beta;
   I.rho = rho;
   I.seed = seed;
-  if (acs.acs) {
-    I.variant = kVariantAcs;
-    I.acs_threshold = acs_threshold_of(acs.q0);
-    I.acs_xi = acs.xi;
-  }
   char* b = (char*)p->arena + off;
   I.dist = (const int32_t*)(b + L.dist);
   I.heta = (float*)(b + L.heta);
@@ -477,6 +461,7 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
   I.delta = (float*)(b + L.delta);
   I.acc = nullptr;
   I.best_tour = (int32_t*)(b + L.best);
+  I.dep_nb = (uint32_t*)(b + L.dep_nb);
   I.st = (IterState*)(b + L.st);
   cudaError_t e = cudaSuccess;
   // Sources of the asynchronous copies below must outlive this call: the
@@ -506,7 +491,6 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
                              p->side)) != cudaSuccess)
       break;
     if ((e = launch_setup(I, p->sms, p->side)) != cudaSuccess) break;
-    if (acs.acs && (e = launch_acs_init(I, p->sms, p->side)) != cudaSuccess) break;
     e = cudaEventRecord(sl.ready, p->side);
   } while (0);
   if (e != cudaSuccess) {
@@ -529,6 +513,35 @@ static int pool_check_status(aco_pool* p, int slot) {
   if (e != cudaSuccess) return cuda_fail(e, "pool synchronize");
   if (status & kStatusTimeout) return fail(ACO_ETIMEOUT, "a device-side wait gave up");
   if (status) return fail(ACO_ECUDA, "device status 0x%x in slot %d", status, slot);
+  return ACO_OK;
+}
+
+// Switch a slot admitted but not yet stepped to another update rule: the
+// descriptor is uploaded again and the rule's start trails written, both on
+// the side stream after the admission's setup.
+template <class Apply>
+static int pool_switch_rule(aco_pool* p, int32_t slot, Apply apply) {
+  PoolSlot& sl = p->slots[(size_t)slot];
+  apply(sl.I);
+  Instance& I = sl.I;
+  cudaError_t e = cudaMemcpyAsync(p->d_inst + slot, &I, sizeof I, cudaMemcpyHostToDevice, p->side);
+  if (e == cudaSuccess)
+    e = I.variant == kVariantAcs ? launch_acs_init(I, p->sms, p->side)
+                                 : launch_mmas_init(I, p->sms, p->side);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.ready, p->side);
+  if (e != cudaSuccess) return cuda_fail(e, "pool rule switch");
+  sl.wait_ready = true;
+  p->dirty = true;
+  return ACO_OK;
+}
+
+static int pool_rule_slot_check(aco_pool* p, int32_t slot) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
+    return fail(ACO_EINVAL, "slot %d is not live", slot);
+  const PoolSlot& sl = p->slots[(size_t)slot];
+  if (sl.started || sl.I.variant != kVariantAs)
+    return fail(ACO_ESTATE, "the update rule is chosen once, before the slot's first step");
   return ACO_OK;
 }
 
@@ -616,27 +629,31 @@ int aco_pool_admit_coords(aco_pool_handle p, int32_t n, const int32_t* xy, float
   return pool_admit_common(p, n, nullptr, xy, alpha, beta, rho, m, seed, iterations, slot);
 }
 
-int aco_pool_admit_acs(aco_pool_handle p, int32_t n, const int32_t* dist, float alpha,
-                       float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
-                       double q0, float xi, int32_t* slot) {
-  if (!dist) return fail(ACO_EINVAL, "dist is NULL");
-  AcsArgs acs;
-  acs.acs = true;
-  acs.q0 = q0;
-  acs.xi = xi;
-  return pool_admit_common(p, n, dist, nullptr, alpha, beta, rho, m, seed, iterations, slot,
-                           acs);
+int aco_pool_set_acs(aco_pool_handle p, int32_t slot, double q0, float xi) {
+  int rc = pool_rule_slot_check(p, slot);
+  if (rc) return rc;
+  if (!(q0 >= 0.0 && q0 <= 1.0)) return fail(ACO_EINVAL, "q0 must lie in [0, 1]");
+  if (!(xi >= 0.0f && xi <= 1.0f)) return fail(ACO_EINVAL, "xi must lie in [0, 1]");
+  const int m = p->slots[(size_t)slot].m;
+  if (m > kAcsMaxAnts)
+    return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants (m=%d)", kAcsMaxAnts, m);
+  return pool_switch_rule(p, slot, [&](Instance& I) {
+    I.variant = kVariantAcs;
+    I.acs_threshold = acs_threshold_of(q0);
+    I.acs_xi = xi;
+  });
 }
 
-int aco_pool_admit_acs_coords(aco_pool_handle p, int32_t n, const int32_t* xy, float alpha,
-                              float beta, float rho, int32_t m, uint64_t seed, int32_t iterations,
-                              double q0, float xi, int32_t* slot) {
-  if (!xy) return fail(ACO_EINVAL, "xy is NULL");
-  AcsArgs acs;
-  acs.acs = true;
-  acs.q0 = q0;
-  acs.xi = xi;
-  return pool_admit_common(p, n, nullptr, xy, alpha, beta, rho, m, seed, iterations, slot, acs);
+int aco_pool_set_mmas(aco_pool_handle p, int32_t slot, double p_best, int32_t best_so_far) {
+  int rc = pool_rule_slot_check(p, slot);
+  if (rc) return rc;
+  if (!(p_best > 0.0 && p_best < 1.0)) return fail(ACO_EINVAL, "p_best must lie in (0, 1)");
+  if (best_so_far != 0 && best_so_far != 1) return fail(ACO_EINVAL, "best_so_far must be 0 or 1");
+  return pool_switch_rule(p, slot, [&](Instance& I) {
+    I.variant = kVariantMmas;
+    I.mmas_f = mmas_f_of(I.n, p_best);
+    I.mmas_best_so_far = best_so_far;
+  });
 }
 
 int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
@@ -669,6 +686,7 @@ int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
     if ((e = cudaGraphLaunch(p->exec, p->stream)) != cudaSuccess) return cuda_fail(e, "pool launch");
     for (int s : p->h_live) {
       PoolSlot& sl = p->slots[(size_t)s];
+      sl.started = true;
       if (sl.iters_left > 0 && --sl.iters_left == 0) {
         sl.live = false;
         sl.finished = true;
@@ -779,7 +797,7 @@ int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t* warps_per_ant,
   if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
     return fail(ACO_EINVAL, "slot %d is not live", slot);
   if (p->dirty) return fail(ACO_ESTATE, "no step has run since the live set changed");
-  if (p->slots[(size_t)slot].acs)
+  if (p->slots[(size_t)slot].I.variant == kVariantAcs)
     return fail(ACO_EINVAL, "slot %d runs the Ant Colony System (one CTA per colony)", slot);
   const int n = p->slots[(size_t)slot].n;
   for (const auto& c : p->classes)

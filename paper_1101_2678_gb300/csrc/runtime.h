@@ -25,6 +25,8 @@ int cuda_fail(cudaError_t e, const char* what);
 int device_sms();
 // Ant Colony System exploitation threshold floor(q0 2^32), q0 in [0, 1].
 unsigned long long acs_threshold_of(double q0);
+// MAX-MIN Ant System trail-limit ratio f for n cities and p_best.
+double mmas_f_of(int n, double p_best);
 // Argument checks shared by aco_create and the batch/pool admission.
 int validate_instance(int32_t n, const int32_t* dist, float alpha, float beta, float rho,
                       int32_t m);

@@ -284,12 +284,8 @@ __global__ void mmas_update_kernel(Instance I, int bump_iteration) {
     float cv[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int j = j0 + c;
-      float t = __fmul_rn(keep, tv[c]);
-      if (j == pred || j == succ) t = __fadd_rn(t, dtau);
-      if (j != i && j < n) t = fminf(fmaxf(t, lo), hi);
-      tv[c] = t;
-      cv[c] = choice_of(t, hv[c], alpha);
+      tv[c] = mmas_cell(tv[c], i, j0 + c, n, pred, succ, keep, dtau, lo, hi);
+      cv[c] = choice_of(tv[c], hv[c], alpha);
     }
     reinterpret_cast<float4*>(I.tau)[e] = make_float4(tv[0], tv[1], tv[2], tv[3]);
     reinterpret_cast<float4*>(I.choice)[e] = make_float4(cv[0], cv[1], cv[2], cv[3]);
@@ -367,7 +363,10 @@ __global__ void update_rows_kernel(const Instance* __restrict__ insts, const int
   const int2 it = rows[idx];
   const Instance& I = insts[it.x];
   if (it.y == 0 && lane == 0) I.st->iteration += 1;
-  gather_row(I, it.y, acc_rows + (size_t)wi * max_ld, lane);
+  if (I.variant == kVariantMmas)
+    mmas_row(I, it.y, lane);
+  else
+    gather_row(I, it.y, acc_rows + (size_t)wi * max_ld, lane);
 }
 
 // Rounded Euclidean distances (TSPLIB EUC_2D): d = floor(sqrt(dx^2 + dy^2) +

@@ -23,6 +23,17 @@ __device__ __forceinline__ void mmas_limits(const Instance& I, long long c_gb, f
   *tau_min = (float)tmin;
 }
 
+// One MAX-MIN Ant System cell (i, j): evaporation, dtau on the depositing
+// tour's edges at row i (its predecessor and successor of city i), the clamp
+// into [lo, hi] off the diagonal and the padding.
+__device__ __forceinline__ float mmas_cell(float tau, int i, int j, int n, int pred, int succ,
+                                           float keep, float dtau, float lo, float hi) {
+  float t = __fmul_rn(keep, tau);
+  if (j == pred || j == succ) t = __fadd_rn(t, dtau);
+  if (j != i && j < n) t = fminf(fmaxf(t, lo), hi);
+  return t;
+}
+
 __device__ __forceinline__ void best_body(const Instance& I) {
   __shared__ long long red_l[32];
   __shared__ int red_k[32];
@@ -164,6 +175,38 @@ __device__ __forceinline__ void gather_row(const Instance& I, const int i,
     o.y = apply_deposit(t4.y, acc[j + 1], keep, inv);
     o.z = apply_deposit(t4.z, acc[j + 2], keep, inv);
     o.w = apply_deposit(t4.w, acc[j + 3], keep, inv);
+    c.x = choice_of(o.x, h4.x, alpha);
+    c.y = choice_of(o.y, h4.y, alpha);
+    c.z = choice_of(o.z, h4.z, alpha);
+    c.w = choice_of(o.w, h4.w, alpha);
+    *reinterpret_cast<float4*>(tau + j) = o;
+    *reinterpret_cast<float4*>(ch + j) = c;
+  }
+}
+
+}  // namespace aco
+
+namespace aco {
+
+// Row i of the MAX-MIN Ant System update by one warp (the pool's row list).
+__device__ __forceinline__ void mmas_row(const Instance& I, const int i, const int lane) {
+  const int n = I.n, ld = I.ld;
+  const float keep = __fsub_rn(1.0f, I.rho);
+  const float dtau = I.st->mmas_dtau, lo = I.st->tau_min, hi = I.st->tau_max;
+  const float alpha = I.alpha;
+  const uint32_t nb = I.dep_nb[i];
+  const int pred = (int)(nb >> 16), succ = (int)(nb & 0xffffu);
+  float* tau = I.tau + (size_t)i * ld;
+  const float* heta = I.heta + (size_t)i * ld;
+  float* ch = I.choice + (size_t)i * ld;
+  for (int j = lane * 4; j < ld; j += 128) {
+    const float4 t4 = *reinterpret_cast<const float4*>(tau + j);
+    const float4 h4 = *reinterpret_cast<const float4*>(heta + j);
+    float4 o, c;
+    o.x = mmas_cell(t4.x, i, j + 0, n, pred, succ, keep, dtau, lo, hi);
+    o.y = mmas_cell(t4.y, i, j + 1, n, pred, succ, keep, dtau, lo, hi);
+    o.z = mmas_cell(t4.z, i, j + 2, n, pred, succ, keep, dtau, lo, hi);
+    o.w = mmas_cell(t4.w, i, j + 3, n, pred, succ, keep, dtau, lo, hi);
     c.x = choice_of(o.x, h4.x, alpha);
     c.y = choice_of(o.y, h4.y, alpha);
     c.z = choice_of(o.z, h4.z, alpha);

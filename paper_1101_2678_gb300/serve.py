@@ -4,8 +4,9 @@ Requests (TSP instances given by integer coordinates) arrive over time.  The
 server admits them in arrival order whenever the pool has a free slot and
 enough of its HBM budget, keeps every admitted instance's state resident on
 the device, and runs one iteration for all live instances per step (Ant
-System and Ant Colony System requests side by side), so work from requests
-that arrived at different times overlaps on the GPU.  A request finishes after its own number of iterations; its latency is
+System, MAX-MIN Ant System and Ant Colony System requests side by side), so
+work from requests that arrived at different times overlaps on the GPU.  A
+request finishes after its own number of iterations; its latency is
 completion time minus arrival time (queueing included).
 
 All compute happens in the library's kernels (aco_pool_step); this module only
@@ -32,10 +33,13 @@ class Request:
     beta: float = 2.0
     rho: float = 0.5
     # "as": the Ant System; "acs": the Ant Colony System with q0 and xi
-    # (m <= 32; rho is then its global-update rate)
+    # (m <= 32); "mmas": the MAX-MIN Ant System with p_best and best_so_far
+    # (rho is then the rule's own rate)
     variant: str = "as"
     q0: float = 0.9
     xi: float = 0.1
+    p_best: float = 0.05
+    best_so_far: bool = False
 
     @property
     def n(self) -> int:
@@ -124,14 +128,14 @@ class Server:
                 w = step_work(r)
                 if live and live_work + w > self.max_step_work:
                     break
-                if r.variant == "acs":
-                    slot = aco.aco_pool_admit_acs_coords(pool, r.coords, r.alpha, r.beta, r.rho,
-                                                         r.m, r.seed, r.iterations, r.q0, r.xi)
-                else:
-                    slot = aco.aco_pool_admit_coords(pool, r.coords, r.alpha, r.beta, r.rho,
-                                                     r.m, r.seed, r.iterations)
+                slot = aco.aco_pool_admit_coords(pool, r.coords, r.alpha, r.beta, r.rho, r.m,
+                                                 r.seed, r.iterations)
                 if slot is None:
                     break
+                if r.variant == "acs":
+                    aco.aco_pool_set_acs(pool, slot, r.q0, r.xi)
+                elif r.variant == "mmas":
+                    aco.aco_pool_set_mmas(pool, slot, r.p_best, r.best_so_far)
                 live[slot] = (queue.popleft(), time.perf_counter() - t0)
                 live_work += w
             if not live:

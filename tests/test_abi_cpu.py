@@ -100,9 +100,8 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.aco_set_acs(None, 0.9, 0.1) == aco.ACO_EINVAL
     assert lib.aco_pool_autotune(None) == aco.ACO_EINVAL
     assert lib.aco_pool_set_tuning(None, None, 0) == aco.ACO_EINVAL
-    d = np.zeros((3, 3), np.int32)
-    assert lib.aco_pool_admit_acs(None, 3, d.ctypes.data, 1.0, 2.0, 0.5, 3, 1, 1, 0.9, 0.1,
-                                  None) == aco.ACO_EINVAL
+    assert lib.aco_pool_set_acs(None, 0, 0.9, 0.1) == aco.ACO_EINVAL
+    assert lib.aco_pool_set_mmas(None, 0, 0.05, 0) == aco.ACO_EINVAL
 
 
 def test_selftest_rejects_bad_arguments_before_touching_the_gpu(lib):

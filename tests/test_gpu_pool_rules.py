@@ -1,11 +1,13 @@
-"""Many Ant Colony System colonies per launch (aco_pool_admit_acs).
+"""The Ant Colony System and the MAX-MIN Ant System in a pool
+(aco_pool_set_acs / aco_pool_set_mmas).
 
 Every live Ant Colony System slot of a pool runs in one launch, one CTA per
-colony, beside the Ant System classes.  Each colony keeps its own seed and
-iteration counter, and its lockstep steps and local updates stay inside its
-own CTA, so a colony's tours, pheromone and best tour must equal the CPU
-oracle's run (reading R14) bit for bit in any mix of sizes, ant counts and
-admission times.
+colony, beside the Ant System classes; MAX-MIN slots construct with the Ant
+System slots and take their own update in the row-update launch.  Each slot
+keeps its own seed and iteration counter, and nothing of one slot's step
+reads another slot's state, so a slot's tours, pheromone and best tour must
+equal the CPU oracle's run (readings R13 and R14) bit for bit in any mix of
+sizes, ant counts, rules and admission times.
 """
 import numpy as np
 import pytest
@@ -133,27 +135,117 @@ def test_acs_admission_errors(aco):
                 aco.aco_pool_admit_acs(p, x.dist, **args)
             assert e.value.code == aco.ACO_EINVAL
         s = aco.aco_pool_admit_acs(p, x.dist, 1.0, 2.0, 0.1, 10, 1, 2, 0.9, 0.1)
+        # the rule is chosen once, before the slot's first step
+        for call in (lambda: aco.aco_pool_set_acs(p, s, 0.9, 0.1),
+                     lambda: aco.aco_pool_set_mmas(p, s, 0.05, False)):
+            with pytest.raises(aco.AcoError) as e:
+                call()
+            assert e.value.code == aco.ACO_ESTATE
+        s2 = aco.aco_pool_admit(p, x.dist, 1.0, 2.0, 0.1, 10, 2, 2)
+        for kw in [dict(p_best=0.0), dict(p_best=1.0), dict(best_so_far=2)]:
+            args = dict(p_best=0.05, best_so_far=0)
+            args.update(kw)
+            with pytest.raises(aco.AcoError) as e:
+                aco.aco_pool_set_mmas(p, s2, **args)
+            assert e.value.code == aco.ACO_EINVAL
         aco.aco_pool_step(p)
         with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_set_mmas(p, s2, 0.05, False)
+        assert e.value.code == aco.ACO_ESTATE
+        with pytest.raises(aco.AcoError) as e:
             aco.aco_pool_tiling(p, s)
+        assert e.value.code == aco.ACO_EINVAL
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_set_acs(p, 7, 0.9, 0.1)
         assert e.value.code == aco.ACO_EINVAL
     finally:
         aco.aco_pool_destroy(p)
 
 
-def test_server_mixes_ant_system_and_colony_system_requests(aco, orc):
-    # Requests of both update rules through serve.Server, by coordinates, in a
-    # step-work budget small enough to stagger admission; each Ant Colony
-    # System result equals the oracle's run, each Ant System result its run
-    # alone.
+def check_mmas_slot(aco, orc, p, slot, dist, m, seed, iters, rho, p_best, bsf):
+    n = dist.shape[0]
+    ref = orc.run_mmas(dist, m, iters, seed, rho=rho, p_best=p_best, best_so_far=bsf)
+    tour, length = aco.aco_pool_result(p, slot, n)
+    assert length == ref["best_len"] and np.array_equal(tour, ref["best_tour"]), slot
+    assert np.array_equal(aco.aco_pool_pheromone(p, slot, n), ref["tau32"]), slot
+
+
+def test_all_three_rules_in_one_pool(aco, orc):
+    # MAX-MIN slots (both deposit choices) share construction classes with
+    # Ant System slots of similar n; Ant Colony System colonies run beside them
+    mm = [(48, 48, 31, 6, 0.02, 0.05, False), (300, 100, 32, 3, 0.1, 0.05, True),
+          (97, 97, 33, 5, 0.2, 0.3, False), (3, 3, 34, 4, 0.02, 0.05, True)]
+    ac = [(60, 10, 41, 5, 0.1, 0.9, 0.1), (250, 32, 42, 3, 0.1, 0.5, 0.2)]
+    asys = [(290, 120, 51, 4), (50, 50, 52, 6)]
+    inst = {}
+    for n, *_r in mm + ac + asys:
+        inst[n] = I.uniform_instance(n, 1000, seed=3000 + n)
+    need = sum(aco.aco_pool_bytes_needed(c[0], c[1]) for c in mm + ac + asys)
+    p = aco.aco_pool_create(16, need + (1 << 20))
+    try:
+        slot = {}
+        for i, (n, m, seed, iters, rho, pb, bsf) in enumerate(mm):
+            slot["mm", i] = aco.aco_pool_admit_mmas(p, inst[n].dist, 1.0, 2.0, rho, m, seed,
+                                                    iters, pb, bsf)
+            if i == 1:
+                for j, (n2, m2, seed2, iters2) in enumerate(asys):
+                    slot["as", j] = aco.aco_pool_admit(p, inst[n2].dist, 1.0, 2.0, 0.5, m2,
+                                                       seed2, iters2)
+                aco.aco_pool_step(p)
+        for i, (n, m, seed, iters, rho, q0, xi) in enumerate(ac):
+            slot["ac", i] = aco.aco_pool_admit_acs(p, inst[n].dist, 1.0, 2.0, rho, m, seed, iters,
+                                                   q0, xi)
+        while aco.aco_pool_step(p) > 0:
+            pass
+        aco.aco_pool_synchronize(p)
+        for i, (n, m, seed, iters, rho, pb, bsf) in enumerate(mm):
+            check_mmas_slot(aco, orc, p, slot["mm", i], inst[n].dist, m, seed, iters, rho, pb, bsf)
+        for i, (n, m, seed, iters, rho, q0, xi) in enumerate(ac):
+            check_acs_slot(aco, orc, p, slot["ac", i], inst[n].dist, m, seed, iters, rho, q0, xi)
+        for j, (n, m, seed, iters) in enumerate(asys):
+            ref = orc.run(inst[n].dist, m, iters, seed)
+            assert np.array_equal(aco.aco_pool_pheromone(p, slot["as", j], n), ref["tau32"])
+            assert aco.aco_pool_result(p, slot["as", j], n)[1] == ref["best_len"]
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+def test_pool_mmas_equals_single_handle_at_full_size(aco):
+    w = I.workload_n1002()
+    d = w["inst"].dist
+    with aco.Colony(d, 256, seed=w["seed"], rho=0.02) as c:
+        aco.aco_set_mmas(c.h, 0.05, False)
+        aco.aco_iterate(c.h, 3)
+        tau_h, (tour_h, len_h) = aco.aco_get_pheromone(c.h, 1002), aco.aco_best_tour(c.h, 1002)
+    p = aco.aco_pool_create(2, 2 * aco.aco_pool_bytes_needed(1002, 256) + (1 << 20))
+    try:
+        s = aco.aco_pool_admit_mmas(p, d, 1.0, 2.0, 0.02, 256, w["seed"], 3, 0.05, False)
+        while aco.aco_pool_step(p) > 0:
+            pass
+        tour_p, len_p = aco.aco_pool_result(p, s, 1002)
+        assert len_p == len_h and np.array_equal(tour_p, tour_h)
+        assert np.array_equal(aco.aco_pool_pheromone(p, s, 1002), tau_h)
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+def test_server_mixes_all_three_rules(aco, orc):
+    # Requests of the three update rules through serve.Server, by
+    # coordinates, in a step-work budget small enough to stagger admission;
+    # each Ant Colony System and MAX-MIN result equals the oracle's run, each
+    # Ant System result its run alone.
     from paper_1101_2678_gb300 import serve
     reqs = []
-    for i, (n, variant) in enumerate([(90, "acs"), (300, "as"), (48, "acs"), (200, "acs"),
-                                      (150, "as"), (33, "acs")]):
+    for i, (n, variant) in enumerate([(90, "acs"), (300, "as"), (48, "acs"), (200, "mmas"),
+                                      (150, "as"), (33, "acs"), (120, "mmas")]):
         inst = I.clustered_instance(n, seed=90 + i, clusters=6, side=4000)
         if variant == "acs":
             reqs.append(serve.Request(inst.coords, m=10 + i, iterations=3 + i, seed=850 + i,
                                       rho=0.1, variant="acs", q0=0.9, xi=0.1))
+        elif variant == "mmas":
+            reqs.append(serve.Request(inst.coords, m=min(n, 128), iterations=3 + i,
+                                      seed=850 + i, rho=0.02, variant="mmas", p_best=0.05,
+                                      best_so_far=i % 2 == 1))
         else:
             reqs.append(serve.Request(inst.coords, m=min(n, 128), iterations=3 + i,
                                       seed=850 + i))
@@ -164,8 +256,11 @@ def test_server_mixes_ant_system_and_colony_system_requests(aco, orc):
     for o in outs:
         r = reqs[o.index]
         d = I.distance_matrix(r.coords)
-        if r.variant == "acs":
-            ref = orc.run_acs(d, r.m, r.iterations, r.seed, rho=r.rho, q0=r.q0, xi=r.xi)
+        if r.variant in ("acs", "mmas"):
+            ref = (orc.run_acs(d, r.m, r.iterations, r.seed, rho=r.rho, q0=r.q0, xi=r.xi)
+                   if r.variant == "acs" else
+                   orc.run_mmas(d, r.m, r.iterations, r.seed, rho=r.rho, p_best=r.p_best,
+                                best_so_far=r.best_so_far))
             assert o.best_len == ref["best_len"], o.index
             assert np.array_equal(o.best_tour, ref["best_tour"]), o.index
         else:
