@@ -328,27 +328,31 @@ def run_ours(args, w, rank, world, local):
            "sort": aco.ACO_DEPOSIT_SORT}[args.deposit]
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    def configure(h):
+        """The run's options and update rule (the timed handle and the e2e solve)."""
+        aco.aco_set_option(h, aco.ACO_OPT_DEPOSIT, dep)
+        if args.warps_per_ant:
+            aco.aco_set_option(h, aco.ACO_OPT_WARPS_PER_ANT, args.warps_per_ant)
+        if args.selection == "data-parallel":
+            aco.aco_set_option(h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
+        if args.nn:
+            aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, args.nn)
+        if args.staging >= 0:
+            aco.aco_set_option(h, aco.ACO_OPT_STAGING, args.staging)
+        if args.variant == "mmas":
+            aco.aco_set_mmas(h, 0.05, False)
+        elif args.variant == "acs":
+            aco.aco_set_acs(h, 0.9, 0.1)
+        if args.lanes_per_ant:
+            aco.aco_set_option(h, aco.ACO_OPT_LANES_PER_ANT, args.lanes_per_ant)
+        if args.ants_per_cta:
+            aco.aco_set_option(h, aco.ACO_OPT_ANTS_PER_CTA, args.ants_per_cta)
+
     col = aco.Colony(d, m, seed=w["seed"] + rank, alpha=w["alpha"], beta=w["beta"], rho=w["rho"])
     h = col.h
     aco.aco_set_option(h, aco.ACO_OPT_STREAM, stream.cuda_stream)
-    aco.aco_set_option(h, aco.ACO_OPT_DEPOSIT, dep)
     aco.aco_set_option(h, aco.ACO_OPT_PROFILE, 1)
-    if args.warps_per_ant:
-        aco.aco_set_option(h, aco.ACO_OPT_WARPS_PER_ANT, args.warps_per_ant)
-    if args.selection == "data-parallel":
-        aco.aco_set_option(h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
-    if args.nn:
-        aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, args.nn)
-    if args.staging >= 0:
-        aco.aco_set_option(h, aco.ACO_OPT_STAGING, args.staging)
-    if args.variant == "mmas":
-        aco.aco_set_mmas(h, 0.05, False)
-    elif args.variant == "acs":
-        aco.aco_set_acs(h, 0.9, 0.1)
-    if args.lanes_per_ant:
-        aco.aco_set_option(h, aco.ACO_OPT_LANES_PER_ANT, args.lanes_per_ant)
-    if args.ants_per_cta:
-        aco.aco_set_option(h, aco.ACO_OPT_ANTS_PER_CTA, args.ants_per_cta)
+    configure(h)
     tiling = (aco.aco_get_option(h, aco.ACO_OPT_WARPS_PER_ANT),
               aco.aco_get_option(h, aco.ACO_OPT_ANTS_PER_CTA),
               aco.aco_get_option(h, aco.ACO_OPT_LANES_PER_ANT))
@@ -393,7 +397,7 @@ def run_ours(args, w, rank, world, local):
     # e2e: a whole solve through the public API from host memory.
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_solve(aco, w, rank)
+        e2e = e2e_solve(aco, w, rank, m, configure)
 
     if rank != 0:
         return
@@ -505,16 +509,18 @@ def construct_roofline(n, m, con_ms, peaks, peak_kind, kernel="construct_kernel"
             "avg_launch_ms": con_ms}
 
 
-def e2e_solve(aco, w, rank):
-    """create (uploads dist) + iterate + best tour to the host, wall-clock timed."""
+def e2e_solve(aco, w, rank, m, configure):
+    """create (uploads dist) + the run's options + iterate + best tour to the host,
+    wall-clock timed."""
     import numpy as np
     import torch
     d = np.ascontiguousarray(w["inst"].dist, dtype=np.int32)
-    n, m, iters = d.shape[0], w["m"], w["iterations"]
+    n, iters = d.shape[0], w["iterations"]
     pinned = torch.from_numpy(d).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = aco.aco_create(pinned, w["alpha"], w["beta"], w["rho"], m, w["seed"] + rank)
+    configure(h)
     aco.aco_iterate(h, iters)
     tour, length = aco.aco_best_tour(h, n)
     t1 = time.perf_counter()

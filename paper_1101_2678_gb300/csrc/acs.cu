@@ -175,6 +175,16 @@ __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* 
         if (lane == 0) atomicOr(&I.st->status, kStatusBadTour);
         next = start;
       }
+      // The next step reads row `next`: start bringing it into L1 now (one
+      // 128-byte line per lane and round), while this ant waits at the
+      // barrier for the others.  Only this CTA writes the colony's matrices,
+      // through the same L1, so the lines the local updates change stay
+      // current; the prefetch is a hint and changes no result.
+      if (s + 1 < n) {
+        const float* nrow = I.choice + (size_t)next * ld;
+        for (int f = 32 * lane; f < n; f += 32 * 32)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(nrow + f));
+      }
     }
     // lockstep: every ant has chosen from the same state; then the local
     // updates of this step, one writer per distinct edge applying it once
