@@ -21,15 +21,6 @@
 
 namespace aco {
 
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(FULL, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
-}
-
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -87,10 +78,14 @@ __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* 
       // is a multiple of 4, so the load stays inside the row); the three
       // passes read the same lines, the later two from L1.  Loads after the
       // CTA barrier see the local updates of the previous step.
-      // Pass 1: the largest unvisited weight, ties to the lower index: max of
-      // (bits(w) << 32 | ~j); the bits of non-negative floats order like
-      // their values.
-      unsigned long long key = 0ull;
+      // Pass 1: the largest unvisited weight, ties to the lower index.  The
+      // bits of non-negative floats order like their values; an unvisited
+      // city's key is bits(w) + 1 and a visited one's 0, so a zero weight
+      // still beats every visited city.  Each lane visits its cities in
+      // ascending order and keeps the first of its largest keys; the warp
+      // reduction breaks ties by index.
+      uint32_t bkey = 0u;
+      int bj = 0;
 #pragma unroll 4
       for (int j0 = 4 * lane; j0 < n; j0 += 128) {
         const uint4 w4 = *reinterpret_cast<const uint4*>(row + j0);
@@ -98,14 +93,24 @@ __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* 
         const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const unsigned long long kk =
-              ((unsigned long long)wv[e] << 32) | (0xffffffffu - (uint32_t)(j0 + e));
-          if (((fr >> e) & 1u) && j0 + e < n && kk > key) key = kk;
+          const uint32_t kk = ((fr >> e) & 1u) && j0 + e < n ? wv[e] + 1u : 0u;
+          if (kk > bkey) {
+            bkey = kk;
+            bj = j0 + e;
+          }
         }
       }
-      key = warp_max_u64(key);
-      const uint32_t mbits = (uint32_t)(key >> 32);
-      next = (int)(0xffffffffu - (uint32_t)key);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t ok = __shfl_xor_sync(FULL, bkey, o);
+        const int oj = __shfl_xor_sync(FULL, bj, o);
+        if (ok > bkey || (ok == bkey && oj < bj)) {
+          bkey = ok;
+          bj = oj;
+        }
+      }
+      const uint32_t mbits = bkey - 1u;  // bkey >= 1: a city is unvisited
+      next = bj;
       const bool exploit = (unsigned long long)x.x2 < I.acs_threshold;
       if (!exploit && mbits != 0u) {
         // Eq. 1 by the integer roulette: q_j = floor(w_j 2^(45 - ilogb M)),
