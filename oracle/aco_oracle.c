@@ -67,6 +67,21 @@
  *     of list(i) by the integer roulette of R2 in list order; if every entry
  *     is visited it moves to the unvisited city with the largest weight,
  *     ties to the lower index.
+ *  R15 (optional selection rule) the exponential race, a per-candidate
+ *     random rule that samples Eq. 1: every unvisited city j draws
+ *     v_j = floor(x / 2^8) + 1 in [1, 2^24] (x as in R8), E_j = -ln(v_j 2^-24)
+ *     is an exponential variate of rate 1, and the ant moves to the smallest
+ *     key E_j / w_j (ties to the lower index), which is city j with
+ *     probability w_j / sum w (the minimum of independent exponentials of
+ *     rates w_j).  Zero weights get the key +inf (so does a key that
+ *     overflows); if every key is +inf the lowest unvisited city is taken.  E_j is computed in IEEE
+ *     single precision by the range-reduced inverse-hyperbolic-tangent
+ *     series of the logarithm: v = 2^e f with f in [1, 2), halved (e + 1)
+ *     when f > sqrt 2; s = (f - 1) / (f + 1); ln f = 2 s (1 + z/3 + z^2/5 +
+ *     z^3/7 + z^4/9), z = s^2, by Horner from the z^4 term, every operation
+ *     rounded on its own (no fused multiply-add); E = (24 - e) ln 2 - ln f;
+ *     the key is fl(E / w).  The constants are the floats nearest sqrt 2,
+ *     ln 2, 1/3, 1/5, 1/7 and 1/9.
  *
  *  R13 (optional variant) the MAX-MIN Ant System, which the paper cites as an
  *     earlier GPU target (Section II-B) and which stands for the "other ACO
@@ -250,6 +265,56 @@ int orc_iroulette(int n, const float *w, const uint8_t *visited, uint64_t seed, 
 }
 
 /* ------------------------------------------------------------------------- */
+/* The exponential race (reading R15).                                        */
+/* ------------------------------------------------------------------------- */
+/* E = -ln(v 2^-24) for v in [1, 2^24], in single precision (R15). */
+float orc_race_exponential(uint32_t v)
+{
+    int e = 0;
+    while (e < 31 && (v >> (e + 1)) != 0u) ++e; /* floor(log2 v) */
+    float f = ldexpf((float)v, -e);             /* exact: v < 2^25, f in [1, 2) */
+    if (f > 0x1.6a09e6p+0f) {                   /* sqrt 2 */
+        f = f * 0.5f;
+        e += 1;
+    }
+    float s = (f - 1.0f) / (f + 1.0f);
+    float z = s * s;
+    float p = 0x1.c71c72p-4f;                   /* 1/9 */
+    p = p * z + 0x1.24924ap-3f;                 /* 1/7 */
+    p = p * z + 0x1.99999ap-3f;                 /* 1/5 */
+    p = p * z + 0x1.555556p-2f;                 /* 1/3 */
+    p = p * z + 1.0f;
+    float ln_f = (s + s) * p;
+    return (float)(24 - e) * 0x1.62e430p-1f - ln_f; /* ln 2 */
+}
+
+void orc_race_exponentials(int count, const uint32_t *v, float *out)
+{
+    for (int i = 0; i < count; ++i) out[i] = orc_race_exponential(v[i]);
+}
+
+int orc_race(int n, const float *w, const uint8_t *visited, uint64_t seed, uint32_t step,
+             uint32_t ant, uint32_t iteration)
+{
+    int best = -1;
+    float best_key = 0.0f;
+    for (int j = 0; j < n; ++j) {
+        if (visited[j]) continue;
+        uint32_t ctr[4] = {step, ant, iteration, 1u + (uint32_t)(j / 4)};
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t x[4];
+        orc_philox4x32_10(ctr, key, x);
+        uint32_t vj = (x[j % 4] >> 8) + 1u;
+        float k = w[j] > 0.0f ? orc_race_exponential(vj) / w[j] : INFINITY;
+        if (best < 0 || k < best_key) { /* strict: the lower index keeps a tie */
+            best = j;
+            best_key = k;
+        }
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Nearest-neighbour lists and the list-restricted step (reading R9).        */
 /* ------------------------------------------------------------------------- */
 void orc_nn_lists(int n, const int32_t *d, int nn, int32_t *lists)
@@ -371,7 +436,8 @@ void orc_choice(int n, const float *tau, const float *heta, float alpha, float *
 /* tour has n+1 entries, tour[n] = tour[0].  Returns C^k.                    */
 /* ------------------------------------------------------------------------- */
 /* rule 0: Eq. 1 (reading R2); rule 1: the paper's data-parallel rule (R8);
-   rule 2: nearest-neighbour lists of length nn (R9). */
+   rule 2: nearest-neighbour lists of length nn (R9); rule 3: the exponential
+   race (R15). */
 int64_t orc_construct_ant_nn(int n, const float *choice, const int32_t *d, uint64_t seed,
                              uint32_t iteration, uint32_t ant, int rule, int nn,
                              const int32_t *lists, int32_t *tour);
@@ -409,6 +475,9 @@ int64_t orc_construct_ant_nn(int n, const float *choice, const int32_t *d, uint6
         } else if (rule == 1) {
             next = orc_iroulette(n, choice + (size_t)cur * n, visited, seed, (uint32_t)s, ant,
                                  iteration);
+        } else if (rule == 3) {
+            next = orc_race(n, choice + (size_t)cur * n, visited, seed, (uint32_t)s, ant,
+                            iteration);
         } else {
             draw(seed, (uint32_t)s, ant, iteration, x);
             uint64_t r = ((uint64_t)x[1] << 32) | (uint64_t)x[0];

@@ -84,6 +84,11 @@ def lib():
             L.orc_iroulette.argtypes = [C.c_int, f32p, u8p, C.c_uint64, C.c_uint32, C.c_uint32,
                                         C.c_uint32]
             L.orc_iroulette.restype = C.c_int
+            L.orc_race_exponentials.argtypes = [C.c_int, vp, vp]
+            L.orc_race_exponentials.restype = None
+            L.orc_race.argtypes = [C.c_int, f32p, u8p, C.c_uint64, C.c_uint32, C.c_uint32,
+                                   C.c_uint32]
+            L.orc_race.restype = C.c_int
             L.orc_construct_rule.argtypes = [C.c_int, C.c_int, f32p, i32p, C.c_uint64, C.c_uint32,
                                              C.c_int, i32p, i64p]
             L.orc_construct_rule.restype = None
@@ -189,7 +194,8 @@ def construct_ant(choice_, dist, seed: int, iteration: int, ant: int):
 
 
 def construct(choice_, dist, m: int, seed: int, iteration: int, rule: int = 0):
-    """rule 0: Eq. 1 by the integer roulette; rule 1: the paper's data-parallel rule."""
+    """rule 0: Eq. 1 by the integer roulette; rule 1: the paper's data-parallel rule;
+    rule 3: the exponential race (R15)."""
     ch = np.ascontiguousarray(choice_, np.float32)
     d = _i32(dist)
     n = d.shape[0]
@@ -235,6 +241,21 @@ def iroulette(w, visited, seed: int, step: int, ant: int, iteration: int) -> int
     w = np.ascontiguousarray(w, np.float32)
     v = np.ascontiguousarray(visited, np.uint8)
     return int(lib().orc_iroulette(len(w), w, v, C.c_uint64(seed), step, ant, iteration))
+
+
+def race_exponentials(v) -> np.ndarray:
+    """E = -ln(v 2^-24) in single precision by the series of R15, for integers v in [1, 2^24]."""
+    v = np.ascontiguousarray(v, np.uint32)
+    out = np.empty(v.shape, np.float32)
+    lib().orc_race_exponentials(v.size, v.ctypes.data, out.ctypes.data)
+    return out
+
+
+def race(w, visited, seed: int, step: int, ant: int, iteration: int) -> int:
+    """One step of the exponential race (R15) over the row w."""
+    w = np.ascontiguousarray(w, np.float32)
+    v = np.ascontiguousarray(visited, np.uint8)
+    return int(lib().orc_race(len(w), w, v, C.c_uint64(seed), step, ant, iteration))
 
 
 def deposit_scale(lens) -> int:
@@ -342,7 +363,7 @@ def run(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.5,
     """A whole Ant System run in mirror mode, with the fp64 pheromone carried alongside.
 
     rule 0 selects by Eq. 1, rule 1 by the paper's data-parallel rule, rule 2
-    by nearest-neighbour lists of length nn."""
+    by nearest-neighbour lists of length nn, rule 3 by the exponential race."""
     d = _i32(dist)
     n = d.shape[0]
     best_tour = np.zeros(n + 1, np.int32)

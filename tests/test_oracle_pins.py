@@ -406,6 +406,78 @@ def test_iroulette_degenerate_rows_and_tours(orc):
 
 
 # --------------------------------------------------------------------------
+# The exponential race (reading R15): a per-candidate random rule for Eq. 1
+# --------------------------------------------------------------------------
+
+def test_race_exponential_is_minus_log_of_the_uniform(orc):
+    # every one of the 2^24 uniforms: within 3 units in the last place of the
+    # float nearest -ln(v 2^-24), exactly 0 at v = 2^24, and non-increasing
+    prev_last = np.inf
+    for lo in range(1, (1 << 24) + 1, 1 << 22):
+        v = np.arange(lo, min(lo + (1 << 22), (1 << 24) + 1), dtype=np.uint32)
+        e = orc.race_exponentials(v)
+        true = -np.log(v.astype(np.float64) / 2.0**24)
+        ulp = np.spacing(np.abs(true).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(e.astype(np.float64) - true) <= 3 * ulp)
+        assert e[0] <= prev_last and np.all(np.diff(e) <= 0)
+        prev_last = e[-1]
+    assert prev_last == 0.0
+    assert orc.race_exponentials(np.array([1], np.uint32))[0] == np.float32(24 * math.log(2))
+
+
+def _race_freqs(orc, w, vis, draws):
+    counts = np.zeros(len(w), np.int64)
+    for i in range(draws):
+        counts[orc.race(w, vis, 23, 1 + (i % 997), i // 997, 5)] += 1
+    return counts
+
+
+def test_race_samples_eq1(orc):
+    # the minimum of independent exponentials of rates w_j is j with
+    # probability w_j / sum w: Eq. 1, unlike the product rule of R8
+    from scipy.stats import binomtest, chisquare
+    w = np.array([1.0, 2.0, 0.5, 4.0, 3.0, 0.0], np.float32)
+    vis = np.array([0, 0, 0, 0, 1, 0], np.uint8)
+    counts = _race_freqs(orc, w, vis, 60_000)
+    assert counts[4] == 0 and counts[5] == 0
+    cand = [0, 1, 2, 3]
+    p = w[cand].astype(np.float64) / float(w[cand].sum())
+    assert chisquare(counts[cand], p * counts.sum()).pvalue > 0.01
+    # two candidates w1 = 3 w2: city 2 with probability 1/4 (the product
+    # rule of R8 gives 1/6)
+    w2 = np.array([0.0, 3.0, 1.0], np.float32)
+    c2 = _race_freqs(orc, w2, np.array([1, 0, 0], np.uint8), 40_000)
+    assert binomtest(int(c2[2]), int(c2.sum()), 0.25).pvalue > 0.01
+
+
+def test_race_degenerate_rows_and_tours(orc):
+    w = np.zeros(6, np.float32)
+    vis = np.array([1, 0, 1, 0, 0, 0], np.uint8)
+    assert orc.race(w, vis, 1, 1, 0, 0) == 1          # every weight 0: lowest unvisited
+    w1 = np.array([5.0, 0.0, 0.0, 1e-3, 0.0, 0.0], np.float32)
+    for step in range(1, 200):                         # the only positive weight wins
+        assert orc.race(w1, vis, 4, step, 2, 0) == 3
+    assert orc.race(np.ones(4, np.float32), np.array([1, 1, 0, 1], np.uint8), 3, 1, 0, 0) == 2
+    inst = I.uniform_instance(23, 1000, seed=3)
+    h = orc.heta(inst.dist, 2.0)
+    ch = orc.choice(np.where(np.eye(23) > 0, 0, 0.3).astype(np.float32), h, 1.0)
+    tours, lens = orc.construct(ch, inst.dist, 11, seed=2, iteration=1, rule=3)
+    for k in range(11):
+        t = tours[k]
+        assert sorted(t[:-1].tolist()) == list(range(23)) and t[-1] == t[0]
+        assert lens[k] == int(inst.dist[t[:-1], t[1:]].astype(np.int64).sum())
+    t0, _ = orc.construct(ch, inst.dist, 11, seed=2, iteration=1, rule=0)
+    assert np.array_equal(t0[:, 0], tours[:, 0])
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (9, 2)])
+def test_race_ant_system_reaches_brute_force_optimum(orc, n, seed):
+    inst = I.uniform_instance(n, 1000, seed=seed)
+    opt, _ = orc.brute_force(inst.dist)
+    assert orc.run(inst.dist, n, 40, seed, rule=3)["best_len"] == opt
+
+
+# --------------------------------------------------------------------------
 # Nearest-neighbour lists (reading R9; Table 2 versions 4-6 use nn = 30)
 # --------------------------------------------------------------------------
 
