@@ -63,8 +63,10 @@ def parse():
                     help="as: the Ant System update (Eqs. 2-4); mmas: the MAX-MIN Ant System "
                          "update (p_best 0.05, iteration-best deposit); acs: the Ant Colony "
                          "System (q0 0.9, xi 0.1; m = min(m, 10))")
-    ap.add_argument("--selection", default="eq1", choices=["eq1", "data-parallel"],
-                    help="eq1: Eq. 1 (default); data-parallel: the paper's product-argmax kernel")
+    ap.add_argument("--selection", default="eq1", choices=["eq1", "data-parallel", "exp-race"],
+                    help="eq1: Eq. 1 by the integer roulette (default); data-parallel: the "
+                         "paper's product-argmax kernel; exp-race: the exponential race "
+                         "(per-candidate exponentials, samples Eq. 1)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-iterations", type=int, default=0,
                     help="0 = the workload's 100; fewer for profiling runs")
@@ -333,8 +335,10 @@ def run_ours(args, w, rank, world, local):
         aco.aco_set_option(h, aco.ACO_OPT_DEPOSIT, dep)
         if args.warps_per_ant:
             aco.aco_set_option(h, aco.ACO_OPT_WARPS_PER_ANT, args.warps_per_ant)
-        if args.selection == "data-parallel":
-            aco.aco_set_option(h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
+        if args.selection != "eq1":
+            aco.aco_set_option(h, aco.ACO_OPT_SELECTION,
+                               {"data-parallel": aco.ACO_SELECT_DATA_PARALLEL,
+                                "exp-race": aco.ACO_SELECT_EXP_RACE}[args.selection])
         if args.nn:
             aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, args.nn)
         if args.staging >= 0:
@@ -455,7 +459,7 @@ def run_ours(args, w, rank, world, local):
 
 CONSTRUCT_SOURCES = ("aco_device.cuh", "construct.cuh", "construct_g1h8.cu", "construct_g1h16.cu",
                      "construct_g1h32.cu", "construct_g2h32.cu", "construct_g4h32.cu",
-                     "construct_rule1.cu")
+                     "construct_rule.cuh", "construct_rule1.cu", "construct_rule2.cu")
 
 
 def construct_sources_sha256() -> str:

@@ -119,6 +119,18 @@ extern "C" {
                                   picks city 2 with probability w2 / (2 w1).
                                   Whole warps per ant only (lanes per ant 32,
                                   warps per ant 1 or 2).                       */
+#define ACO_SELECT_EXP_RACE 2  /* the exponential race, a per-candidate random
+                                  rule that samples Eq. 1: every unvisited city
+                                  j takes v_j = floor(x/2^8) + 1 from the same
+                                  counter and word as above, E_j = -ln(v_j
+                                  2^-24) in single precision by the range-
+                                  reduced inverse-hyperbolic-tangent series
+                                  (every operation rounded on its own), and
+                                  the smallest key fl(E_j / w_j) wins (ties to
+                                  the lower index; zero weights and
+                                  overflowing keys are +inf).  City j then wins
+                                  with probability w_j / sum w.  Same tilings
+                                  as ACO_SELECT_DATA_PARALLEL.                 */
 
 #define ACO_DEPOSIT_GATHER 0   /* atomic-free: edges bucketed per city by the
                                   construction kernel, one warp reduces a row  */
@@ -553,6 +565,16 @@ int aco_selftest_bounded_wait(int32_t polls, int32_t complete);
  * 1 <= count <= 2^24; ACO_EINVAL on NULL pointers.
  */
 int aco_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int32_t count);
+
+/*
+ * aco_race_exponential - the exponential race's variate (ACO_SELECT_EXP_RACE)
+ * as the construction kernels compute it, on the GPU: out[i] = E for the
+ * Philox word x[i], E = -ln(v 2^-24), v = floor(x[i] / 2^8) + 1, in single
+ * precision by the range-reduced inverse-hyperbolic-tangent series.  x and
+ * out are host arrays of `count` entries, 1 <= count <= 2^24; ACO_EINVAL on
+ * NULL pointers.
+ */
+int aco_race_exponential(const uint32_t *x, float *out, int32_t count);
 
 #ifdef __cplusplus
 }

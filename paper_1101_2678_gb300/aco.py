@@ -38,6 +38,7 @@ ACO_OPT_STAGING = 10
 ACO_OPT_CHECK = 11
 ACO_SELECT_EQ1 = 0
 ACO_SELECT_DATA_PARALLEL = 1
+ACO_SELECT_EXP_RACE = 2
 
 ACO_DEPOSIT_GATHER = 0
 ACO_DEPOSIT_ATOMIC_U64 = 1
@@ -78,6 +79,7 @@ SIGNATURES = [
     ("aco_save_state", C.c_int, [_vp, _vp, C.c_uint64, C.POINTER(C.c_uint64)]),
     ("aco_restore_state", C.c_int, [_vp, _vp, C.c_uint64]),
     ("aco_philox4x32_10", C.c_int, [_vp, _vp, _vp, C.c_int32]),
+    ("aco_race_exponential", C.c_int, [_vp, _vp, C.c_int32]),
     ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
     ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
     ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
@@ -240,6 +242,14 @@ def aco_philox4x32_10(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, np.uint32).reshape(2)
     out = np.empty_like(c)
     _check(load().aco_philox4x32_10(_ptr(c), _ptr(k), _ptr(out), c.shape[0]), "aco_philox4x32_10")
+    return out
+
+
+def aco_race_exponential(x) -> np.ndarray:
+    """The exponential race's variate E for Philox words x (uint32), computed on the GPU."""
+    xs = np.ascontiguousarray(x, np.uint32)
+    out = np.empty(xs.shape, np.float32)
+    _check(load().aco_race_exponential(_ptr(xs), _ptr(out), xs.size), "aco_race_exponential")
     return out
 
 

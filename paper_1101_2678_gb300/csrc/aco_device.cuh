@@ -51,7 +51,8 @@ struct Instance {
   int ldm;   // nbr row stride (>= m, multiple of 32)
   float alpha, beta, rho;
   int rule;                     // 0: Eq. 1 (integer roulette); 1: product of a uniform and the
-                                // weight, highest wins (the paper's data-parallel kernel)
+                                // weight, highest wins (the paper's data-parallel kernel);
+                                // 2: the exponential race (smallest E_j / w_j)
   int stage;                    // row staging: 0 bulk copy (TMA) + mbarrier, 1 lane copies
   unsigned long long seed;
   const int32_t* dist;          // [n][ld]

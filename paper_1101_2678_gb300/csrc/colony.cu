@@ -93,6 +93,7 @@ ConstructTiling batched_construct_tiling(int n) { return default_construct_tilin
 cudaError_t launch_construct(const Instance& I, ConstructTiling t, cudaStream_t st) {
   if (t.W < 1 || t.W > 8) return cudaErrorInvalidValue;
   if (I.rule == 1) return launch_construct_rule1(I, t, st);
+  if (I.rule == 2) return launch_construct_rule2(I, t, st);
   if (t.G == 1 && t.H == 8) return launch_construct_g1h8(I, t.C, t.W, st);
   if (t.G == 1 && t.H == 16) return launch_construct_g1h16(I, t.C, t.W, st);
   if (t.G == 1 && t.H == 32) return launch_construct_g1h32(I, t.C, t.W, st);
@@ -199,7 +200,7 @@ static ConstructTiling tiling_of(const aco_colony* h) {
 static bool tiling_ok(ConstructTiling t, int rule) {
   if (t.C == 0 || t.W < 1 || t.W > 8) return false;
   if (t.H < 32 && t.G != 1) return false;
-  if (rule == 1 && (t.H != 32 || t.G > 2)) return false;
+  if (rule != 0 && (t.H != 32 || t.G > 2)) return false;
   return ants_per_cta(t) >= 1;
 }
 
@@ -799,7 +800,8 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
       break;
     }
     case ACO_OPT_SELECTION: {
-      if (value != ACO_SELECT_EQ1 && value != ACO_SELECT_DATA_PARALLEL)
+      if (value != ACO_SELECT_EQ1 && value != ACO_SELECT_DATA_PARALLEL &&
+          value != ACO_SELECT_EXP_RACE)
         return fail(ACO_EINVAL, "selection rule %lld", (long long)value);
       if (value != ACO_SELECT_EQ1 && h->I.nn > 0)
         return fail(ACO_EINVAL, "nearest-neighbour lists use Eq. 1 (ACO_SELECT_EQ1)");
@@ -809,7 +811,7 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
       h->I.rule = (int)value;
       if (!tiling_ok(tiling_of(h), h->I.rule)) {
         h->I.rule = old;
-        return fail(ACO_EINVAL, "the data-parallel rule needs whole warps per ant (H = 32, G <= 2)");
+        return fail(ACO_EINVAL, "per-candidate rules need whole warps per ant (H = 32, G <= 2)");
       }
       break;
     }

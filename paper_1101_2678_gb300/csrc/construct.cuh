@@ -210,10 +210,42 @@ __host__ __device__ constexpr int groups_per_cta(int warps) {
   return H == 32 ? warps / G : warps * (32 / H);
 }
 
+// E = -ln(v 2^-24) for the candidate word x, v = floor(x / 2^8) + 1 in
+// [1, 2^24], in single precision by the range-reduced inverse-hyperbolic-
+// tangent series of the logarithm: v = 2^e f with f in [1, 2), halved when
+// f > sqrt 2; s = (f - 1) / (f + 1); ln f = 2 s (1 + z/3 + z^2/5 + z^3/7 +
+// z^4/9), z = s^2; E = (24 - e) ln 2 - ln f.  Every operation is rounded on
+// its own (no contraction), so any IEEE implementation of the same sequence
+// gives the same bits.  The constants are the floats nearest sqrt 2, ln 2,
+// 1/3, 1/5, 1/7 and 1/9.
+__device__ __forceinline__ float race_exponential(uint32_t x) {
+  const uint32_t v = (x >> 8) + 1u;
+  int e = 31 - __clz((int)v);
+  // v 2^-e, exact: v < 2^25 is a float and 2^-e a normal power of two
+  float f = __fmul_rn(__uint2float_rn(v), __uint_as_float((uint32_t)(127 - e) << 23));
+  if (f > 0x1.6a09e6p+0f) {
+    f = __fmul_rn(f, 0.5f);
+    e += 1;
+  }
+  const float s = __fdiv_rn(__fsub_rn(f, 1.0f), __fadd_rn(f, 1.0f));
+  const float z = __fmul_rn(s, s);
+  float p = 0x1.c71c72p-4f;
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.24924ap-3f);
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.99999ap-3f);
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.555556p-2f);
+  p = __fadd_rn(__fmul_rn(p, z), 1.0f);
+  const float ln_f = __fmul_rn(__fadd_rn(s, s), p);
+  return __fsub_rn(__fmul_rn(__int2float_rn(24 - e), 0x1.62e430p-1f), ln_f);
+}
+
 // R = 0: Eq. 1 by the integer roulette.  R = 1: the paper's data-parallel
 // rule: every unvisited city scores u_j * w_j with its own uniform u_j, the
 // highest score wins (ties to the lower index; all scores 0: the lowest
-// unvisited city).
+// unvisited city).  R = 2: the exponential race, which samples Eq. 1: every
+// unvisited city gets the key E_j / w_j from its own exponential variate
+// E_j, the smallest key wins (ties to the lower index; zero weights and
+// overflowing keys are +inf, so with every weight 0 the lowest unvisited
+// city wins).
 template <int C, int G, int H, int R = 0>
 __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, const int tg,
                                               const Seg<H> seg, GroupSmem* gs, const int bar_id,
@@ -370,7 +402,46 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
       else mx = 0u;           // every score is 0: the rule below takes the lowest unvisited
       next = (int)(0xffffffffu - (uint32_t)key);
     }
-    if (R == 1 && mx != 0u) {
+    if constexpr (R == 2) {
+      // Keys are non-negative floats (their bits order like their values);
+      // a visited city keeps the sentinel above every key.  A thread's four
+      // consecutive cities share one Philox call, and each thread walks its
+      // cities in ascending order keeping the first smallest key.
+      uint32_t bkey = 0xffffffffu, bj = 0xffffffffu;
+#pragma unroll
+      for (int i = 0; i < C; i += 4) {
+        const Philox4 x = philox4x32_10((uint32_t)s, (uint32_t)ant, iter,
+                                        1u + (uint32_t)((base + i) >> 2), (uint32_t)seed,
+                                        (uint32_t)(seed >> 32));
+        const uint32_t xs[4] = {x.x0, x.x1, x.x2, x.x3};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int li = i + e;
+          const float w = __uint_as_float(v[li]);
+          const float key = w > 0.0f ? __fdiv_rn(race_exponential(xs[e]), w)
+                                     : __uint_as_float(0x7f800000u);
+          const uint32_t kb = __float_as_uint(key);
+          if (!((vis[li >> 5] >> (li & 31)) & 1u) && kb < bkey) {
+            bkey = kb;
+            bj = (uint32_t)(base + li);
+          }
+        }
+      }
+      uint64_t key = ((uint64_t)bkey << 32) | bj;
+#pragma unroll
+      for (int o = H / 2; o > 0; o >>= 1) {
+        const uint64_t other = seg.shfl_xor(key, o);
+        key = other < key ? other : key;
+      }
+      if (G > 1) {
+        if (hl == 0) gs->wsum[wg] = key;
+        group_sync(bar_id, NT);
+#pragma unroll
+        for (int w = 0; w < G; ++w) key = gs->wsum[w] < key ? gs->wsum[w] : key;
+      }
+      next = (int)(uint32_t)key;
+    }
+    if ((R == 1 && mx != 0u) || R == 2) {
       // chosen above
     } else if (mx == 0u) {
       // Every unvisited weight is zero: the lowest-index unvisited city.

@@ -79,6 +79,7 @@ ACO_DECLARE_CONSTRUCT(g4h32)
 bool construct_supported(int C, int G, int H);
 // The paper's data-parallel selection rule (Instance::rule == 1); H = 32, G = 1 or 2.
 cudaError_t launch_construct_rule1(const Instance& I, ConstructTiling t, cudaStream_t st);
+cudaError_t launch_construct_rule2(const Instance& I, ConstructTiling t, cudaStream_t st);
 cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
                                    ConstructTiling t, cudaStream_t st);
 

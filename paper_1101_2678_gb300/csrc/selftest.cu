@@ -7,6 +7,7 @@
 // copy is left in flight either way, so the kernel ends cleanly.
 #include "../../include/aco.h"
 #include "aco_device.cuh"
+#include "construct.cuh"
 #include "runtime.h"
 
 namespace aco {
@@ -92,5 +93,38 @@ extern "C" int aco_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint3
   if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(e, "philox");
+  return ACO_OK;
+}
+
+namespace aco {
+
+// The exponential race's variate E(x) (the construction kernels' function).
+__global__ void race_exponential_kernel(const uint32_t* __restrict__ x, float* __restrict__ out,
+                                        int count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    out[i] = race_exponential(x[i]);
+}
+
+}  // namespace aco
+
+extern "C" int aco_race_exponential(const uint32_t* x, float* out, int32_t count) {
+  if (!x || !out) return fail(ACO_EINVAL, "NULL argument");
+  if (count < 1 || count > (1 << 24)) return fail(ACO_EINVAL, "count outside [1, 2^24]");
+  const size_t bytes = (size_t)count * 4;
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 2 * bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "race alloc");
+  uint32_t* dx = static_cast<uint32_t*>(d);
+  float* dout = reinterpret_cast<float*>(dx + count);
+  e = cudaMemcpy(dx, x, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    int blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    race_exponential_kernel<<<blocks, 256>>>(dx, dout, count);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "race exponential");
   return ACO_OK;
 }

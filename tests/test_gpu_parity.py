@@ -382,6 +382,72 @@ def test_data_parallel_rule_run_bit_exact(aco, orc):
 
 
 # ---------------------------------------------------------------------------
+# The exponential race (optional, ACO_SELECT_EXP_RACE; reading R15)
+# ---------------------------------------------------------------------------
+
+def test_race_exponential_device_equals_oracle_on_every_uniform(aco, orc):
+    # all 2^24 values of v = floor(x / 2^8) + 1, and words with low bits set
+    v = np.arange(1, (1 << 24) + 1, dtype=np.uint32)
+    x = (v - 1) << 8
+    assert np.array_equal(aco.aco_race_exponential(x).view(np.uint32),
+                          orc.race_exponentials(v).view(np.uint32))
+    xr = np.random.default_rng(3).integers(0, 1 << 32, 1 << 20, dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(aco.aco_race_exponential(xr).view(np.uint32),
+                          orc.race_exponentials((xr >> 8) + 1).view(np.uint32))
+
+
+@pytest.mark.parametrize("n", [5, 48, 300, 1100, 2400])
+def test_race_tours_match_oracle(aco, orc, n):
+    inst = I.uniform_instance(n, 1000, seed=310 + n)
+    m = 9 if n > 1000 else n + 1
+    ch = oracle_initial_choice(orc, inst.dist, m)
+    with aco.Colony(inst.dist, m, seed=6) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_EXP_RACE)
+        ref_t, ref_l = orc.construct(ch, inst.dist, m, seed=6, iteration=0, rule=3)
+        for G, A in [(0, 0), (1, 1), (2, 2)]:
+            if G:
+                try:
+                    aco.aco_set_option(c.h, aco.ACO_OPT_WARPS_PER_ANT, G)
+                    aco.aco_set_option(c.h, aco.ACO_OPT_ANTS_PER_CTA, A)
+                except aco.AcoError:
+                    continue
+            tours, lens = aco.aco_construct_tours(c.h, n, m)
+            assert np.array_equal(tours, ref_t), (G, A)
+            assert np.array_equal(lens, ref_l), (G, A)
+        with pytest.raises(aco.AcoError):
+            aco.aco_set_option(c.h, aco.ACO_OPT_LANES_PER_ANT, 16)
+        with pytest.raises(aco.AcoError):
+            aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 10)
+
+
+def test_race_run_bit_exact_with_zero_weights(aco, orc):
+    # beta = 0 on an instance with alpha = 0 would give equal weights; here
+    # rho = 1 and a few iterations drive most trails to exactly 0, so zero
+    # weights (key +inf) and their lowest-index fallback are exercised
+    inst = I.clustered_instance(97, seed=8, clusters=5, side=3000)
+    for rho, iters in [(0.5, 8), (1.0, 4)]:
+        ref = orc.run(inst.dist, 50, iters, 21, rho=rho, rule=3)
+        with aco.Colony(inst.dist, 50, seed=21, rho=rho) as c:
+            aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_EXP_RACE)
+            aco.aco_iterate(c.h, iters)
+            assert np.array_equal(aco.aco_get_pheromone(c.h, 97), ref["tau32"])
+            tour, best = aco.aco_best_tour(c.h, 97)
+        assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+
+
+def test_race_full_size_sampled(aco, orc):
+    w = I.workload_n1002()
+    d, m = w["inst"].dist, w["m"]
+    ch = oracle_initial_choice(orc, d, m)
+    with aco.Colony(d, m, seed=w["seed"]) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_EXP_RACE)
+        tours, lens = aco.aco_construct_tours(c.h, 1002, m)
+    check_tours(tours, lens, d)
+    ref_t, ref_l = orc.construct(ch, d, 4, seed=w["seed"], iteration=0, rule=3)
+    assert np.array_equal(tours[:4], ref_t) and np.array_equal(lens[:4], ref_l)
+
+
+# ---------------------------------------------------------------------------
 # Nearest-neighbour-list construction (optional, ACO_OPT_NN_LIST)
 # ---------------------------------------------------------------------------
 
