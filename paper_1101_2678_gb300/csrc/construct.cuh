@@ -344,28 +344,37 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     }
     const float* row = srow;
 
+    // The race over long chunks reads its weights from the staged row as it
+    // goes (a register copy of 60 or more weights beside its per-candidate
+    // arithmetic measured slower); everything else works on a register copy.
+    constexpr bool kRowRace = R == 2 && C >= 60;
     uint32_t v[C];  // weight bits; w >= 0 orders like its bit pattern
+    uint32_t mx = 0u;
+    if constexpr (!kRowRace) {
 #pragma unroll
-    for (int i = 0; i < C; i += 4) {
-      // Chunk entries at or beyond ld hold stale data; their tabu bits are set.
-      const uint4 t = *reinterpret_cast<const uint4*>(row + base + i);
-      v[i] = t.x;
-      v[i + 1] = t.y;
-      v[i + 2] = t.z;
-      v[i + 3] = t.w;
+      for (int i = 0; i < C; i += 4) {
+        // Chunk entries at or beyond ld hold stale data; their tabu bits are set.
+        const uint4 t = *reinterpret_cast<const uint4*>(row + base + i);
+        v[i] = t.x;
+        v[i + 1] = t.y;
+        v[i + 2] = t.z;
+        v[i + 3] = t.w;
+      }
     }
-    uint32_t m4[4] = {0u, 0u, 0u, 0u};  // four independent max chains
+    if constexpr (R != 2) {
+      uint32_t m4[4] = {0u, 0u, 0u, 0u};  // four independent max chains
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
-      m4[i & 3] = max(m4[i & 3], v[i]);
-    }
-    uint32_t mx = seg.max_u32(max(max(m4[0], m4[1]), max(m4[2], m4[3])));
-    if (G > 1) {
-      if (hl == 0) gs->wmax[wg] = mx;
-      group_sync(bar_id, NT);
+      for (int i = 0; i < C; ++i) {
+        if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+        m4[i & 3] = max(m4[i & 3], v[i]);
+      }
+      mx = seg.max_u32(max(max(m4[0], m4[1]), max(m4[2], m4[3])));
+      if (G > 1) {
+        if (hl == 0) gs->wmax[wg] = mx;
+        group_sync(bar_id, NT);
 #pragma unroll
-      for (int w = 0; w < G; ++w) mx = max(mx, gs->wmax[w]);
+        for (int w = 0; w < G; ++w) mx = max(mx, gs->wmax[w]);
+      }
     }
 
     int next;
@@ -414,14 +423,29 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
                                         1u + (uint32_t)((base + i) >> 2), (uint32_t)seed,
                                         (uint32_t)(seed >> 32));
         const uint32_t xs[4] = {x.x0, x.x1, x.x2, x.x3};
+        uint32_t wv[4];
+        if constexpr (kRowRace) {
+          const uint4 t = *reinterpret_cast<const uint4*>(row + base + i);
+          wv[0] = t.x;
+          wv[1] = t.y;
+          wv[2] = t.z;
+          wv[3] = t.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) wv[e] = v[i + e];
+        }
+        // the four tabu bits of these cities (i % 4 == 0: one word)
+        const uint32_t vis4 = vis[i >> 5] >> (i & 31);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int li = i + e;
-          const float w = __uint_as_float(v[li]);
-          const float key = w > 0.0f ? __fdiv_rn(race_exponential(xs[e]), w)
-                                     : __uint_as_float(0x7f800000u);
+          const float w = __uint_as_float(wv[e]);
+          const bool open = !((vis4 >> e) & 1u);
+          // visited cities skip the logarithm and the division
+          const float key = open && w > 0.0f ? __fdiv_rn(race_exponential(xs[e]), w)
+                                             : __uint_as_float(0x7f800000u);
           const uint32_t kb = __float_as_uint(key);
-          if (!((vis[li >> 5] >> (li & 31)) & 1u) && kb < bkey) {
+          if (open && kb < bkey) {
             bkey = kb;
             bj = (uint32_t)(base + li);
           }
