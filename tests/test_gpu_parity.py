@@ -121,6 +121,41 @@ def test_max_n_sampled(aco, orc):
             assert np.array_equal(tours[k], t) and lens[k] == L
 
 
+@pytest.mark.parametrize("sel,orc_rule", [("ACO_SELECT_DATA_PARALLEL", 1),
+                                          ("ACO_SELECT_EXP_RACE", 3)])
+def test_max_n_per_candidate_rules_sampled(aco, orc, sel, orc_rule):
+    # n = 4096 takes two warps per ant (G = 2) by default
+    n, m = 4096, 8
+    inst = I.uniform_instance(n, 1000, seed=4097)
+    ch = oracle_initial_choice(orc, inst.dist, m)
+    with aco.Colony(inst.dist, m, seed=5) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, getattr(aco, sel))
+        assert aco.aco_get_option(c.h, aco.ACO_OPT_WARPS_PER_ANT) == 2
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+    check_tours(tours, lens, inst.dist)
+    ref_t, ref_l = orc.construct(ch, inst.dist, 2, seed=5, iteration=0, rule=orc_rule)
+    assert np.array_equal(tours[:2], ref_t) and np.array_equal(lens[:2], ref_l)
+
+
+def test_max_n_update_rules_one_iteration(aco, orc):
+    # the MAX-MIN and Ant Colony System updates at n = 4096 against whole
+    # oracle runs (tau compared cell for cell)
+    n = 4096
+    inst = I.uniform_instance(n, 1000, seed=4098)
+    ref = orc.run_mmas(inst.dist, 6, 1, 9, rho=0.02, p_best=0.05)
+    with aco.Colony(inst.dist, 6, seed=9, rho=0.02) as c:
+        aco.aco_set_mmas(c.h, 0.05, False)
+        aco.aco_iterate(c.h, 1)
+        assert np.array_equal(aco.aco_get_pheromone(c.h, n), ref["tau32"])
+        assert aco.aco_best_tour(c.h, n)[1] == ref["best_len"]
+    ref = orc.run_acs(inst.dist, 4, 1, 9, rho=0.1, q0=0.9, xi=0.1)
+    with aco.Colony(inst.dist, 4, seed=9, rho=0.1) as c:
+        aco.aco_set_acs(c.h, 0.9, 0.1)
+        aco.aco_iterate(c.h, 1)
+        assert np.array_equal(aco.aco_get_pheromone(c.h, n), ref["tau32"])
+        assert aco.aco_best_tour(c.h, n)[1] == ref["best_len"]
+
+
 def test_construct_is_idempotent_and_graph_equals_eager(aco):
     inst = I.uniform_instance(200, 1000, seed=5)
     with aco.Colony(inst.dist, 64, seed=11) as a, aco.Colony(inst.dist, 64, seed=11) as b:
