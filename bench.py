@@ -74,9 +74,12 @@ def parse():
                     help="batched: default tiling for every class (profiling runs)")
     ap.add_argument("--no-loop-baseline", action="store_true",
                     help="skip the per-instance loop (profiling runs)")
-    ap.add_argument("--serve-seconds", type=float, default=20.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson arrival window for --workload served")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--no-multirate", action="store_true",
+                    help="served: one iteration per step for every request (no multi-rate "
+                         "stepping)")
     ap.add_argument("--serve-loop-sample", type=int, default=16,
                     help="requests solved one at a time for the loop comparison")
     return ap.parse_args()
@@ -737,10 +740,11 @@ def run_served(args, rank, world, local):
     for r in range(len(arrivals)):
         q = instances.served_request(r)
         reqs.append(serve.Request(q["inst"].coords, q["m"], q["iterations"], q["seed"]))
-    with serve.Server(budget_bytes=64 << 30, max_slots=4096) as srv:
+    mr = not args.no_multirate
+    with serve.Server(budget_bytes=64 << 30, max_slots=4096, multirate=mr) as srv:
         # configured stream: stop admitting/stepping at the end of the arrival window
         outs, st = srv.run(reqs, arrivals, deadline=args.serve_seconds)
-    with serve.Server(budget_bytes=64 << 30, max_slots=4096) as srv:
+    with serve.Server(budget_bytes=64 << 30, max_slots=4096, multirate=mr) as srv:
         # sustainable stream at 0.7x the measured completion rate
         cap = max(st["solves_per_s"], 0.5)
         rate = 0.7 * cap
@@ -759,7 +763,8 @@ def run_served(args, rank, world, local):
         loop_lens.append(aco.aco_best_tour(h, r.n)[1])
         aco.aco_destroy(h)
     t_loop = time.perf_counter() - t0
-    with serve.Server(budget_bytes=64 << 30, max_slots=4096, max_step_work=1 << 62) as srv:
+    with serve.Server(budget_bytes=64 << 30, max_slots=4096, max_step_work=1 << 62,
+                      multirate=mr) as srv:
         outs3, st3 = srv.run(sample, np.zeros(len(sample)), realtime=False)
     same = sorted((o.index, o.best_len) for o in outs3) == list(enumerate(loop_lens))
     if rank != 0:
@@ -770,7 +775,8 @@ def run_served(args, rank, world, local):
         "ms_per_step": st["elapsed_s"] / max(st["steps"], 1) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "as-served-poisson", "rate_per_s": args.serve_rate,
-                   "window_s": args.serve_seconds, "budget_gb": 64, "iterations": 200},
+                   "window_s": args.serve_seconds, "budget_gb": 64, "iterations": 200,
+                   "multirate": mr},
         "configured_stream": st,
         "sustainable_stream": dict(st2, rate_per_s=rate),
         "loop_comparison": {

@@ -414,8 +414,9 @@ int aco_pool_set_acs(aco_pool_handle p, int32_t slot, double q0, float xi);
 int aco_pool_set_mmas(aco_pool_handle p, int32_t slot, double p_best, int32_t best_so_far);
 
 /*
- * aco_pool_step - one iteration for every live slot (asynchronous).  A slot
- * whose iteration budget is used up becomes finished and leaves the live set.
+ * aco_pool_step - one iteration for every live slot (asynchronous; with
+ * multi-rate stepping, each slot's own rate).  A slot whose iteration budget
+ * is used up becomes finished and leaves the live set.
  * *live_after (may be NULL) receives the number of slots still live.
  */
 int aco_pool_step(aco_pool_handle p, int32_t *live_after);
@@ -466,6 +467,23 @@ int aco_pool_stats(aco_pool_handle p, int32_t *live, int32_t *finished, uint64_t
  *     ACO_ESTATE before the first step after the live set changed.
  */
 int aco_pool_set_autotune(aco_pool_handle p, int32_t on);
+/*
+ * aco_pool_set_multirate - on = 1: every aco_pool_step runs k iterations for
+ * each group of slots (a construction class, or all Ant Colony System
+ * colonies), each group on its own stream with its own best and update
+ * launches, where k = floor(T_max / T_group) within [1, 64] from a model of
+ * one iteration's time alone (about n (0.6 + 0.025 n / 32) us; 4 n us for a
+ * colony) and T_max that of the slowest group, and never more than the
+ * iterations any slot of the group has left.  Short instances then keep
+ * pace with the longest instead of waiting one long step per iteration.
+ * Every slot still runs exactly its own iterations, so its results are
+ * unchanged.  on = 0 (default): one iteration per step for every slot.
+ * ACO_EINVAL for a static batch (aco_batch_*), whose steps count iterations.
+ * aco_pool_rate: the iterations the last step ran for `slot` (live or
+ * finished; 1 unless multi-rate; ACO_ESTATE before its first step).
+ */
+int aco_pool_set_multirate(aco_pool_handle p, int32_t on);
+int aco_pool_rate(aco_pool_handle p, int32_t slot, int32_t *iterations_per_step);
 int aco_pool_autotune(aco_pool_handle p);
 int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t *warps_per_ant,
                     int32_t *lanes_per_ant, int32_t *cities_per_lane, int32_t *staging);

@@ -96,6 +96,8 @@ SIGNATURES = [
                                         C.c_int32, C.c_uint64, C.c_int32, _i32p]),
     ("aco_pool_set_acs", C.c_int, [_vp, C.c_int32, C.c_double, C.c_float]),
     ("aco_pool_set_mmas", C.c_int, [_vp, C.c_int32, C.c_double, C.c_int32]),
+    ("aco_pool_set_multirate", C.c_int, [_vp, C.c_int32]),
+    ("aco_pool_rate", C.c_int, [_vp, C.c_int32, _i32p]),
     ("aco_pool_step", C.c_int, [_vp, _i32p]),
     ("aco_pool_finished", C.c_int, [_vp, _vp, C.c_int32, _i32p]),
     ("aco_pool_result", C.c_int, [_vp, C.c_int32, _vp, _vp]),
@@ -347,6 +349,16 @@ def aco_pool_admit(p, dist, alpha, beta, rho, m, seed, iterations):
     _check(load().aco_pool_admit(p, d.shape[0], _ptr(d), alpha, beta, rho, m, seed, iterations,
                                  C.byref(slot)), "aco_pool_admit")
     return slot.value
+
+
+def aco_pool_set_multirate(p, on: bool) -> None:
+    _check(load().aco_pool_set_multirate(p, int(on)), "aco_pool_set_multirate")
+
+
+def aco_pool_rate(p, slot: int) -> int:
+    k = C.c_int32()
+    _check(load().aco_pool_rate(p, slot, C.byref(k)), "aco_pool_rate")
+    return k.value
 
 
 def aco_pool_set_acs(p, slot: int, q0: float, xi: float) -> None:

@@ -94,6 +94,7 @@ struct PoolSlot {
   cudaEvent_t ready = nullptr;  // setup done on the side stream
   bool wait_ready = false;
   bool started = false;  // taken part in a step (the update rule is then fixed)
+  int rate = 1;          // iterations per step (multi-rate stepping)
 };
 
 struct aco_pool {
@@ -113,16 +114,24 @@ struct aco_pool {
   int2* d_rows = nullptr;
   int* d_coords = nullptr;  // staging for aco_pool_admit_coords (n pairs)
   int* d_acs = nullptr;     // live Ant Colony System slots
+  int* d_cls_slots = nullptr;  // the live slots of each class, class after class
   size_t items_cap = 0, rows_cap = 0;
   // host mirrors of the lists
-  std::vector<int> h_live, h_acs;
+  std::vector<int> h_live, h_acs, h_cls_slots;
   int acs_max_m = 0, acs_max_n = 0;
+  // Multi-rate stepping: each class (and the colonies) runs `k` iterations
+  // per step, chosen so that short instances keep pace with the longest.
+  bool multirate = false;
+  int acs_k = 1;
   std::vector<int2> h_items, h_rows;
   struct Class {
     ConstructTiling t;
-    int begin, count;
+    int begin, count;               // its items (slot, ant)
     std::tuple<int, int, int> key;  // the default tiling's (G, H, C)
     int max_n;
+    int slot_begin, slot_count;     // its slots in h_cls_slots
+    int row_begin, row_count, max_ld;  // its rows in h_rows
+    int k;                          // iterations per step
   };
   std::vector<Class> classes;
   // Autotuner: for each default class, the (G, H, ants per CTA) that measured
@@ -194,10 +203,34 @@ static int ensure_capacity(void** ptr, size_t* cap, size_t need, size_t elem) {
   return ACO_OK;
 }
 
+// Modelled time of one iteration of an instance of n cities run alone, in
+// microseconds: n dependent steps, each costing a fixed latency plus the
+// per-lane chunk (n / 32 cities); the Ant Colony System's lockstep step is
+// about 4 us.  Only ratios matter (they set the iterations per step).
+static double iteration_time_model(int n, bool acs) {
+  return acs ? 4.0 * n : n * (0.6 + 0.025 * n / 32.0);
+}
+constexpr int kMaxRate = 64;  // iterations per step at most
+
+// Iterations per step for a group whose slowest instance takes t (model) in
+// a step whose slowest group takes t_max, limited so that no slot of the
+// group runs past its iteration budget.
+static int group_rate(const aco_pool* p, const int* slots, int count, double t, double t_max) {
+  if (!p->multirate) return 1;
+  int k = (int)std::floor(t_max / t);
+  k = std::max(1, std::min(k, kMaxRate));
+  for (int i = 0; i < count; ++i) {
+    const long long left = p->slots[(size_t)slots[i]].iters_left;
+    if (left > 0 && left < k) k = (int)left;
+  }
+  return k;
+}
+
 // Rebuild the device work lists for the current live set.
 static int pool_rebuild(aco_pool* p) {
   p->h_live.clear();
   p->h_acs.clear();
+  p->h_cls_slots.clear();
   p->h_items.clear();
   p->h_rows.clear();
   p->classes.clear();
@@ -253,14 +286,34 @@ static int pool_rebuild(aco_pool* p) {
     for (int s : by_class[key])
       for (int k = 0; k < p->slots[(size_t)s].m; ++k) p->h_items.push_back(make_int2(s, k));
     c.count = (int)p->h_items.size() - c.begin;
+    c.slot_begin = (int)p->h_cls_slots.size();
+    c.row_begin = (int)p->h_rows.size();
+    c.max_ld = 4;
+    for (int s : by_class[key]) {
+      const PoolSlot& sl = p->slots[(size_t)s];
+      p->h_cls_slots.push_back(s);
+      c.max_ld = std::max(c.max_ld, sl.I.ld);
+      for (int i = 0; i < sl.n; ++i) p->h_rows.push_back(make_int2(s, i));
+    }
+    c.slot_count = (int)p->h_cls_slots.size() - c.slot_begin;
+    c.row_count = (int)p->h_rows.size() - c.row_begin;
+    p->max_ld = std::max(p->max_ld, c.max_ld);
+    c.k = 1;
     p->classes.push_back(c);
   }
-  for (int s : live) {
-    const PoolSlot& sl = p->slots[(size_t)s];
-    if (sl.I.variant == kVariantAcs) continue;
-    p->max_ld = std::max(p->max_ld, sl.I.ld);
-    for (int i = 0; i < sl.n; ++i) p->h_rows.push_back(make_int2(s, i));
+  // iterations per step of each group (1 unless multi-rate stepping is on)
+  double t_max = p->h_acs.empty() ? 0.0 : iteration_time_model(p->acs_max_n, true);
+  for (const auto& c : p->classes) t_max = std::max(t_max, iteration_time_model(c.max_n, false));
+  for (auto& c : p->classes) {
+    c.k = group_rate(p, p->h_cls_slots.data() + c.slot_begin, c.slot_count,
+                     iteration_time_model(c.max_n, false), t_max);
+    for (int i = 0; i < c.slot_count; ++i)
+      p->slots[(size_t)p->h_cls_slots[(size_t)(c.slot_begin + i)]].rate = c.k;
   }
+  p->acs_k = p->h_acs.empty() ? 1
+                              : group_rate(p, p->h_acs.data(), (int)p->h_acs.size(),
+                                           iteration_time_model(p->acs_max_n, true), t_max);
+  for (int s : p->h_acs) p->slots[(size_t)s].rate = p->acs_k;
   int rc = ensure_capacity((void**)&p->d_items, &p->items_cap, p->h_items.size(), sizeof(int2));
   if (!rc) rc = ensure_capacity((void**)&p->d_rows, &p->rows_cap, p->h_rows.size(), sizeof(int2));
   if (rc) return rc;
@@ -276,6 +329,9 @@ static int pool_rebuild(aco_pool* p) {
                         cudaMemcpyHostToDevice, p->stream);
   if (e == cudaSuccess && !p->h_acs.empty())
     e = cudaMemcpyAsync(p->d_acs, p->h_acs.data(), p->h_acs.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess && !p->h_cls_slots.empty())
+    e = cudaMemcpyAsync(p->d_cls_slots, p->h_cls_slots.data(), p->h_cls_slots.size() * sizeof(int),
                         cudaMemcpyHostToDevice, p->stream);
   // The host vectors must outlive the copies: synchronise before they change.
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
@@ -358,8 +414,11 @@ static int pool_enqueue_step(aco_pool* p) {
   cudaError_t e;
   int launches = 0;
   // Fork: every tiling class, and the Ant Colony System colonies, get their
-  // own stream so that the tail of one overlaps the others; join before the
-  // best/update launches.
+  // own stream so that the tail of one overlaps the others.  One iteration
+  // per step: join before the best/update launches, which cover all slots.
+  // Multi-rate: each group runs its k iterations (construct, best, update)
+  // on its own stream, and the streams join at the end.
+  const bool mr = p->multirate;
   const int ncls = (int)p->classes.size();
   const int nacs = (int)p->h_acs.size();
   const int nstreams = std::min(ncls + (nacs > 0 ? 1 : 0), (int)aco_pool::kClassStreams);
@@ -372,16 +431,34 @@ static int pool_enqueue_step(aco_pool* p) {
   const int first = nacs > 0 ? 1 : 0;
   if (nacs > 0) {
     cudaStream_t st = nstreams > 1 ? p->class_stream[0] : p->stream;
-    e = launch_acs_construct_slots(p->d_inst, p->d_acs, nacs, p->acs_max_m, p->acs_max_n, st);
-    if (e != cudaSuccess) return cuda_fail(e, "pool acs construct");
-    ++launches;
+    for (int r = 0; r < (mr ? p->acs_k : 1); ++r) {
+      e = launch_acs_construct_slots(p->d_inst, p->d_acs, nacs, p->acs_max_m, p->acs_max_n, st);
+      if (e != cudaSuccess) return cuda_fail(e, "pool acs construct");
+      ++launches;
+      if (!mr) break;
+      if ((e = launch_best_slots(p->d_inst, p->d_acs, nacs, st)) != cudaSuccess)
+        return cuda_fail(e, "pool acs best");
+      if ((e = launch_acs_global_slots(p->d_inst, p->d_acs, nacs, st)) != cudaSuccess)
+        return cuda_fail(e, "pool acs update");
+      launches += 2;
+    }
   }
   for (int ci = 0; ci < ncls; ++ci) {
     const auto& c = p->classes[(size_t)ci];
     cudaStream_t st = nstreams > 1 ? p->class_stream[(ci + first) % nstreams] : p->stream;
-    e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, st);
-    if (e != cudaSuccess) return cuda_fail(e, "pool construct");
-    ++launches;
+    for (int r = 0; r < (mr ? c.k : 1); ++r) {
+      e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, st);
+      if (e != cudaSuccess) return cuda_fail(e, "pool construct");
+      ++launches;
+      if (!mr) break;
+      if ((e = launch_best_slots(p->d_inst, p->d_cls_slots + c.slot_begin, c.slot_count, st)) !=
+          cudaSuccess)
+        return cuda_fail(e, "pool best");
+      if ((e = launch_update_rows(p->d_inst, p->d_rows + c.row_begin, c.row_count, c.max_ld,
+                                  st)) != cudaSuccess)
+        return cuda_fail(e, "pool update");
+      launches += 2;
+    }
   }
   for (int i = 0; i < nstreams && nstreams > 1; ++i) {
     if ((e = cudaEventRecord(p->join_ev[i], p->class_stream[i])) != cudaSuccess)
@@ -389,17 +466,19 @@ static int pool_enqueue_step(aco_pool* p) {
     if ((e = cudaStreamWaitEvent(p->stream, p->join_ev[i], 0)) != cudaSuccess)
       return cuda_fail(e, "pool join wait");
   }
-  if ((e = launch_best_slots(p->d_inst, p->d_live, (int)p->h_live.size(), p->stream)) !=
-      cudaSuccess)
-    return cuda_fail(e, "pool best");
-  ++launches;
-  if ((e = launch_update_rows(p->d_inst, p->d_rows, (int)p->h_rows.size(), p->max_ld,
-                              p->stream)) != cudaSuccess)
-    return cuda_fail(e, "pool update");
-  launches += p->h_rows.empty() ? 0 : 1;
-  if ((e = launch_acs_global_slots(p->d_inst, p->d_acs, nacs, p->stream)) != cudaSuccess)
-    return cuda_fail(e, "pool acs update");
-  launches += nacs > 0 ? 1 : 0;
+  if (!mr) {
+    if ((e = launch_best_slots(p->d_inst, p->d_live, (int)p->h_live.size(), p->stream)) !=
+        cudaSuccess)
+      return cuda_fail(e, "pool best");
+    ++launches;
+    if ((e = launch_update_rows(p->d_inst, p->d_rows, (int)p->h_rows.size(), p->max_ld,
+                                p->stream)) != cudaSuccess)
+      return cuda_fail(e, "pool update");
+    launches += p->h_rows.empty() ? 0 : 1;
+    if ((e = launch_acs_global_slots(p->d_inst, p->d_acs, nacs, p->stream)) != cudaSuccess)
+      return cuda_fail(e, "pool acs update");
+    launches += nacs > 0 ? 1 : 0;
+  }
   p->launches = launches;
   return ACO_OK;
 }
@@ -573,6 +652,7 @@ int aco_pool_create(int32_t max_slots, uint64_t budget_bytes, aco_pool_handle* o
     if ((e = cudaMalloc(&p->d_inst, sizeof(Instance) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->d_live, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->d_acs, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&p->d_cls_slots, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess) break;
     for (int i = 0; i < aco_pool::kClassStreams && e == cudaSuccess; ++i) {
       e = cudaStreamCreateWithFlags(&p->class_stream[i], cudaStreamNonBlocking);
@@ -600,6 +680,7 @@ int aco_pool_destroy(aco_pool_handle p) {
   if (p->d_inst) cudaFree(p->d_inst);
   if (p->d_live) cudaFree(p->d_live);
   if (p->d_acs) cudaFree(p->d_acs);
+  if (p->d_cls_slots) cudaFree(p->d_cls_slots);
   if (p->d_items) cudaFree(p->d_items);
   if (p->d_rows) cudaFree(p->d_rows);
   for (int i = 0; i < aco_pool::kClassStreams; ++i) {
@@ -687,11 +768,16 @@ int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
     for (int s : p->h_live) {
       PoolSlot& sl = p->slots[(size_t)s];
       sl.started = true;
-      if (sl.iters_left > 0 && --sl.iters_left == 0) {
-        sl.live = false;
-        sl.finished = true;
-        p->finished_order.push_back(s);
-        p->dirty = true;
+      if (sl.iters_left > 0) {
+        sl.iters_left -= sl.rate;  // rate <= iters_left by construction
+        if (sl.iters_left == 0) {
+          sl.live = false;
+          sl.finished = true;
+          p->finished_order.push_back(s);
+          p->dirty = true;
+        } else if (sl.iters_left < sl.rate) {
+          p->dirty = true;  // the group's rate must shrink to the budget left
+        }
       }
     }
   } else {
@@ -726,6 +812,28 @@ int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t* tour, int64_t* len
     e = cudaMemcpyAsync(len, &sl.I.st->best_len, 8, cudaMemcpyDeviceToHost, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "pool result");
   return pool_check_status(p, slot);
+}
+
+int aco_pool_set_multirate(aco_pool_handle p, int32_t on) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (on != 0 && on != 1) return fail(ACO_EINVAL, "on must be 0 or 1");
+  if (on && p->unlimited)
+    return fail(ACO_EINVAL, "a static batch steps one iteration per aco_batch_iterate step");
+  if (p->multirate != (on != 0)) {
+    p->multirate = on != 0;
+    p->dirty = true;
+  }
+  return ACO_OK;
+}
+
+int aco_pool_rate(aco_pool_handle p, int32_t slot, int32_t* iterations_per_step) {
+  if (!p || !iterations_per_step) return fail(ACO_EINVAL, "NULL argument");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].used)
+    return fail(ACO_EINVAL, "slot %d is not in use", slot);
+  if (!p->slots[(size_t)slot].started)
+    return fail(ACO_ESTATE, "slot %d has not taken part in a step yet", slot);
+  *iterations_per_step = p->slots[(size_t)slot].rate;
+  return ACO_OK;
 }
 
 int aco_pool_set_autotune(aco_pool_handle p, int32_t on) {

@@ -70,11 +70,16 @@ class Server:
     the candidate evaluations one step may contain (the sum of step_work over
     live requests): a larger batch raises throughput but every live request
     waits for the whole step, so the bound trades throughput for latency.  A
-    request larger than the bound is admitted alone."""
+    request larger than the bound is admitted alone.  With `multirate`, each
+    step runs several iterations of the shorter requests, so they no longer
+    wait one step of the longest request per iteration."""
 
     def __init__(self, budget_bytes: int = 64 << 30, max_slots: int = 2048,
-                 max_step_work: int = 20_000_000_000):
+                 max_step_work: int = 20_000_000_000, multirate: bool = False):
         self.pool = aco.aco_pool_create(max_slots, budget_bytes)
+        if multirate:
+            # short requests run several iterations per step (aco_pool_set_multirate)
+            aco.aco_pool_set_multirate(self.pool, True)
         self.budget = budget_bytes
         self.max_slots = max_slots
         self.max_step_work = max_step_work

@@ -268,3 +268,89 @@ def test_server_mixes_all_three_rules(aco, orc):
                 aco.aco_iterate(c.h, r.iterations)
                 tour, length = aco.aco_best_tour(c.h, r.n)
             assert o.best_len == length and np.array_equal(o.best_tour, tour), o.index
+
+
+def test_multirate_steps_keep_every_result(aco, orc):
+    # One long instance (n = 1000) beside short ones of all three rules:
+    # with multi-rate stepping the short groups run several iterations per
+    # step, finish in fewer steps, and every slot still equals its run alone.
+    big = I.uniform_instance(1000, 1000, seed=4100)
+    small = [(60, "as", 60, 31, 30), (48, "mmas", 48, 32, 25), (90, "acs", 10, 33, 20),
+             (130, "as", 64, 34, 12)]
+    insts = {n: I.uniform_instance(n, 1000, seed=4100 + n) for n, *_r in small}
+    need = aco.aco_pool_bytes_needed(1000, 256) + sum(
+        aco.aco_pool_bytes_needed(n, m) for n, _v, m, *_r in small)
+    p = aco.aco_pool_create(8, need + (1 << 20))
+    try:
+        aco.aco_pool_set_multirate(p, True)
+        sb = aco.aco_pool_admit(p, big.dist, 1.0, 2.0, 0.5, 256, 30, 4)
+        slots = {}
+        for n, variant, m, seed, iters in small:
+            if variant == "acs":
+                slots[n] = aco.aco_pool_admit_acs(p, insts[n].dist, 1.0, 2.0, 0.1, m, seed,
+                                                  iters, 0.9, 0.1)
+            elif variant == "mmas":
+                slots[n] = aco.aco_pool_admit_mmas(p, insts[n].dist, 1.0, 2.0, 0.02, m, seed,
+                                                   iters, 0.05, False)
+            else:
+                slots[n] = aco.aco_pool_admit(p, insts[n].dist, 1.0, 2.0, 0.5, m, seed, iters)
+        steps = 0
+        aco.aco_pool_step(p)
+        steps += 1
+        rates = {n: aco.aco_pool_rate(p, s) for n, s in slots.items()}
+        assert aco.aco_pool_rate(p, sb) == 1
+        assert all(k > 1 for k in rates.values()), rates
+        while aco.aco_pool_step(p) > 0:
+            steps += 1
+        steps += 1
+        # one iteration per step would take 30 steps (the longest budget);
+        # the colony group runs 3 per step beside the long instance and one
+        # per step once it is alone
+        assert steps < 20, steps
+        aco.aco_pool_synchronize(p)
+        for n, variant, m, seed, iters in small:
+            d = insts[n].dist
+            if variant == "acs":
+                ref = orc.run_acs(d, m, iters, seed, rho=0.1, q0=0.9, xi=0.1)
+            elif variant == "mmas":
+                ref = orc.run_mmas(d, m, iters, seed, rho=0.02, p_best=0.05)
+            else:
+                ref = orc.run(d, m, iters, seed)
+            assert np.array_equal(aco.aco_pool_pheromone(p, slots[n], n), ref["tau32"]), n
+            assert aco.aco_pool_result(p, slots[n], n)[1] == ref["best_len"], n
+        tau_a, (tour_a, len_a) = as_alone(aco, big.dist, 256, 30, 4)
+        assert np.array_equal(aco.aco_pool_pheromone(p, sb, 1000), tau_a)
+        assert aco.aco_pool_result(p, sb, 1000)[1] == len_a
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+def test_multirate_rate_never_exceeds_the_budget_left(aco, orc):
+    # a short instance with 5 iterations beside a long one: its rate is
+    # capped at 5, so it finishes after one step and runs exactly 5
+    big = I.uniform_instance(700, 1000, seed=4200)
+    x = I.uniform_instance(40, 1000, seed=4201)
+    p = aco.aco_pool_create(4, aco.aco_pool_bytes_needed(700, 128) +
+                            aco.aco_pool_bytes_needed(40, 40) + (1 << 20))
+    try:
+        aco.aco_pool_set_multirate(p, True)
+        aco.aco_pool_admit(p, big.dist, 1.0, 2.0, 0.5, 128, 1, 3)
+        s = aco.aco_pool_admit(p, x.dist, 1.0, 2.0, 0.5, 40, 2, 5)
+        aco.aco_pool_step(p)
+        assert aco.aco_pool_finished(p) == [s]
+        ref = orc.run(x.dist, 40, 5, 2)
+        assert np.array_equal(aco.aco_pool_pheromone(p, s, 40), ref["tau32"])
+        assert aco.aco_pool_rate(p, s) == 5
+        s2 = aco.aco_pool_admit(p, x.dist, 1.0, 2.0, 0.5, 40, 3, 2)
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_rate(p, s2)  # no step yet
+        assert e.value.code == aco.ACO_ESTATE
+    finally:
+        aco.aco_pool_destroy(p)
+    b = aco.aco_batch_create([x.dist], [40], [2])
+    try:
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_set_multirate(b, True)
+        assert e.value.code == aco.ACO_EINVAL
+    finally:
+        aco.aco_batch_destroy(b)
