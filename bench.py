@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson arrival window for --workload served")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-step-work", type=float, default=1e11,
+                    help="served: candidate evaluations one step may hold (admission bound)")
     ap.add_argument("--no-multirate", action="store_true",
                     help="served: one iteration per step for every request (no multi-rate "
                          "stepping)")
@@ -741,10 +743,13 @@ def run_served(args, rank, world, local):
         q = instances.served_request(r)
         reqs.append(serve.Request(q["inst"].coords, q["m"], q["iterations"], q["seed"]))
     mr = not args.no_multirate
-    with serve.Server(budget_bytes=64 << 30, max_slots=4096, multirate=mr) as srv:
+    work = int(args.serve_step_work)
+    with serve.Server(budget_bytes=64 << 30, max_slots=4096, multirate=mr,
+                      max_step_work=work) as srv:
         # configured stream: stop admitting/stepping at the end of the arrival window
         outs, st = srv.run(reqs, arrivals, deadline=args.serve_seconds)
-    with serve.Server(budget_bytes=64 << 30, max_slots=4096, multirate=mr) as srv:
+    with serve.Server(budget_bytes=64 << 30, max_slots=4096, multirate=mr,
+                      max_step_work=work) as srv:
         # sustainable stream at 0.7x the measured completion rate
         cap = max(st["solves_per_s"], 0.5)
         rate = 0.7 * cap
@@ -763,10 +768,20 @@ def run_served(args, rank, world, local):
         loop_lens.append(aco.aco_best_tour(h, r.n)[1])
         aco.aco_destroy(h)
     t_loop = time.perf_counter() - t0
-    with serve.Server(budget_bytes=64 << 30, max_slots=4096, max_step_work=1 << 62,
-                      multirate=mr) as srv:
-        outs3, st3 = srv.run(sample, np.zeros(len(sample)), realtime=False)
-    same = sorted((o.index, o.best_len) for o in outs3) == list(enumerate(loop_lens))
+    loop = None
+    if sample:
+        with serve.Server(budget_bytes=64 << 30, max_slots=4096, max_step_work=1 << 62,
+                          multirate=mr) as srv:
+            outs3, st3 = srv.run(sample, np.zeros(len(sample)), realtime=False)
+        same = sorted((o.index, o.best_len) for o in outs3) == list(enumerate(loop_lens))
+        loop = {
+            "requests": len(sample), "per_request_loop_solves_per_s": len(sample) / t_loop,
+            "server_solves_per_s": st3["solves_per_s"],
+            "speedup_vs_loop": st3["solves_per_s"] * t_loop / len(sample),
+            "identical_best_lengths": same,
+            "what": "the first requests of the stream solved one at a time (aco_create_coords "
+                    "+ aco_iterate(200) + aco_best_tour) vs the server with all of them "
+                    "admitted at once"}
     if rank != 0:
         return
     line = {
@@ -776,17 +791,10 @@ def run_served(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "as-served-poisson", "rate_per_s": args.serve_rate,
                    "window_s": args.serve_seconds, "budget_gb": 64, "iterations": 200,
-                   "multirate": mr},
+                   "multirate": mr, "max_step_work": work},
         "configured_stream": st,
         "sustainable_stream": dict(st2, rate_per_s=rate),
-        "loop_comparison": {
-            "requests": len(sample), "per_request_loop_solves_per_s": len(sample) / t_loop,
-            "server_solves_per_s": st3["solves_per_s"],
-            "speedup_vs_loop": st3["solves_per_s"] * t_loop / len(sample),
-            "identical_best_lengths": same,
-            "what": "the first requests of the stream solved one at a time (aco_create_coords "
-                    "+ aco_iterate(200) + aco_best_tour) vs the server with all of them "
-                    "admitted at once"},
+        "loop_comparison": loop,
     }
     print(json.dumps(line), flush=True)
 
