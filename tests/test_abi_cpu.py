@@ -102,10 +102,17 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.aco_pool_set_tuning(None, None, 0) == aco.ACO_EINVAL
     assert lib.aco_pool_set_acs(None, 0, 0.9, 0.1) == aco.ACO_EINVAL
     assert lib.aco_pool_set_mmas(None, 0, 0.05, 0) == aco.ACO_EINVAL
+    assert lib.aco_pool_set_multirate(None, 1) == aco.ACO_EINVAL
+    k = C.c_int32()
+    assert lib.aco_pool_rate(None, 0, C.byref(k)) == aco.ACO_EINVAL
 
 
 def test_selftest_rejects_bad_arguments_before_touching_the_gpu(lib):
     from paper_1101_2678_gb300 import aco
+    x = np.zeros(4, np.uint32)
+    out = np.zeros(4, np.float32)
+    assert lib.aco_race_exponential(None, out.ctypes.data, 4) == aco.ACO_EINVAL
+    assert lib.aco_race_exponential(x.ctypes.data, out.ctypes.data, 0) == aco.ACO_EINVAL
     assert lib.aco_selftest_bounded_wait(0, 1) == aco.ACO_EINVAL
     assert lib.aco_selftest_bounded_wait((1 << 20) + 1, 1) == aco.ACO_EINVAL
     assert lib.aco_selftest_bounded_wait(100, 2) == aco.ACO_EINVAL
