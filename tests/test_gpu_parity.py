@@ -486,7 +486,8 @@ def test_race_full_size_sampled(aco, orc):
 # Nearest-neighbour-list construction (optional, ACO_OPT_NN_LIST)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n,nn,m", [(10, 9, 12), (48, 8, 48), (300, 30, 64), (333, 1, 20)])
+@pytest.mark.parametrize("n,nn,m", [(10, 9, 12), (48, 8, 48), (300, 30, 64), (333, 1, 20),
+                                    (1500, 30, 40), (2000, 32, 24)])
 def test_nn_list_tours_match_oracle(aco, orc, n, nn, m):
     inst = I.clustered_instance(n, seed=n + nn, clusters=6, side=4000)
     ch = oracle_initial_choice(orc, inst.dist, m)
