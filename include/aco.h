@@ -468,7 +468,8 @@ int aco_pool_stats(aco_pool_handle p, int32_t *live, int32_t *finished, uint64_t
  */
 int aco_pool_set_autotune(aco_pool_handle p, int32_t on);
 /*
- * aco_pool_set_multirate - on = 1: every aco_pool_step runs k iterations for
+ * aco_pool_set_multirate (no counterpart in the paper: a serving extension
+ * of the batched step) - on = 1: every aco_pool_step runs k iterations for
  * each group of slots (a construction class, or all Ant Colony System
  * colonies), each group on its own stream with its own best and update
  * launches, where k = floor(T_max / T_group) within [1, 64] from a model of
@@ -585,8 +586,10 @@ int aco_selftest_bounded_wait(int32_t polls, int32_t complete);
 int aco_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int32_t count);
 
 /*
- * aco_race_exponential - the exponential race's variate (ACO_SELECT_EXP_RACE)
- * as the construction kernels compute it, on the GPU: out[i] = E for the
+ * aco_race_exponential - the exponential race's variate (ACO_SELECT_EXP_RACE,
+ * a per-candidate rule that samples Eq. 1 of Section II; no counterpart in
+ * the paper's kernels) as the construction kernels compute it, on the GPU:
+ * out[i] = E for the
  * Philox word x[i], E = -ln(v 2^-24), v = floor(x[i] / 2^8) + 1, in single
  * precision by the range-reduced inverse-hyperbolic-tangent series.  x and
  * out are host arrays of `count` entries, 1 <= count <= 2^24; ACO_EINVAL on
