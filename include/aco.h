@@ -589,11 +589,10 @@ int aco_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, i
  * aco_race_exponential - the exponential race's variate (ACO_SELECT_EXP_RACE,
  * a per-candidate rule that samples Eq. 1 of Section II; no counterpart in
  * the paper's kernels) as the construction kernels compute it, on the GPU:
- * out[i] = E for the
- * Philox word x[i], E = -ln(v 2^-24), v = floor(x[i] / 2^8) + 1, in single
- * precision by the range-reduced inverse-hyperbolic-tangent series.  x and
- * out are host arrays of `count` entries, 1 <= count <= 2^24; ACO_EINVAL on
- * NULL pointers.
+ * out[i] = E for the Philox word x[i], E = -ln(v 2^-24), v = floor(x[i] /
+ * 2^8) + 1, in single precision by the range-reduced inverse-hyperbolic-
+ * tangent series.  x and out are host arrays of `count` entries,
+ * 1 <= count <= 2^24; ACO_EINVAL on NULL pointers.
  */
 int aco_race_exponential(const uint32_t *x, float *out, int32_t count);
 
