@@ -414,6 +414,24 @@ int aco_pool_set_acs(aco_pool_handle p, int32_t slot, double q0, float xi);
 int aco_pool_set_mmas(aco_pool_handle p, int32_t slot, double p_best, int32_t best_so_far);
 
 /*
+ * aco_pool_save_slot / aco_pool_restore_slot - checkpoints of pool slots, in
+ * the format of aco_save_state (library feature; the paper has no
+ * counterpart).  A blob from either side restores into the other.
+ *   aco_pool_save_slot: *size = bytes of the checkpoint of slot (live or
+ *     finished); with buf != NULL and capacity >= *size it is written to buf
+ *     (host memory).  Synchronises the pool.
+ *   aco_pool_restore_slot: load a checkpoint into a live slot admitted with
+ *     the same n, distances, alpha, beta, rho, m and seed, before its first
+ *     step and rule switch (ACO_ESTATE otherwise); the slot takes the
+ *     checkpoint's update rule and iteration counter, and its own admitted
+ *     iteration budget counts from there.  choice_info is recomputed from
+ *     tau.  ACO_EINVAL on a mismatch, a truncated or foreign buffer.
+ */
+int aco_pool_save_slot(aco_pool_handle p, int32_t slot, void *buf, uint64_t capacity,
+                       uint64_t *size);
+int aco_pool_restore_slot(aco_pool_handle p, int32_t slot, const void *buf, uint64_t size);
+
+/*
  * aco_pool_step - one iteration for every live slot (asynchronous; with
  * multi-rate stepping, each slot's own rate).  A slot whose iteration budget
  * is used up becomes finished and leaves the live set.

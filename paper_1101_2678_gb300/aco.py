@@ -98,6 +98,8 @@ SIGNATURES = [
     ("aco_pool_set_mmas", C.c_int, [_vp, C.c_int32, C.c_double, C.c_int32]),
     ("aco_pool_set_multirate", C.c_int, [_vp, C.c_int32]),
     ("aco_pool_rate", C.c_int, [_vp, C.c_int32, _i32p]),
+    ("aco_pool_save_slot", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64, C.POINTER(C.c_uint64)]),
+    ("aco_pool_restore_slot", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64]),
     ("aco_pool_step", C.c_int, [_vp, _i32p]),
     ("aco_pool_finished", C.c_int, [_vp, _vp, C.c_int32, _i32p]),
     ("aco_pool_result", C.c_int, [_vp, C.c_int32, _vp, _vp]),
@@ -349,6 +351,22 @@ def aco_pool_admit(p, dist, alpha, beta, rho, m, seed, iterations):
     _check(load().aco_pool_admit(p, d.shape[0], _ptr(d), alpha, beta, rho, m, seed, iterations,
                                  C.byref(slot)), "aco_pool_admit")
     return slot.value
+
+
+def aco_pool_save_slot(p, slot: int) -> bytes:
+    """A checkpoint of a pool slot (the format of aco_save_state)."""
+    size = C.c_uint64()
+    _check(load().aco_pool_save_slot(p, slot, None, 0, C.byref(size)), "aco_pool_save_slot")
+    buf = np.empty(size.value, np.uint8)
+    _check(load().aco_pool_save_slot(p, slot, _ptr(buf), size.value, C.byref(size)),
+           "aco_pool_save_slot")
+    return buf.tobytes()
+
+
+def aco_pool_restore_slot(p, slot: int, blob: bytes) -> None:
+    """Load a checkpoint into a freshly admitted slot of the same instance."""
+    buf = np.frombuffer(blob, np.uint8)
+    _check(load().aco_pool_restore_slot(p, slot, _ptr(buf), buf.size), "aco_pool_restore_slot")
 
 
 def aco_pool_set_multirate(p, on: bool) -> None:

@@ -10,6 +10,7 @@
 #include "aco_device.cuh"
 #include "kernels.h"
 #include "runtime.h"
+#include "checkpoint.h"
 
 namespace aco {
 
@@ -629,30 +630,6 @@ int aco_set_acs(aco_handle h, double q0, float xi) {
   return check_status(h);
 }
 
-// Checkpoint blob: header, the device iteration state, tau (n*n, unpadded)
-// and the best-so-far tour (n+1).  The instance itself (distances, eta^beta,
-// nearest-neighbour lists) is not stored: it is rebuilt by creating the
-// handle again with the same arguments, which the header checks.
-struct CheckpointHeader {
-  uint32_t magic, version;
-  int32_t n, m;
-  float alpha, beta, rho;
-  int32_t variant, mmas_best_so_far;
-  double mmas_f;
-  unsigned long long acs_threshold;
-  float acs_xi;
-  int32_t constructed;
-  unsigned long long seed;
-  long long host_iteration;
-  uint32_t state_bytes, reserved;
-};
-static constexpr uint32_t kCheckpointMagic = 0x31434f41u;  // "ACO1"
-
-static uint64_t checkpoint_bytes(int n) {
-  return sizeof(CheckpointHeader) + sizeof(IterState) + (uint64_t)n * n * 4 +
-         ((uint64_t)n + 1) * 4;
-}
-
 int aco_save_state(aco_handle h, void* buf, uint64_t capacity, uint64_t* size) {
   NvtxRange nvtx_range("aco_save_state");
   if (!h || !size) return fail(ACO_EINVAL, "NULL argument");
@@ -661,23 +638,9 @@ int aco_save_state(aco_handle h, void* buf, uint64_t capacity, uint64_t* size) {
   if (!buf) return ACO_OK;
   if (capacity < *size) return fail(ACO_EINVAL, "buffer holds %llu bytes, %llu needed",
                                     (unsigned long long)capacity, (unsigned long long)*size);
-  CheckpointHeader hd{};
-  hd.magic = kCheckpointMagic;
-  hd.version = 1;
-  hd.n = n;
-  hd.m = h->I.m;
-  hd.alpha = h->I.alpha;
-  hd.beta = h->I.beta;
-  hd.rho = h->I.rho;
-  hd.variant = h->I.variant;
-  hd.mmas_best_so_far = h->I.mmas_best_so_far;
-  hd.mmas_f = h->I.mmas_f;
-  hd.acs_threshold = h->I.acs_threshold;
-  hd.acs_xi = h->I.acs_xi;
+  CheckpointHeader hd = checkpoint_header(h->I);
   hd.constructed = h->constructed ? 1 : 0;
-  hd.seed = h->I.seed;
   hd.host_iteration = h->host_iteration;
-  hd.state_bytes = (uint32_t)sizeof(IterState);
   char* b = static_cast<char*>(buf);
   std::memcpy(b, &hd, sizeof hd);
   char* st = b + sizeof hd;
@@ -699,28 +662,14 @@ int aco_restore_state(aco_handle h, const void* buf, uint64_t size) {
   NvtxRange nvtx_range("aco_restore_state");
   if (!h || !buf) return fail(ACO_EINVAL, "NULL argument");
   CheckpointHeader hd{};
-  if (size < sizeof hd) return fail(ACO_EINVAL, "checkpoint too short");
-  std::memcpy(&hd, buf, sizeof hd);
-  if (hd.magic != kCheckpointMagic || hd.version != 1 || hd.state_bytes != sizeof(IterState))
-    return fail(ACO_EINVAL, "not a checkpoint of this library");
-  if (hd.n != h->I.n || hd.m != h->I.m || hd.seed != h->I.seed || hd.alpha != h->I.alpha ||
-      hd.beta != h->I.beta || hd.rho != h->I.rho)
-    return fail(ACO_EINVAL, "the checkpoint is of another instance (n, m, seed or parameters)");
-  if (size < checkpoint_bytes(hd.n)) return fail(ACO_EINVAL, "checkpoint truncated");
-  if (hd.variant < kVariantAs || hd.variant > kVariantAcs)
-    return fail(ACO_EINVAL, "checkpoint names an unknown update rule");
+  IterState st{};
+  const float* tau = nullptr;
+  const int32_t* best = nullptr;
+  int rc = checkpoint_parse(h->I, buf, size, hd, st, tau, best);
+  if (rc) return rc;
   if (hd.variant == kVariantAcs && (h->I.nn > 0 || h->I.rule != 0 || h->I.m > kAcsMaxAnts))
     return fail(ACO_EINVAL, "the Ant Colony System uses its own construction");
   const int n = hd.n;
-  const char* b = static_cast<const char*>(buf);
-  IterState st{};
-  std::memcpy(&st, b + sizeof hd, sizeof st);
-  if (st.status != 0) return fail(ACO_EINVAL, "the checkpoint records a device error");
-  const float* tau = reinterpret_cast<const float*>(b + sizeof hd + sizeof st);
-  const int32_t* best = reinterpret_cast<const int32_t*>(b + sizeof hd + sizeof st + (size_t)n * n * 4);
-  if (hd.constructed)
-    for (int i = 0; i <= n; ++i)
-      if (best[i] < 0 || best[i] >= n) return fail(ACO_EINVAL, "checkpoint tour out of range");
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->I.st, &st, sizeof st, cudaMemcpyHostToDevice, h->stream);

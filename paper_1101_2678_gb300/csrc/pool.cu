@@ -23,6 +23,7 @@
 #include "aco_device.cuh"
 #include "kernels.h"
 #include "runtime.h"
+#include "checkpoint.h"
 
 namespace aco {
 
@@ -94,6 +95,7 @@ struct PoolSlot {
   cudaEvent_t ready = nullptr;  // setup done on the side stream
   bool wait_ready = false;
   bool started = false;  // taken part in a step (the update rule is then fixed)
+  bool restored = false; // state loaded from a checkpoint (rule fixed as well)
   int rate = 1;          // iterations per step (multi-rate stepping)
 };
 
@@ -619,7 +621,7 @@ static int pool_rule_slot_check(aco_pool* p, int32_t slot) {
   if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
     return fail(ACO_EINVAL, "slot %d is not live", slot);
   const PoolSlot& sl = p->slots[(size_t)slot];
-  if (sl.started || sl.I.variant != kVariantAs)
+  if (sl.started || sl.restored || sl.I.variant != kVariantAs)
     return fail(ACO_ESTATE, "the update rule is chosen once, before the slot's first step");
   return ACO_OK;
 }
@@ -812,6 +814,89 @@ int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t* tour, int64_t* len
     e = cudaMemcpyAsync(len, &sl.I.st->best_len, 8, cudaMemcpyDeviceToHost, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "pool result");
   return pool_check_status(p, slot);
+}
+
+int aco_pool_save_slot(aco_pool_handle p, int32_t slot, void* buf, uint64_t capacity,
+                       uint64_t* size) {
+  NvtxRange nvtx_range("aco_pool_save_slot");
+  if (!p || !size) return fail(ACO_EINVAL, "NULL argument");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].used)
+    return fail(ACO_EINVAL, "slot %d is not in use", slot);
+  const PoolSlot& sl = p->slots[(size_t)slot];
+  const int n = sl.n;
+  *size = checkpoint_bytes(n);
+  if (!buf) return ACO_OK;
+  if (capacity < *size) return fail(ACO_EINVAL, "buffer holds %llu bytes, %llu needed",
+                                    (unsigned long long)capacity, (unsigned long long)*size);
+  char* b = static_cast<char*>(buf);
+  char* stp = b + sizeof(CheckpointHeader);
+  float* tau = reinterpret_cast<float*>(stp + sizeof(IterState));
+  int32_t* best = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(tau) + (size_t)n * n * 4);
+  // the slot's steps and setup first
+  cudaError_t e = cudaStreamSynchronize(p->side);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(stp, sl.I.st, sizeof(IterState), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(tau, (size_t)n * 4, sl.I.tau, (size_t)sl.I.ld * 4, (size_t)n * 4,
+                          (size_t)n, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(best, sl.I.best_tour, ((size_t)n + 1) * 4, cudaMemcpyDeviceToHost,
+                        p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pool save slot");
+  IterState st{};
+  std::memcpy(&st, stp, sizeof st);
+  if (st.status & kStatusTimeout) return fail(ACO_ETIMEOUT, "a device-side wait gave up");
+  if (st.status) return fail(ACO_ECUDA, "device status 0x%x in slot %d", st.status, slot);
+  CheckpointHeader hd = checkpoint_header(sl.I);
+  hd.constructed = st.iteration > 0 ? 1 : 0;
+  hd.host_iteration = (long long)st.iteration;
+  std::memcpy(b, &hd, sizeof hd);
+  return ACO_OK;
+}
+
+int aco_pool_restore_slot(aco_pool_handle p, int32_t slot, const void* buf, uint64_t size) {
+  NvtxRange nvtx_range("aco_pool_restore_slot");
+  if (!p || !buf) return fail(ACO_EINVAL, "NULL argument");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
+    return fail(ACO_EINVAL, "slot %d is not live", slot);
+  PoolSlot& sl = p->slots[(size_t)slot];
+  if (sl.started || sl.restored)
+    return fail(ACO_ESTATE, "a slot takes a checkpoint once, before its first step");
+  CheckpointHeader hd{};
+  IterState st{};
+  const float* tau = nullptr;
+  const int32_t* best = nullptr;
+  int rc = checkpoint_parse(sl.I, buf, size, hd, st, tau, best);
+  if (rc) return rc;
+  if (hd.variant == kVariantAcs && sl.m > kAcsMaxAnts)
+    return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants", kAcsMaxAnts);
+  Instance& I = sl.I;
+  I.variant = hd.variant;
+  I.mmas_best_so_far = hd.mmas_best_so_far;
+  I.mmas_f = hd.mmas_f;
+  I.acs_threshold = hd.acs_threshold;
+  I.acs_xi = hd.acs_xi;
+  const int n = I.n;
+  // On the side stream after the admission's setup: the state, tau and best
+  // tour, the descriptor with the rule, then choice_info from tau.  The
+  // sources are the caller's buffer and locals: synchronise before returning.
+  cudaError_t e = cudaMemcpyAsync(I.st, &st, sizeof st, cudaMemcpyHostToDevice, p->side);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(I.tau, (size_t)I.ld * 4, tau, (size_t)n * 4, (size_t)n * 4, (size_t)n,
+                          cudaMemcpyHostToDevice, p->side);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(I.best_tour, best, ((size_t)n + 1) * 4, cudaMemcpyHostToDevice, p->side);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_inst + slot, &I, sizeof I, cudaMemcpyHostToDevice, p->side);
+  if (e == cudaSuccess) e = launch_choice(I, p->sms, p->side);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.ready, p->side);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->side);
+  if (e != cudaSuccess) return cuda_fail(e, "pool restore slot");
+  sl.restored = true;
+  sl.wait_ready = true;
+  p->dirty = true;
+  return ACO_OK;
 }
 
 int aco_pool_set_multirate(aco_pool_handle p, int32_t on) {
