@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="n1002", choices=sorted(WORKLOADS))
     ap.add_argument("--deposit", default="sym", choices=["gather", "u64", "f32", "sym", "sort"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dist-timeout", type=float, default=600.0,
+                    help="seconds a rank waits in a barrier or collective for the others")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--warps-per-ant", type=int, default=0, help="0 = library default")
@@ -95,10 +97,13 @@ def dist_init(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import datetime
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        # a replica that dies makes the others' next barrier fail after this
+        # long instead of waiting forever
+        dist.init_process_group("nccl", timeout=datetime.timedelta(seconds=args.dist_timeout))
     return rank, world, local
 
 

@@ -55,6 +55,44 @@ def test_two_replicas_take_the_slowest_rank():
         assert value == pytest.approx(2 * 1000.0 / 2.0)
 
 
+def _failing_worker(rank, world, port, out):
+    import datetime
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    import bench
+    if rank == 1:
+        # this replica dies between steps, with nothing in flight
+        os._exit(3)
+    try:
+        bench.barrier(world)
+        out.put((rank, "passed"))
+    except Exception as exc:  # the surviving rank learns of it on the host
+        out.put((rank, type(exc).__name__))
+
+
+def test_a_dead_replica_fails_the_barrier_instead_of_hanging():
+    import multiprocessing as mp
+    import time
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    rank, outcome = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and outcome != "passed"
+    assert procs[1].exitcode == 3
+    assert time.time() - t0 < 100
+
+
 def test_single_rank_needs_no_process_group():
     import sys
     sys.path.insert(0, ROOT)
