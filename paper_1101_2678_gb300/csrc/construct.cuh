@@ -381,7 +381,11 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     if constexpr (R == 1) {
       // Scores u_j * w_j; a thread's four consecutive cities share one
       // Philox call (C and base are multiples of 4).
-      uint64_t key = 0;  // (score bits << 32) | ~index: max = best score, lowest index
+      // Each thread walks its cities in ascending order and keeps the first
+      // of its highest scores (bits of a non-negative float order like its
+      // value; 0 = no positive score); the segment reduction breaks ties by
+      // index.
+      uint32_t bs = 0u, bj = 0xffffffffu;
 #pragma unroll
       for (int i = 0; i < C; i += 4) {
         const Philox4 x = philox4x32_10((uint32_t)s, (uint32_t)ant, iter,
@@ -390,17 +394,24 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
         const uint32_t xs[4] = {x.x0, x.x1, x.x2, x.x3};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float score = __fmul_rn(candidate_uniform_of(xs[e]), __uint_as_float(v[i + e]));
-          const uint64_t k = ((uint64_t)__float_as_uint(score) << 32) |
-                             (uint32_t)(0xffffffffu - (uint32_t)(base + i + e));
-          if (score > 0.0f && k > key) key = k;
+          const uint32_t sb = __float_as_uint(
+              __fmul_rn(candidate_uniform_of(xs[e]), __uint_as_float(v[i + e])));
+          if (sb > bs) {
+            bs = sb;
+            bj = (uint32_t)(base + i + e);
+          }
         }
       }
 #pragma unroll
       for (int o = H / 2; o > 0; o >>= 1) {
-        const uint64_t other = seg.shfl_xor(key, o);
-        key = other > key ? other : key;
+        const uint32_t os = seg.shfl_xor(bs, o), oj = seg.shfl_xor(bj, o);
+        if (os > bs || (os == bs && oj < bj)) {
+          bs = os;
+          bj = oj;
+        }
       }
+      // (score bits << 32) | ~index: max = best score, lowest index
+      uint64_t key = bs ? ((uint64_t)bs << 32) | (uint32_t)(0xffffffffu - bj) : 0ull;
       if (G > 1) {
         if (hl == 0) gs->wsum[wg] = key;
         group_sync(bar_id, NT);
