@@ -98,7 +98,7 @@ extern "C" {
                                   and, when all are visited, moves to the
                                   unvisited city with the largest choice_info
                                   value (ties to the lower index).  Needs
-                                  ACO_SELECT_EQ1; not available in pools.      */
+                                  ACO_SELECT_EQ1; pool slots: aco_pool_set_nn. */
 #define ACO_OPT_STAGING 10     /* how the construction kernel brings row
                                   choice[cur] into shared memory at each step:
                                   0 one bulk copy (TMA engine, cp.async.bulk)
@@ -412,6 +412,18 @@ int aco_pool_admit_coords(aco_pool_handle p, int32_t n, const int32_t *xy, float
  */
 int aco_pool_set_acs(aco_pool_handle p, int32_t slot, double q0, float xi);
 int aco_pool_set_mmas(aco_pool_handle p, int32_t slot, double p_best, int32_t best_so_far);
+
+/*
+ * aco_pool_set_nn - nearest-neighbour-list construction for a live slot
+ * before its first step, as ACO_OPT_NN_LIST does for a handle (the
+ * construction of the paper's Table 2 versions 4-6, Section II): nn = 1 ..
+ * min(n - 1, 32) entries, 0 = dense Eq. 1 again.  Composes with the Ant
+ * System and the MAX-MIN Ant System (not with the Ant Colony System:
+ * ACO_EINVAL either way round).  All list slots of a pool construct in one
+ * launch (one warp per ant) and refresh their list-ordered choice_info after
+ * each update.  ACO_ESTATE after the slot's first step.
+ */
+int aco_pool_set_nn(aco_pool_handle p, int32_t slot, int32_t nn);
 
 /*
  * aco_pool_save_slot / aco_pool_restore_slot - checkpoints of pool slots, in

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("aco_pool_rate", C.c_int, [_vp, C.c_int32, _i32p]),
     ("aco_pool_save_slot", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64, C.POINTER(C.c_uint64)]),
     ("aco_pool_restore_slot", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64]),
+    ("aco_pool_set_nn", C.c_int, [_vp, C.c_int32, C.c_int32]),
     ("aco_pool_step", C.c_int, [_vp, _i32p]),
     ("aco_pool_finished", C.c_int, [_vp, _vp, C.c_int32, _i32p]),
     ("aco_pool_result", C.c_int, [_vp, C.c_int32, _vp, _vp]),
@@ -367,6 +368,10 @@ def aco_pool_restore_slot(p, slot: int, blob: bytes) -> None:
     """Load a checkpoint into a freshly admitted slot of the same instance."""
     buf = np.frombuffer(blob, np.uint8)
     _check(load().aco_pool_restore_slot(p, slot, _ptr(buf), buf.size), "aco_pool_restore_slot")
+
+
+def aco_pool_set_nn(p, slot: int, nn: int) -> None:
+    _check(load().aco_pool_set_nn(p, slot, nn), "aco_pool_set_nn")
 
 
 def aco_pool_set_multirate(p, on: bool) -> None:

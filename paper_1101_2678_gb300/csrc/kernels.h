@@ -88,6 +88,13 @@ cudaError_t launch_construct_items(const Instance* insts, const int2* items, int
 cudaError_t launch_nn_lists(const Instance& I, int nn, cudaStream_t st);
 cudaError_t launch_nn_choice(const Instance& I, cudaStream_t st);
 cudaError_t launch_construct_nn(const Instance& I, cudaStream_t st);
+// The same for many instances (pool slots): one warp per (slot, ant) item,
+// bitmaps sized for the largest n; and the list-ordered choice_info refresh
+// of `count` slots after their update.
+cudaError_t launch_construct_nn_items(const Instance* insts, const int2* items, int count,
+                                      int max_n, cudaStream_t st);
+cudaError_t launch_nn_choice_slots(const Instance* insts, const int* slots, int count,
+                                   int max_n, cudaStream_t st);
 
 // Batched best / gather update over device-side lists.
 cudaError_t launch_best_slots(const Instance* insts, const int* slots, int count, cudaStream_t st);

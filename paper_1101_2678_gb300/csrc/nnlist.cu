@@ -2,6 +2,7 @@
 // Table 2 versions 4-6, Section II): an ant at city i samples Eq. 1 among the
 // unvisited cities of list(i), the nn nearest cities of i; if all of them are
 // visited it moves to the unvisited city with the largest choice_info value.
+#include <algorithm>
 #include <climits>
 
 #include "aco_device.cuh"
@@ -60,13 +61,9 @@ __global__ void nn_choice_kernel(Instance I) {
 
 // One warp per ant; lane l holds list entry l of the current city.  The
 // tabu list is a bitmap of n bits in shared memory (one per warp).
-__global__ void __launch_bounds__(128) construct_nn_kernel(Instance I) {
-  extern __shared__ uint32_t nn_bits[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int ant = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (ant >= I.m) return;
+__device__ __forceinline__ void nn_construct_ant(const Instance& I, const int ant, const int lane,
+                                                 uint32_t* bits) {
   const int n = I.n, nn = I.nn, ld = I.ld, words = (n + 31) >> 5;
-  uint32_t* bits = nn_bits + (size_t)warp * words;
   const uint32_t iter = (uint32_t)I.st->iteration;
   const unsigned long long seed = I.seed;
   for (int i = lane; i < words; i += 32) bits[i] = 0u;
@@ -160,6 +157,38 @@ __global__ void __launch_bounds__(128) construct_nn_kernel(Instance I) {
   if (lane == 0) I.lens[ant] = len;
 }
 
+__global__ void __launch_bounds__(128) construct_nn_kernel(Instance I) {
+  extern __shared__ uint32_t nn_bits[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ant = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (ant >= I.m) return;
+  nn_construct_ant(I, ant, lane, nn_bits + (size_t)warp * ((I.n + 31) / 32));
+}
+
+// Many instances: warp w builds ant items[w].y of instance insts[items[w].x];
+// the bitmaps are sized for the largest n among them.
+__global__ void __launch_bounds__(128) construct_nn_items_kernel(
+    const Instance* __restrict__ insts, const int2* __restrict__ items, int count, int words) {
+  extern __shared__ uint32_t nn_bits[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (idx >= count) return;
+  const int2 it = items[idx];
+  nn_construct_ant(insts[it.x], it.y, lane, nn_bits + (size_t)warp * words);
+}
+
+// nnchoice refresh for many instances: block row y serves insts[slots[y]].
+__global__ void nn_choice_slots_kernel(const Instance* __restrict__ insts,
+                                       const int* __restrict__ slots) {
+  const Instance& I = insts[slots[blockIdx.y]];
+  const size_t total = (size_t)I.n * kNnStride;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / kNnStride), l = (int)(e % kNnStride);
+    if (l < I.nn) I.nnchoice[e] = I.choice[(size_t)i * I.ld + I.nnlist[e]];
+  }
+}
+
 cudaError_t launch_nn_lists(const Instance& I, int nn, cudaStream_t st) {
   nn_list_kernel<<<(I.n + 3) / 4, 128, 0, st>>>(I, nn);
   return cudaGetLastError();
@@ -177,6 +206,25 @@ cudaError_t launch_construct_nn(const Instance& I, cudaStream_t st) {
   const int warps = 4;
   const size_t smem = (size_t)warps * ((I.n + 31) / 32) * sizeof(uint32_t);
   construct_nn_kernel<<<(I.m + warps - 1) / warps, 32 * warps, smem, st>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_construct_nn_items(const Instance* insts, const int2* items, int count,
+                                      int max_n, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int warps = 4, words = (max_n + 31) / 32;
+  const size_t smem = (size_t)warps * words * sizeof(uint32_t);
+  construct_nn_items_kernel<<<(count + warps - 1) / warps, 32 * warps, smem, st>>>(insts, items,
+                                                                                  count, words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nn_choice_slots(const Instance* insts, const int* slots, int count,
+                                   int max_n, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t total = (size_t)max_n * kNnStride;
+  const unsigned bx = (unsigned)std::min<size_t>((total + 255) / 256, 64);
+  nn_choice_slots_kernel<<<dim3(bx, (unsigned)count), 256, 0, st>>>(insts, slots);
   return cudaGetLastError();
 }
 

@@ -30,7 +30,8 @@ namespace aco {
 static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
-  size_t dist, heta, tau, choice, tours, lens, nbr, q, delta, best, dep_nb, st, total;
+  size_t dist, heta, tau, choice, tours, lens, nbr, q, delta, best, dep_nb, nnlist, nnchoice, st,
+      total;
 };
 
 static Layout layout_of(int n, int m) {
@@ -55,6 +56,8 @@ static Layout layout_of(int n, int m) {
   L.delta = take((size_t)m * 4);
   L.best = take(((size_t)n + 1) * 4);
   L.dep_nb = take((size_t)n * 4);
+  L.nnlist = take((size_t)n * kNnStride * 4);
+  L.nnchoice = take((size_t)n * kNnStride * 4);
   L.st = take(sizeof(IterState));
   L.total = off;
   return L;
@@ -97,6 +100,7 @@ struct PoolSlot {
   bool started = false;  // taken part in a step (the update rule is then fixed)
   bool restored = false; // state loaded from a checkpoint (rule fixed as well)
   int rate = 1;          // iterations per step (multi-rate stepping)
+  bool nn_built = false; // nearest-neighbour lists built (aco_pool_set_nn)
 };
 
 struct aco_pool {
@@ -134,6 +138,7 @@ struct aco_pool {
     int slot_begin, slot_count;     // its slots in h_cls_slots
     int row_begin, row_count, max_ld;  // its rows in h_rows
     int k;                          // iterations per step
+    bool nn;                        // nearest-neighbour-list construction
   };
   std::vector<Class> classes;
   // Autotuner: for each default class, the (G, H, ants per CTA) that measured
@@ -209,8 +214,8 @@ static int ensure_capacity(void** ptr, size_t* cap, size_t need, size_t elem) {
 // microseconds: n dependent steps, each costing a fixed latency plus the
 // per-lane chunk (n / 32 cities); the Ant Colony System's lockstep step is
 // about 4 us.  Only ratios matter (they set the iterations per step).
-static double iteration_time_model(int n, bool acs) {
-  return acs ? 4.0 * n : n * (0.6 + 0.025 * n / 32.0);
+static double iteration_time_model(int n, bool acs, bool nn = false) {
+  return acs ? 4.0 * n : nn ? 0.65 * n : n * (0.6 + 0.025 * n / 32.0);
 }
 constexpr int kMaxRate = 64;  // iterations per step at most
 
@@ -264,16 +269,20 @@ static int pool_rebuild(aco_pool* p) {
   for (int s : live) {
     if (p->slots[(size_t)s].I.variant == kVariantAcs) continue;
     const ConstructTiling t = batched_construct_tiling(p->slots[(size_t)s].n);
-    const auto key = std::make_tuple(t.G, t.H, t.C);
+    // nearest-neighbour-list slots: one class of their own (key 0, 0, 0)
+    const auto key = p->slots[(size_t)s].I.nn > 0 ? std::make_tuple(0, 0, 0)
+                                                  : std::make_tuple(t.G, t.H, t.C);
     if (!by_class.count(key)) class_order.push_back(key);
     by_class[key].push_back(s);
   }
   for (const auto& key : class_order) {
     aco_pool::Class c;
     c.key = key;
-    c.max_n = p->slots[(size_t)by_class[key][0]].n;
+    c.nn = key == std::make_tuple(0, 0, 0);
+    c.max_n = 0;
+    for (int s : by_class[key]) c.max_n = std::max(c.max_n, p->slots[(size_t)s].n);
     c.t = batched_construct_tiling(c.max_n);
-    if (p->autotune) {
+    if (p->autotune && !c.nn) {
       auto it = p->tuned.find(key);
       if (it == p->tuned.end()) {
         p->tuned_pending = true;
@@ -305,10 +314,11 @@ static int pool_rebuild(aco_pool* p) {
   }
   // iterations per step of each group (1 unless multi-rate stepping is on)
   double t_max = p->h_acs.empty() ? 0.0 : iteration_time_model(p->acs_max_n, true);
-  for (const auto& c : p->classes) t_max = std::max(t_max, iteration_time_model(c.max_n, false));
+  for (const auto& c : p->classes)
+    t_max = std::max(t_max, iteration_time_model(c.max_n, false, c.nn));
   for (auto& c : p->classes) {
     c.k = group_rate(p, p->h_cls_slots.data() + c.slot_begin, c.slot_count,
-                     iteration_time_model(c.max_n, false), t_max);
+                     iteration_time_model(c.max_n, false, c.nn), t_max);
     for (int i = 0; i < c.slot_count; ++i)
       p->slots[(size_t)p->h_cls_slots[(size_t)(c.slot_begin + i)]].rate = c.k;
   }
@@ -358,7 +368,7 @@ static int pool_autotune(aco_pool* p) {
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   for (auto& c : p->classes) {
     if (e != cudaSuccess) break;
-    if (p->tuned.count(c.key)) continue;
+    if (c.nn || p->tuned.count(c.key)) continue;
     float best_ms = 0.0f;
     int bi = -1;
     const ConstructTiling d = batched_construct_tiling(c.max_n);
@@ -449,7 +459,8 @@ static int pool_enqueue_step(aco_pool* p) {
     const auto& c = p->classes[(size_t)ci];
     cudaStream_t st = nstreams > 1 ? p->class_stream[(ci + first) % nstreams] : p->stream;
     for (int r = 0; r < (mr ? c.k : 1); ++r) {
-      e = launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, st);
+      e = c.nn ? launch_construct_nn_items(p->d_inst, p->d_items + c.begin, c.count, c.max_n, st)
+               : launch_construct_items(p->d_inst, p->d_items + c.begin, c.count, c.t, st);
       if (e != cudaSuccess) return cuda_fail(e, "pool construct");
       ++launches;
       if (!mr) break;
@@ -460,6 +471,12 @@ static int pool_enqueue_step(aco_pool* p) {
                                   st)) != cudaSuccess)
         return cuda_fail(e, "pool update");
       launches += 2;
+      if (c.nn) {
+        if ((e = launch_nn_choice_slots(p->d_inst, p->d_cls_slots + c.slot_begin, c.slot_count,
+                                        c.max_n, st)) != cudaSuccess)
+          return cuda_fail(e, "pool nn choice");
+        ++launches;
+      }
     }
   }
   for (int i = 0; i < nstreams && nstreams > 1; ++i) {
@@ -480,6 +497,13 @@ static int pool_enqueue_step(aco_pool* p) {
     if ((e = launch_acs_global_slots(p->d_inst, p->d_acs, nacs, p->stream)) != cudaSuccess)
       return cuda_fail(e, "pool acs update");
     launches += nacs > 0 ? 1 : 0;
+    for (const auto& c : p->classes) {
+      if (!c.nn) continue;
+      if ((e = launch_nn_choice_slots(p->d_inst, p->d_cls_slots + c.slot_begin, c.slot_count,
+                                      c.max_n, p->stream)) != cudaSuccess)
+        return cuda_fail(e, "pool nn choice");
+      ++launches;
+    }
   }
   p->launches = launches;
   return ACO_OK;
@@ -543,6 +567,9 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
   I.acc = nullptr;
   I.best_tour = (int32_t*)(b + L.best);
   I.dep_nb = (uint32_t*)(b + L.dep_nb);
+  I.nnlist = (int32_t*)(b + L.nnlist);
+  I.nnchoice = (float*)(b + L.nnchoice);
+  I.nn = 0;
   I.st = (IterState*)(b + L.st);
   cudaError_t e = cudaSuccess;
   // Sources of the asynchronous copies below must outlive this call: the
@@ -720,6 +747,8 @@ int aco_pool_set_acs(aco_pool_handle p, int32_t slot, double q0, float xi) {
   const int m = p->slots[(size_t)slot].m;
   if (m > kAcsMaxAnts)
     return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants (m=%d)", kAcsMaxAnts, m);
+  if (p->slots[(size_t)slot].I.nn > 0)
+    return fail(ACO_EINVAL, "the Ant Colony System uses its own construction (no lists)");
   return pool_switch_rule(p, slot, [&](Instance& I) {
     I.variant = kVariantAcs;
     I.acs_threshold = acs_threshold_of(q0);
@@ -816,6 +845,34 @@ int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t* tour, int64_t* len
   return pool_check_status(p, slot);
 }
 
+int aco_pool_set_nn(aco_pool_handle p, int32_t slot, int32_t nn) {
+  NvtxRange nvtx_range("aco_pool_set_nn");
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].live)
+    return fail(ACO_EINVAL, "slot %d is not live", slot);
+  PoolSlot& sl = p->slots[(size_t)slot];
+  if (sl.started) return fail(ACO_ESTATE, "lists are chosen before the slot's first step");
+  const int most = std::min(sl.n - 1, kNnStride);
+  if (nn < 0 || nn > most)
+    return fail(ACO_EINVAL, "nearest-neighbour list length must be in [0, %d]", most);
+  if (nn > 0 && sl.I.variant == kVariantAcs)
+    return fail(ACO_EINVAL, "the Ant Colony System uses its own construction");
+  Instance& I = sl.I;
+  cudaError_t e = cudaSuccess;
+  // on the side stream after the admission's setup (and any rule switch)
+  if (nn > 0 && !sl.nn_built) e = launch_nn_lists(I, most, p->side);
+  I.nn = nn;
+  if (e == cudaSuccess && nn > 0) e = launch_nn_choice(I, p->side);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->d_inst + slot, &I, sizeof I, cudaMemcpyHostToDevice, p->side);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.ready, p->side);
+  if (e != cudaSuccess) return cuda_fail(e, "pool set nn");
+  if (nn > 0) sl.nn_built = true;
+  sl.wait_ready = true;
+  p->dirty = true;
+  return ACO_OK;
+}
+
 int aco_pool_save_slot(aco_pool_handle p, int32_t slot, void* buf, uint64_t capacity,
                        uint64_t* size) {
   NvtxRange nvtx_range("aco_pool_save_slot");
@@ -869,8 +926,9 @@ int aco_pool_restore_slot(aco_pool_handle p, int32_t slot, const void* buf, uint
   const int32_t* best = nullptr;
   int rc = checkpoint_parse(sl.I, buf, size, hd, st, tau, best);
   if (rc) return rc;
-  if (hd.variant == kVariantAcs && sl.m > kAcsMaxAnts)
-    return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants", kAcsMaxAnts);
+  if (hd.variant == kVariantAcs && (sl.m > kAcsMaxAnts || sl.I.nn > 0))
+    return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants, without lists",
+                kAcsMaxAnts);
   Instance& I = sl.I;
   I.variant = hd.variant;
   I.mmas_best_so_far = hd.mmas_best_so_far;
@@ -890,6 +948,7 @@ int aco_pool_restore_slot(aco_pool_handle p, int32_t slot, const void* buf, uint
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->d_inst + slot, &I, sizeof I, cudaMemcpyHostToDevice, p->side);
   if (e == cudaSuccess) e = launch_choice(I, p->sms, p->side);
+  if (e == cudaSuccess && I.nn > 0) e = launch_nn_choice(I, p->side);
   if (e == cudaSuccess) e = cudaEventRecord(sl.ready, p->side);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->side);
   if (e != cudaSuccess) return cuda_fail(e, "pool restore slot");
@@ -992,6 +1051,9 @@ int aco_pool_tiling(aco_pool_handle p, int32_t slot, int32_t* warps_per_ant,
   if (p->dirty) return fail(ACO_ESTATE, "no step has run since the live set changed");
   if (p->slots[(size_t)slot].I.variant == kVariantAcs)
     return fail(ACO_EINVAL, "slot %d runs the Ant Colony System (one CTA per colony)", slot);
+  if (p->slots[(size_t)slot].I.nn > 0)
+    return fail(ACO_EINVAL, "slot %d constructs with nearest-neighbour lists (one warp per ant)",
+                slot);
   const int n = p->slots[(size_t)slot].n;
   for (const auto& c : p->classes)
     if (c.key == std::make_tuple(batched_construct_tiling(n).G, batched_construct_tiling(n).H,

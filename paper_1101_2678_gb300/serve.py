@@ -40,6 +40,9 @@ class Request:
     xi: float = 0.1
     p_best: float = 0.05
     best_so_far: bool = False
+    # nearest-neighbour lists of this length (0: every unvisited city); not
+    # with the Ant Colony System
+    nn: int = 0
 
     @property
     def n(self) -> int:
@@ -141,6 +144,8 @@ class Server:
                     aco.aco_pool_set_acs(pool, slot, r.q0, r.xi)
                 elif r.variant == "mmas":
                     aco.aco_pool_set_mmas(pool, slot, r.p_best, r.best_so_far)
+                if r.nn:
+                    aco.aco_pool_set_nn(pool, slot, r.nn)
                 live[slot] = (queue.popleft(), time.perf_counter() - t0)
                 live_work += w
             if not live:

@@ -103,6 +103,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.aco_pool_set_acs(None, 0, 0.9, 0.1) == aco.ACO_EINVAL
     assert lib.aco_pool_set_mmas(None, 0, 0.05, 0) == aco.ACO_EINVAL
     assert lib.aco_pool_set_multirate(None, 1) == aco.ACO_EINVAL
+    assert lib.aco_pool_set_nn(None, 0, 8) == aco.ACO_EINVAL
     sz = C.c_uint64()
     assert lib.aco_pool_save_slot(None, 0, None, 0, C.byref(sz)) == aco.ACO_EINVAL
     assert lib.aco_pool_restore_slot(None, 0, None, 0) == aco.ACO_EINVAL

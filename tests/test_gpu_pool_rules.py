@@ -354,3 +354,83 @@ def test_multirate_rate_never_exceeds_the_budget_left(aco, orc):
         assert e.value.code == aco.ACO_EINVAL
     finally:
         aco.aco_batch_destroy(b)
+
+
+def nn_alone(aco, dist, m, seed, iters, nn, rho=0.5, mmas=False):
+    n = dist.shape[0]
+    with aco.Colony(dist, m, seed=seed, rho=rho) as c:
+        if mmas:
+            aco.aco_set_mmas(c.h, 0.05, False)
+        aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, nn)
+        aco.aco_iterate(c.h, iters)
+        return aco.aco_get_pheromone(c.h, n), aco.aco_best_tour(c.h, n)
+
+
+@pytest.mark.parametrize("multirate", [False, True])
+def test_nn_list_slots_equal_their_handle_runs(aco, orc, multirate):
+    # list slots of several sizes and list lengths (one with the MAX-MIN
+    # update) beside dense Ant System slots and a colony; each equals its
+    # handle run with ACO_OPT_NN_LIST, and the smallest the oracle's run
+    cases = [(10, 9, 12, 5, 41, False), (300, 30, 64, 4, 42, False), (130, 20, 60, 6, 43, True),
+             (700, 32, 40, 3, 44, False)]
+    insts = {n: I.clustered_instance(n, seed=n + 7, clusters=6, side=4000) for n, *_r in cases}
+    dense = I.uniform_instance(200, 1000, seed=46)
+    colony = I.uniform_instance(60, 1000, seed=47)
+    need = sum(aco.aco_pool_bytes_needed(n, m) for n, _nn, m, *_r in cases)
+    need += aco.aco_pool_bytes_needed(200, 100) + aco.aco_pool_bytes_needed(60, 10)
+    p = aco.aco_pool_create(8, need + (1 << 20))
+    try:
+        aco.aco_pool_set_multirate(p, multirate)
+        slots = {}
+        for n, nn, m, iters, seed, mmas in cases:
+            rho = 0.02 if mmas else 0.5
+            slots[n] = aco.aco_pool_admit(p, insts[n].dist, 1.0, 2.0, rho, m, seed, iters)
+            if mmas:
+                aco.aco_pool_set_mmas(p, slots[n], 0.05, False)
+            aco.aco_pool_set_nn(p, slots[n], nn)
+        sd = aco.aco_pool_admit(p, dense.dist, 1.0, 2.0, 0.5, 100, 48, 4)
+        sc = aco.aco_pool_admit_acs(p, colony.dist, 1.0, 2.0, 0.1, 10, 49, 5, 0.9, 0.1)
+        while aco.aco_pool_step(p) > 0:
+            pass
+        aco.aco_pool_synchronize(p)
+        for n, nn, m, iters, seed, mmas in cases:
+            tau_a, (tour_a, len_a) = nn_alone(aco, insts[n].dist, m, seed, iters, nn,
+                                              rho=0.02 if mmas else 0.5, mmas=mmas)
+            assert np.array_equal(aco.aco_pool_pheromone(p, slots[n], n), tau_a), n
+            tour_p, len_p = aco.aco_pool_result(p, slots[n], n)
+            assert len_p == len_a and np.array_equal(tour_p, tour_a), n
+        ref = orc.run(insts[10].dist, 12, 5, 41, rule=2, nn=9)
+        assert np.array_equal(aco.aco_pool_pheromone(p, slots[10], 10), ref["tau32"])
+        tau_a, (_, len_a) = as_alone(aco, dense.dist, 100, 48, 4)
+        assert np.array_equal(aco.aco_pool_pheromone(p, sd, 200), tau_a)
+        check_acs_slot(aco, orc, p, sc, colony.dist, 10, 49, 5, 0.1, 0.9, 0.1)
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+def test_nn_list_slot_errors(aco):
+    x = I.uniform_instance(40, 1000, seed=9)
+    p = aco.aco_pool_create(4, 4 * aco.aco_pool_bytes_needed(40, 10) + (1 << 20))
+    try:
+        s = aco.aco_pool_admit(p, x.dist, 1.0, 2.0, 0.5, 10, 1, 3)
+        for bad in (-1, 33):
+            with pytest.raises(aco.AcoError) as e:
+                aco.aco_pool_set_nn(p, s, bad)
+            assert e.value.code == aco.ACO_EINVAL
+        aco.aco_pool_set_nn(p, s, 8)
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_set_acs(p, s, 0.9, 0.1)
+        assert e.value.code == aco.ACO_EINVAL
+        c = aco.aco_pool_admit_acs(p, x.dist, 1.0, 2.0, 0.1, 10, 2, 3, 0.9, 0.1)
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_set_nn(p, c, 8)
+        assert e.value.code == aco.ACO_EINVAL
+        aco.aco_pool_step(p)
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_set_nn(p, s, 4)
+        assert e.value.code == aco.ACO_ESTATE
+        with pytest.raises(aco.AcoError) as e:
+            aco.aco_pool_tiling(p, s)
+        assert e.value.code == aco.ACO_EINVAL
+    finally:
+        aco.aco_pool_destroy(p)

@@ -60,6 +60,10 @@ class FakeAco:
         p.slots[slot]["rule"] = "mmas"
         p.log.append(("rule", slot, "mmas"))
 
+    def aco_pool_set_nn(self, p, slot, nn):
+        p.slots[slot]["nn"] = nn
+        p.log.append(("rule", slot, f"nn{nn}"))
+
     def aco_pool_stats(self, p):
         return dict(live=len(p.slots), finished=len(p.finished), bytes_in_use=p.used,
                     launches_last_step=1)
@@ -146,14 +150,14 @@ def test_hbm_budget_limits_admission(fake):
 
 def test_rules_and_multirate_reach_the_pool(fake):
     reqs = [req(40, 2, seed=1, variant="acs", q0=0.8, xi=0.2),
-            req(50, 2, seed=2, variant="mmas", p_best=0.1, best_so_far=True),
+            req(50, 2, seed=2, variant="mmas", p_best=0.1, best_so_far=True, nn=16),
             req(60, 2, seed=3)]
     with serve.Server(budget_bytes=1 << 30, max_slots=8, multirate=True) as srv:
         outs, st = srv.run(reqs, np.zeros(3), realtime=False)
     pool = fake.pools[0]
     assert pool.multirate
     rules = [e[2] for e in pool.log if e[0] == "rule"]
-    assert sorted(rules) == ["acs", "mmas"]
+    assert sorted(rules) == ["acs", "mmas", "nn16"]
     assert st["completed"] == 3
 
 
