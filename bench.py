@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-step-work", type=float, default=1e11,
                     help="served: candidate evaluations one step may hold (admission bound)")
+    ap.add_argument("--serve-nn", type=int, default=0,
+                    help="served: nearest-neighbour lists of this length for every request "
+                         "(0: dense Eq. 1, the configured workload)")
     ap.add_argument("--no-multirate", action="store_true",
                     help="served: one iteration per step for every request (no multi-rate "
                          "stepping)")
@@ -746,7 +749,8 @@ def run_served(args, rank, world, local):
     reqs = []
     for r in range(len(arrivals)):
         q = instances.served_request(r)
-        reqs.append(serve.Request(q["inst"].coords, q["m"], q["iterations"], q["seed"]))
+        reqs.append(serve.Request(q["inst"].coords, q["m"], q["iterations"], q["seed"],
+                                  nn=args.serve_nn))
     mr = not args.no_multirate
     work = int(args.serve_step_work)
     with serve.Server(budget_bytes=64 << 30, max_slots=4096, multirate=mr,
@@ -769,6 +773,8 @@ def run_served(args, rank, world, local):
     loop_lens = []
     for r in sample:
         h = aco.aco_create_coords(r.coords, r.alpha, r.beta, r.rho, r.m, r.seed)
+        if r.nn:
+            aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, r.nn)
         aco.aco_iterate(h, r.iterations)
         loop_lens.append(aco.aco_best_tour(h, r.n)[1])
         aco.aco_destroy(h)
@@ -796,7 +802,7 @@ def run_served(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "as-served-poisson", "rate_per_s": args.serve_rate,
                    "window_s": args.serve_seconds, "budget_gb": 64, "iterations": 200,
-                   "multirate": mr, "max_step_work": work},
+                   "multirate": mr, "max_step_work": work, "nn_list": args.serve_nn},
         "configured_stream": st,
         "sustainable_stream": dict(st2, rate_per_s=rate),
         "loop_comparison": loop,

@@ -64,8 +64,9 @@ class Outcome:
 
 
 def step_work(r: Request) -> int:
-    """Candidate evaluations one iteration of request r costs (m ants x n steps x n cities)."""
-    return int(r.m) * r.n * r.n
+    """Candidate evaluations one iteration of request r costs: m ants x n steps x the
+    candidates of a step (n cities, or the nn list entries)."""
+    return int(r.m) * r.n * (min(r.nn, r.n) if r.nn else r.n)
 
 
 class Server:
