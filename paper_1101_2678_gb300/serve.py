@@ -74,13 +74,16 @@ class Server:
     the candidate evaluations one step may contain (the sum of step_work over
     live requests): a larger batch raises throughput but every live request
     waits for the whole step, so the bound trades throughput for latency.  A
-    request larger than the bound is admitted alone.  With `multirate`, each
+    request larger than the bound is admitted alone.  `max_live` (optional)
+    caps the number of live requests as well.  With `multirate`, each
     step runs several iterations of the shorter requests, so they no longer
     wait one step of the longest request per iteration."""
 
     def __init__(self, budget_bytes: int = 64 << 30, max_slots: int = 2048,
-                 max_step_work: int = 20_000_000_000, multirate: bool = False):
+                 max_step_work: int = 20_000_000_000, multirate: bool = False,
+                 max_live: int | None = None):
         self.pool = aco.aco_pool_create(max_slots, budget_bytes)
+        self.max_live = max_live
         if multirate:
             # short requests run several iterations per step (aco_pool_set_multirate)
             aco.aco_pool_set_multirate(self.pool, True)
@@ -136,6 +139,8 @@ class Server:
                 r = requests[queue[0]]
                 w = step_work(r)
                 if live and live_work + w > self.max_step_work:
+                    break
+                if self.max_live is not None and len(live) >= self.max_live:
                     break
                 slot = aco.aco_pool_admit_coords(pool, r.coords, r.alpha, r.beta, r.rho, r.m,
                                                  r.seed, r.iterations)

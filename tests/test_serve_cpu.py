@@ -168,3 +168,13 @@ def test_deadline_stops_with_a_backlog(fake):
     assert st["completed"] == 0 and st["backlog"] == 3
     assert st["still_live"] == 1 and st["queued"] == 2
     assert st["queue_depth_max"] == 2 and st["steps"] >= 1
+
+
+def test_live_cap(fake):
+    reqs = [req(30, 3, seed=i) for i in range(7)]
+    with serve.Server(budget_bytes=1 << 30, max_slots=16, max_step_work=10**12,
+                      max_live=3) as srv:
+        outs, st = srv.run(reqs, np.zeros(7), realtime=False)
+    steps = [e[1] for e in fake.pools[0].log if e[0] == "step"]
+    assert st["completed"] == 7 and st["max_live"] == 3
+    assert max(len(s) for s in steps) == 3
