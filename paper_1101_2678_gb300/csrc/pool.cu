@@ -1,16 +1,22 @@
-// Batched and served Ant System instances: a pool of device-resident slots
+// Batched and served instances: a pool of device-resident slots
 // (include/aco.h, aco_pool_* and aco_batch_*).
 //
 // Memory: one cudaMalloc'ed arena of the caller's HBM budget, carved by a
 // first-fit free list (host side) into one block per instance.  Each step
 // runs, for every live slot, the same three phases as a single instance:
 //   construct  one launch per tiling class (C cities per lane, G warps per
-//              ant), items (slot, ant) listed longest instance first;
+//              ant), items (slot, ant) listed longest instance first; one
+//              launch for all nearest-neighbour-list slots; one launch for
+//              all Ant Colony System colonies (a CTA each);
 //   best       one CTA per live slot;
 //   update     one warp per (slot, row): gather deposit + evaporation +
-//              choice_info, fused.
-// The device-side lists are rebuilt and the step re-captured as a CUDA graph
-// only when the live set changes.
+//              choice_info, fused (the MAX-MIN rule for its slots), then the
+//              list-order refresh for list slots; the colonies' global
+//              update on their best tours.
+// Slots choose their rule, lists and checkpoint before their first step.
+// Multi-rate stepping repeats each group's phases k times per step on its
+// own stream.  The device-side lists are rebuilt and the step re-captured as
+// a CUDA graph only when the live set (or a group's rate) changes.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
