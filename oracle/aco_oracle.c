@@ -67,6 +67,14 @@
  *     of list(i) by the integer roulette of R2 in list order; if every entry
  *     is visited it moves to the unvisited city with the largest weight,
  *     ties to the lower index.
+ *  R16 (optional) the Ant Colony System of R14 with the nearest-neighbour
+ *     lists of R9: at city i, if an entry of list(i) is unvisited, an
+ *     exploiting step moves to the unvisited entry of largest choice_info
+ *     (ties to the earlier entry) and an exploring step samples Eq. 1 over
+ *     the unvisited entries by the integer roulette in list order; if every
+ *     entry is visited, either step moves to the unvisited city of largest
+ *     choice_info (ties to the lower index).  The weights are the current
+ *     choice_info values (after the local updates), read at the list's cities.
  *  R15 (optional selection rule) the exponential race, a per-candidate
  *     random rule that samples Eq. 1: every unvisited city j draws
  *     v_j = floor(x / 2^8) + 1 in [1, 2^24] (x as in R8), E_j = -ln(v_j 2^-24)
@@ -832,6 +840,23 @@ int orc_acs_select(int n, const float *w, const uint8_t *visited, uint64_t r, ui
     return orc_roulette(n, w, visited, r);
 }
 
+/* The same with nearest-neighbour lists (reading R16): list holds the nn
+ * cities of list(i). */
+int orc_acs_select_nn(int n, int nn, const int32_t *list, const float *w, const uint8_t *visited,
+                      uint64_t r, uint32_t x2, uint64_t threshold)
+{
+    int any = 0;
+    for (int l = 0; l < nn; ++l)
+        if (!visited[list[l]]) any = 1;
+    if (!any || (uint64_t)x2 >= threshold) return orc_nn_select(n, nn, list, w, visited, r);
+    int best = -1;
+    for (int l = 0; l < nn; ++l) {
+        int j = list[l];
+        if (!visited[j] && (best < 0 || w[j] > w[best])) best = j;
+    }
+    return best;
+}
+
 /* One local update of one cell. */
 float orc_acs_local(float tau, float xi, float tau0)
 {
@@ -858,13 +883,19 @@ static void acs_cross(int n, int a, int b, float xi, float tau0, float alpha, co
 }
 
 /* A whole ACS run.  tau_out (n*n) is the final pheromone; the others as in
- * orc_run_nn. */
-int orc_run_acs(int n, const int32_t *d, float alpha, float beta, float rho, int m,
-                uint64_t seed, int iterations, double q0, float xi, int32_t *best_tour,
-                int64_t *best_len, float *tau_out, int32_t *last_tours, int64_t *last_lens,
-                int64_t *iter_best)
+ * orc_run_nn.  nn > 0: with nearest-neighbour lists of that length (R16). */
+int orc_run_acs_nn(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+                   uint64_t seed, int iterations, double q0, float xi, int nn,
+                   int32_t *best_tour, int64_t *best_len, float *tau_out, int32_t *last_tours,
+                   int64_t *last_lens, int64_t *iter_best)
 {
-    if (n < 3 || m < 1) return -1;
+    if (n < 3 || m < 1 || nn < 0 || nn > 32 || nn > n - 1) return -1;
+    int32_t *lists = NULL;
+    if (nn > 0) {
+        lists = (int32_t *)malloc((size_t)n * nn * sizeof(int32_t));
+        if (!lists) return -2;
+        orc_nn_lists(n, d, nn, lists);
+    }
     size_t cells = (size_t)n * n;
     float *heta = (float *)malloc(cells * sizeof(float));
     float *tau = (float *)malloc(cells * sizeof(float));
@@ -902,8 +933,11 @@ int orc_run_acs(int n, const int32_t *d, float alpha, float beta, float rho, int
             for (int k = 0; k < m; ++k) {
                 draw(seed, (uint32_t)s, (uint32_t)k, (uint32_t)it, x);
                 uint64_t r = ((uint64_t)x[1] << 32) | (uint64_t)x[0];
-                next[k] = orc_acs_select(n, choice + (size_t)cur[k] * n, visited + (size_t)k * n,
-                                         r, x[2], thr);
+                next[k] = nn > 0 ? orc_acs_select_nn(n, nn, lists + (size_t)cur[k] * nn,
+                                                     choice + (size_t)cur[k] * n,
+                                                     visited + (size_t)k * n, r, x[2], thr)
+                                 : orc_acs_select(n, choice + (size_t)cur[k] * n,
+                                                  visited + (size_t)k * n, r, x[2], thr);
             }
             for (int k = 0; k < m; ++k) {
                 acs_cross(n, cur[k], next[k], xi, tau0, alpha, heta, tau, choice);
@@ -946,8 +980,17 @@ int orc_run_acs(int n, const int32_t *d, float alpha, float beta, float rho, int
     if (last_tours) memcpy(last_tours, tours, (size_t)m * (n + 1) * sizeof(int32_t));
     if (last_lens) memcpy(last_lens, lens, (size_t)m * sizeof(int64_t));
     free(heta); free(tau); free(choice); free(tours); free(lens); free(gb); free(visited);
-    free(cur); free(next);
+    free(cur); free(next); free(lists);
     return 0;
+}
+
+int orc_run_acs(int n, const int32_t *d, float alpha, float beta, float rho, int m,
+                uint64_t seed, int iterations, double q0, float xi, int32_t *best_tour,
+                int64_t *best_len, float *tau_out, int32_t *last_tours, int64_t *last_lens,
+                int64_t *iter_best)
+{
+    return orc_run_acs_nn(n, d, alpha, beta, rho, m, seed, iterations, q0, xi, 0, best_tour,
+                          best_len, tau_out, last_tours, last_lens, iter_best);
 }
 
 /* ------------------------------------------------------------------------- */

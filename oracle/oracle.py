@@ -119,12 +119,19 @@ def lib():
             L.orc_acs_threshold.restype = C.c_uint64
             L.orc_acs_select.argtypes = [C.c_int, f32p, u8p, C.c_uint64, C.c_uint32, C.c_uint64]
             L.orc_acs_select.restype = C.c_int
+            L.orc_acs_select_nn.argtypes = [C.c_int, C.c_int, i32p, f32p, u8p, C.c_uint64,
+                                            C.c_uint32, C.c_uint64]
+            L.orc_acs_select_nn.restype = C.c_int
             L.orc_acs_local.argtypes = [C.c_float, C.c_float, C.c_float]
             L.orc_acs_local.restype = C.c_float
             L.orc_run_acs.argtypes = [C.c_int, i32p, C.c_float, C.c_float, C.c_float, C.c_int,
                                       C.c_uint64, C.c_int, C.c_double, C.c_float,
                                       vp, vp, vp, vp, vp, vp]
             L.orc_run_acs.restype = C.c_int
+            L.orc_run_acs_nn.argtypes = [C.c_int, i32p, C.c_float, C.c_float, C.c_float,
+                                         C.c_int, C.c_uint64, C.c_int, C.c_double, C.c_float,
+                                         C.c_int, vp, vp, vp, vp, vp, vp]
+            L.orc_run_acs_nn.restype = C.c_int
             L.orc_brute_force.argtypes = [C.c_int, i32p, i32p]
             L.orc_brute_force.restype = C.c_int64
             _lib = L
@@ -333,13 +340,22 @@ def acs_select(w, visited, r: int, x2: int, q0: float) -> int:
                                     C.c_uint64(acs_threshold(q0))))
 
 
+def acs_select_nn(w, visited, lst, r: int, x2: int, q0: float) -> int:
+    """One step of the Ant Colony System with a nearest-neighbour list (R16)."""
+    w = np.ascontiguousarray(w, np.float32)
+    v = np.ascontiguousarray(visited, np.uint8)
+    lst = np.ascontiguousarray(lst, np.int32)
+    return int(lib().orc_acs_select_nn(w.shape[0], lst.shape[0], lst, w, v, C.c_uint64(r),
+                                       C.c_uint32(x2), C.c_uint64(acs_threshold(q0))))
+
+
 def acs_local(tau: float, xi: float, tau0: float) -> float:
     return float(np.float32(lib().orc_acs_local(float(tau), float(xi), float(tau0))))
 
 
 def run_acs(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0.1,
-            q0=0.9, xi=0.1) -> dict:
-    """A whole Ant Colony System run (R14)."""
+            q0=0.9, xi=0.1, nn: int = 0) -> dict:
+    """A whole Ant Colony System run (R14); nn > 0: with nearest-neighbour lists (R16)."""
     d = _i32(dist)
     n = d.shape[0]
     best_tour = np.zeros(n + 1, np.int32)
@@ -348,10 +364,10 @@ def run_acs(dist, m: int, iterations: int, seed: int, alpha=1.0, beta=2.0, rho=0
     tours = np.zeros((m, n + 1), np.int32)
     lens = np.zeros(m, np.int64)
     iter_best = np.zeros(max(iterations, 1), np.int64)
-    rc = lib().orc_run_acs(n, d, float(alpha), float(beta), float(rho), int(m), C.c_uint64(seed),
-                           int(iterations), float(q0), float(xi), best_tour.ctypes.data,
-                           best_len.ctypes.data, tau.ctypes.data, tours.ctypes.data,
-                           lens.ctypes.data, iter_best.ctypes.data)
+    rc = lib().orc_run_acs_nn(n, d, float(alpha), float(beta), float(rho), int(m),
+                              C.c_uint64(seed), int(iterations), float(q0), float(xi), int(nn),
+                              best_tour.ctypes.data, best_len.ctypes.data, tau.ctypes.data,
+                              tours.ctypes.data, lens.ctypes.data, iter_best.ctypes.data)
     if rc != 0:
         raise ValueError("oracle ACS run failed")
     return dict(best_tour=best_tour, best_len=int(best_len[0]), tau32=tau, tours=tours,

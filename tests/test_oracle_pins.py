@@ -754,3 +754,66 @@ def test_acs_reaches_brute_force_optimum(orc, n, seed):
     opt, _ = orc.brute_force(inst.dist)
     r = orc.run_acs(inst.dist, 10, 60, seed)
     assert r["best_len"] == opt
+
+
+# --------------------------------------------------------------------------
+# The Ant Colony System with nearest-neighbour lists (reading R16)
+# --------------------------------------------------------------------------
+
+def test_acs_list_step_rules(orc):
+    # the heaviest city (7) is outside the list [2, 5, 3]: exploitation takes
+    # the heaviest unvisited entry (5, not 7); with 5 visited, the earlier of
+    # two equal entries (2 before 3); with every entry visited, the dense
+    # argmax (7); exploration samples only list entries, by q_j / Q in list
+    # order
+    w = np.array([0, 1, 4, 4, 0, 6, 0, 9], np.float32)
+    vis = np.zeros(8, np.uint8)
+    lst = np.array([2, 5, 3], np.int32)
+    assert orc.acs_select_nn(w, vis, lst, 0, 0, 1.0) == 5
+    assert orc.acs_select_nn(w, np.array([0, 0, 0, 0, 0, 1, 0, 0], np.uint8), lst, 0, 0, 1.0) == 2
+    all_vis = np.array([0, 0, 1, 1, 0, 1, 0, 0], np.uint8)
+    assert orc.acs_select_nn(w, all_vis, lst, 0, 0, 1.0) == 7
+    assert orc.acs_select_nn(w, all_vis, lst, 0, 0, 0.0) == 7
+    # exploring: T at the very start picks the first list entry (2), the top
+    # of the range the last (3); never a city outside the list
+    assert orc.acs_select_nn(w, vis, lst, 0, 0xffffffff, 0.9) == 2
+    assert orc.acs_select_nn(w, vis, lst, 2**64 - 1, 0xffffffff, 0.9) == 3
+    rng = np.random.default_rng(1)
+    picks = [orc.acs_select_nn(w, vis, lst, int(rng.integers(0, 2**63)) * 2, 0xffffffff, 0.9)
+             for _ in range(2000)]
+    assert set(picks) == {2, 5, 3}
+
+
+def test_acs_lists_pure_exploitation_is_the_dense_greedy_walk(orc):
+    # q0 = 1, xi = 0: tau stays uniform during the first iteration, so the
+    # largest choice_info among unvisited list entries is the nearest
+    # unvisited city whenever one of them is unvisited (the list is sorted by
+    # distance, ties to the lower index like the dense argmax), and the
+    # fallback is the dense argmax itself: the tours equal the dense ones.
+    inst = I.uniform_instance(50, 1000, seed=14)
+    dense = orc.run_acs(inst.dist, 8, 1, 3, q0=1.0, xi=0.0)
+    listed = orc.run_acs(inst.dist, 8, 1, 3, q0=1.0, xi=0.0, nn=6)
+    assert np.array_equal(listed["tours"], dense["tours"])
+
+
+def test_acs_lists_pure_exploration_is_the_list_roulette(orc):
+    # q0 = 0, xi = 0: every step is the restricted roulette of R9 on
+    # choice_info = tau0 * eta^2, so the first iteration equals the Ant
+    # System's list construction on that matrix.
+    inst = I.uniform_instance(60, 1000, seed=15)
+    n, m, nn = 60, 12, 8
+    r = orc.run_acs(inst.dist, m, 1, 7, q0=0.0, xi=0.0, nn=nn)
+    tau0 = np.float32(1.0 / (n * orc.nn_tour_length(inst.dist)))
+    tau = np.where(np.eye(n) > 0, 0, tau0).astype(np.float32)
+    ch = orc.choice(tau, orc.heta(inst.dist, 2.0), 1.0)
+    tours, lens = orc.construct_nn(ch, inst.dist, m, seed=7, iteration=0, nn=nn)
+    assert np.array_equal(r["tours"], tours) and np.array_equal(r["lens"], lens)
+    dense = orc.run_acs(inst.dist, m, 1, 7, q0=0.0, xi=0.0)
+    assert not np.array_equal(dense["tours"], r["tours"])  # the lists do restrict
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (9, 2), (10, 3)])
+def test_acs_lists_reach_brute_force_optimum(orc, n, seed):
+    inst = I.uniform_instance(n, 1000, seed=seed)
+    opt, _ = orc.brute_force(inst.dist)
+    assert orc.run_acs(inst.dist, 10, 60, seed, nn=5)["best_len"] == opt
