@@ -291,7 +291,12 @@ int aco_set_mmas(aco_handle h, double p_best, int32_t best_so_far);
  *    no other cell evaporates.
  * The colony runs in one CTA, so m <= 32 (the variant's usual m is 10).
  * Because construction changes tau, construction calls are not idempotent
- * under this rule.  Nearest-neighbour lists and ACO_OPT_SELECTION do not
+ * under this rule.  With ACO_OPT_NN_LIST the steps use the lists (the
+ * original variant's candidate lists): at city i, if an entry of list(i) is
+ * unvisited, exploitation takes the unvisited entry of largest choice_info
+ * (ties to the earlier entry) and exploration samples Eq. 1 over the
+ * unvisited entries in list order; if every entry is visited, either takes
+ * the unvisited city of largest choice_info.  ACO_OPT_SELECTION does not
  * apply.  Call once, before the first construction (ACO_ESTATE otherwise);
  * q0 and xi must lie in [0, 1] and m <= 32 (ACO_EINVAL).
  */

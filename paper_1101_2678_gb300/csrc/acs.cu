@@ -43,7 +43,10 @@ __device__ __forceinline__ float acs_local(float tau, float keep, float add) {
 
 // One colony in one CTA.  Warp k < m builds ant k's tour; further warps (a
 // launch over colonies with different m sizes the CTA for the largest) take
-// part in the lockstep barriers only.
+// part in the lockstep barriers only.  kNN: with the instance's
+// nearest-neighbour lists (I.nn entries): lane l holds entry l of the
+// current city's list and its current choice_info value.
+template <bool kNN>
 __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* acs_seen,
                                                    uint32_t* s_edge) {
   const int n = I.n, ld = I.ld, m = I.m;
@@ -71,7 +74,47 @@ __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* 
   int cur = start;
   for (int s = 1; s <= n; ++s) {
     int next = start;
-    if (active && s < n) {
+    bool listed = false;  // chosen among the list entries
+    if constexpr (kNN) {
+      if (active && s < n) {
+        const Philox4 x = step_draw(I.seed, (uint32_t)s, (uint32_t)k, it);
+        const float* row = I.choice + (size_t)cur * ld;
+        int j = 0;
+        uint32_t wb = 0u;
+        bool unv = false;
+        if (lane < I.nn) {
+          j = I.nnlist[(size_t)cur * kNnStride + lane];
+          wb = __float_as_uint(row[j]);  // after this colony's local updates
+          unv = !((seen[j >> 5] >> (j & 31)) & 1u);
+        }
+        const unsigned any = __ballot_sync(FULL, unv);
+        if (any) {
+          listed = true;
+          if ((unsigned long long)x.x2 < I.acs_threshold) {
+            // the heaviest unvisited entry, ties to the earlier entry
+            const uint32_t key = unv ? wb + 1u : 0u;
+            const uint32_t top = __reduce_max_sync(FULL, key);
+            next = __shfl_sync(FULL, j, __ffs(__ballot_sync(FULL, key == top)) - 1);
+          } else {
+            // Eq. 1 over the unvisited entries, in list order
+            const uint32_t wm = unv ? wb : 0u;
+            const uint32_t mx = __reduce_max_sync(FULL, wm);
+            if (mx == 0u) {
+              next = __shfl_sync(FULL, j, __ffs(any) - 1);
+            } else {
+              float f1, f1s, f2;
+              quant_factors(kRouletteBits - 1 - exponent_of_bits(mx), f1, f1s, f2);
+              const unsigned long long incl =
+                  warp_incl_scan_u64(quant_value(wm, f1, f1s, f2), lane);
+              const unsigned long long r = ((unsigned long long)x.x1 << 32) | x.x0;
+              const unsigned long long T = __umul64hi(r, __shfl_sync(FULL, incl, 31));
+              next = __shfl_sync(FULL, j, max(__ffs(__ballot_sync(FULL, incl > T)) - 1, 0));
+            }
+          }
+        }
+      }
+    }
+    if (active && s < n && !listed) {
       const Philox4 x = step_draw(I.seed, (uint32_t)s, (uint32_t)k, it);
       const float* row = I.choice + (size_t)cur * ld;
       // Lane l reads cities 4l..4l+3 of every 128 with one 16-byte load (ld
@@ -111,7 +154,8 @@ __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* 
       }
       const uint32_t mbits = bkey - 1u;  // bkey >= 1: a city is unvisited
       next = bj;
-      const bool exploit = (unsigned long long)x.x2 < I.acs_threshold;
+      // with lists, every entry is visited here: the heaviest city, always
+      const bool exploit = kNN || (unsigned long long)x.x2 < I.acs_threshold;
       if (!exploit && mbits != 0u) {
         // Eq. 1 by the integer roulette: q_j = floor(w_j 2^(45 - ilogb M)),
         // T = floor(r Q / 2^64), the first j whose prefix sum exceeds T.
@@ -191,6 +235,12 @@ __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* 
           asm volatile("prefetch.global.L1 [%0];" ::"l"(nrow + f));
       }
     }
+    if constexpr (kNN) {
+      if (active && s < n && (unsigned)next >= (unsigned)n) {  // cannot happen
+        if (lane == 0) atomicOr(&I.st->status, kStatusBadTour);
+        next = start;
+      }
+    }
     // lockstep: every ant has chosen from the same state; then the local
     // updates of this step, one writer per distinct edge applying it once
     // per ant that crossed the edge
@@ -236,10 +286,11 @@ __device__ __forceinline__ void acs_construct_body(const Instance& I, uint32_t* 
   if (lane == 0) I.lens[k] = len;
 }
 
+template <bool kNN>
 __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
   extern __shared__ uint32_t acs_seen[];  // m tabu bitmaps of (n + 31) / 32 words
   __shared__ uint32_t s_edge[32];         // (min << 16 | max) crossed by ant k
-  acs_construct_body(I, acs_seen, s_edge);
+  acs_construct_body<kNN>(I, acs_seen, s_edge);
 }
 
 // Many colonies per launch: CTA b runs the colony of slot slots[b].
@@ -247,7 +298,7 @@ __global__ void __launch_bounds__(1024, 1)
     acs_construct_slots_kernel(const Instance* __restrict__ insts, const int* __restrict__ slots) {
   extern __shared__ uint32_t acs_seen[];
   __shared__ uint32_t s_edge[32];
-  acs_construct_body(insts[slots[blockIdx.x]], acs_seen, s_edge);
+  acs_construct_body<false>(insts[slots[blockIdx.x]], acs_seen, s_edge);
 }
 
 // Global update on the best-so-far tour: edge s of the tour per thread from
@@ -306,7 +357,10 @@ cudaError_t launch_acs_init(const Instance& I, int sms, cudaStream_t st) {
 cudaError_t launch_acs_construct(const Instance& I, cudaStream_t st) {
   if (I.m < 1 || I.m > kAcsMaxAnts) return cudaErrorInvalidValue;
   const size_t smem = (size_t)I.m * ((I.n + 31) / 32) * sizeof(uint32_t);
-  acs_construct_kernel<<<1, 32 * I.m, smem, st>>>(I);
+  if (I.nn > 0)
+    acs_construct_kernel<true><<<1, 32 * I.m, smem, st>>>(I);
+  else
+    acs_construct_kernel<false><<<1, 32 * I.m, smem, st>>>(I);
   return cudaGetLastError();
 }
 

@@ -255,7 +255,8 @@ static int enqueue_update(aco_colony* h) {
                                                                           : h->deposit,
                                                h->sms, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "update");
-  if (h->I.nn > 0 && (e = launch_nn_choice(h->I, h->stream)) != cudaSuccess)
+  // (the Ant Colony System reads its list weights from choice_info itself)
+  if (h->I.nn > 0 && variant != kVariantAcs && (e = launch_nn_choice(h->I, h->stream)) != cudaSuccess)
     return cuda_fail(e, "nn choice");
   if (h->profile && (e = record_event(h, h->ev[4], h->stream)) != cudaSuccess)
     return cuda_fail(e, "event");
@@ -617,8 +618,8 @@ int aco_set_acs(aco_handle h, double q0, float xi) {
   if (h->I.m > kAcsMaxAnts)
     return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants (m=%d)", kAcsMaxAnts,
                 h->I.m);
-  if (h->I.nn > 0 || h->I.rule != 0)
-    return fail(ACO_EINVAL, "the Ant Colony System uses its own rule (no lists, no selection option)");
+  if (h->I.rule != 0)
+    return fail(ACO_EINVAL, "the Ant Colony System uses its own rule (no selection option)");
   if (h->constructed || h->host_iteration != 0 || h->I.variant != kVariantAs)
     return fail(ACO_ESTATE, "the update rule is chosen once, before the first construction");
   h->I.acs_threshold = acs_threshold_of(q0);
@@ -667,7 +668,7 @@ int aco_restore_state(aco_handle h, const void* buf, uint64_t size) {
   const int32_t* best = nullptr;
   int rc = checkpoint_parse(h->I, buf, size, hd, st, tau, best);
   if (rc) return rc;
-  if (hd.variant == kVariantAcs && (h->I.nn > 0 || h->I.rule != 0 || h->I.m > kAcsMaxAnts))
+  if (hd.variant == kVariantAcs && (h->I.rule != 0 || h->I.m > kAcsMaxAnts))
     return fail(ACO_EINVAL, "the Ant Colony System uses its own construction");
   const int n = hd.n;
   cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -735,8 +736,6 @@ int aco_set_option(aco_handle h, int32_t key, int64_t value) {
         return fail(ACO_EINVAL, "nearest-neighbour list length must be in [0, %d]", most);
       if (value > 0 && h->I.rule != 0)
         return fail(ACO_EINVAL, "nearest-neighbour lists use Eq. 1 (ACO_SELECT_EQ1)");
-      if (value > 0 && h->I.variant == kVariantAcs)
-        return fail(ACO_EINVAL, "the Ant Colony System uses its own construction");
       cudaError_t e = cudaSuccess;
       if (value > 0 && !h->nn_lists_built) {
         e = launch_nn_lists(h->I, most, h->stream);
@@ -868,7 +867,7 @@ int aco_kernel_launches_per_iteration(aco_handle h, int32_t* count) {
   *count = (h->I.variant != kVariantAs     ? 3
             : h->deposit == kDepositSort ? 3 + sort_deposit_launches(h->I.n)
                                          : launches_for_variant(h->deposit)) +
-           (h->I.nn > 0 ? 1 : 0) + (h->check ? 1 : 0);
+           (h->I.nn > 0 && h->I.variant != kVariantAcs ? 1 : 0) + (h->check ? 1 : 0);
   return ACO_OK;
 }
 

@@ -88,17 +88,57 @@ def test_acs_argument_and_state_errors(aco):
             with pytest.raises(aco.AcoError) as e:
                 aco.aco_set_acs(c.h, q0, xi)
             assert e.value.code == aco.ACO_EINVAL
-        aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 5)
+        aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_DATA_PARALLEL)
         with pytest.raises(aco.AcoError) as e:
-            aco.aco_set_acs(c.h, 0.9, 0.1)
+            aco.aco_set_acs(c.h, 0.9, 0.1)  # the variant has its own rule
         assert e.value.code == aco.ACO_EINVAL
-        aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 0)
+        aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_EQ1)
         aco.aco_set_acs(c.h, 0.9, 0.1)
         with pytest.raises(aco.AcoError):
-            aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, 5)
+            aco.aco_set_option(c.h, aco.ACO_OPT_SELECTION, aco.ACO_SELECT_EXP_RACE)
         with pytest.raises(aco.AcoError) as e:
             aco.aco_set_mmas(c.h, 0.05, False)
         assert e.value.code == aco.ACO_ESTATE
         aco.aco_iterate(c.h, 2)
         tour, length = aco.aco_best_tour(c.h, 20)
         assert sorted(tour[:-1].tolist()) == list(range(20))
+
+
+def run_gpu_nn(aco, dist, m, iters, seed, rho, q0, xi, nn, lists_first=True):
+    n = dist.shape[0]
+    with aco.Colony(dist, m, seed=seed, rho=rho) as c:
+        if lists_first:
+            aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, nn)
+        aco.aco_set_acs(c.h, q0, xi)
+        if not lists_first:
+            aco.aco_set_option(c.h, aco.ACO_OPT_NN_LIST, nn)
+        aco.aco_iterate(c.h, iters - 1)
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+        aco.aco_update_pheromone(c.h)
+        return dict(tau=aco.aco_get_pheromone(c.h, n), best=aco.aco_best_tour(c.h, n),
+                    tours=tours, lens=lens,
+                    launches=aco.aco_kernel_launches_per_iteration(c.h))
+
+
+@pytest.mark.parametrize("n,m,nn,iters,q0,xi", [(10, 4, 9, 6, 0.9, 0.1), (97, 10, 10, 8, 0.9, 0.1),
+                                                (300, 16, 30, 4, 0.5, 0.2),
+                                                (200, 32, 32, 3, 0.0, 0.1),
+                                                (150, 7, 20, 5, 1.0, 0.3)])
+def test_acs_with_lists_bit_exact(aco, orc, n, m, nn, iters, q0, xi):
+    # reading R16: list-restricted exploitation and exploration, the dense
+    # argmax when a list is exhausted, the lockstep local updates
+    inst = I.clustered_instance(n, seed=80 + n, clusters=5, sigma=150, side=3000)
+    ref = orc.run_acs(inst.dist, m, iters, 23, rho=0.1, q0=q0, xi=xi, nn=nn)
+    g = run_gpu_nn(aco, inst.dist, m, iters, 23, 0.1, q0, xi, nn, lists_first=n % 2 == 0)
+    assert np.array_equal(g["tours"], ref["tours"]) and np.array_equal(g["lens"], ref["lens"])
+    assert np.array_equal(g["tau"], ref["tau32"])
+    assert g["best"][1] == ref["best_len"] and np.array_equal(g["best"][0], ref["best_tour"])
+    assert g["launches"] == 3
+
+
+def test_acs_with_lists_full_size(aco, orc):
+    w = I.workload_n1002()
+    d = w["inst"].dist
+    ref = orc.run_acs(d, 10, 2, w["seed"], nn=30)
+    g = run_gpu_nn(aco, d, 10, 2, w["seed"], 0.1, 0.9, 0.1, 30)
+    assert np.array_equal(g["tours"], ref["tours"]) and np.array_equal(g["tau"], ref["tau32"])
