@@ -422,11 +422,12 @@ int aco_pool_set_mmas(aco_pool_handle p, int32_t slot, double p_best, int32_t be
  * aco_pool_set_nn - nearest-neighbour-list construction for a live slot
  * before its first step, as ACO_OPT_NN_LIST does for a handle (the
  * construction of the paper's Table 2 versions 4-6, Section II): nn = 1 ..
- * min(n - 1, 32) entries, 0 = dense Eq. 1 again.  Composes with the Ant
- * System and the MAX-MIN Ant System (not with the Ant Colony System:
- * ACO_EINVAL either way round).  All list slots of a pool construct in one
- * launch (one warp per ant) and refresh their list-ordered choice_info after
- * each update.  ACO_ESTATE after the slot's first step.
+ * min(n - 1, 32) entries, 0 = dense Eq. 1 again.  Composes with all three
+ * rules (the Ant Colony System as with ACO_OPT_NN_LIST on a handle).  All
+ * Ant System and MAX-MIN list slots of a pool construct in one launch (one
+ * warp per ant) and refresh their list-ordered choice_info after each
+ * update; Ant Colony System colonies with lists run in one launch of their
+ * own.  ACO_ESTATE after the slot's first step.
  */
 int aco_pool_set_nn(aco_pool_handle p, int32_t slot, int32_t nn);
 

@@ -293,12 +293,14 @@ __global__ void __launch_bounds__(1024, 1) acs_construct_kernel(Instance I) {
   acs_construct_body<kNN>(I, acs_seen, s_edge);
 }
 
-// Many colonies per launch: CTA b runs the colony of slot slots[b].
+// Many colonies per launch: CTA b runs the colony of slot slots[b] (all of
+// them with lists, or all without).
+template <bool kNN>
 __global__ void __launch_bounds__(1024, 1)
     acs_construct_slots_kernel(const Instance* __restrict__ insts, const int* __restrict__ slots) {
   extern __shared__ uint32_t acs_seen[];
   __shared__ uint32_t s_edge[32];
-  acs_construct_body<false>(insts[slots[blockIdx.x]], acs_seen, s_edge);
+  acs_construct_body<kNN>(insts[slots[blockIdx.x]], acs_seen, s_edge);
 }
 
 // Global update on the best-so-far tour: edge s of the tour per thread from
@@ -370,11 +372,14 @@ cudaError_t launch_acs_global(const Instance& I, cudaStream_t st) {
 }
 
 cudaError_t launch_acs_construct_slots(const Instance* insts, const int* slots, int count,
-                                       int max_m, int max_n, cudaStream_t st) {
+                                       int max_m, int max_n, bool lists, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   if (max_m < 1 || max_m > kAcsMaxAnts) return cudaErrorInvalidValue;
   const size_t smem = (size_t)max_m * ((max_n + 31) / 32) * sizeof(uint32_t);
-  acs_construct_slots_kernel<<<count, 32 * max_m, smem, st>>>(insts, slots);
+  if (lists)
+    acs_construct_slots_kernel<true><<<count, 32 * max_m, smem, st>>>(insts, slots);
+  else
+    acs_construct_slots_kernel<false><<<count, 32 * max_m, smem, st>>>(insts, slots);
   return cudaGetLastError();
 }
 

@@ -52,9 +52,10 @@ cudaError_t launch_acs_init(const Instance& I, int sms, cudaStream_t st);
 cudaError_t launch_acs_construct(const Instance& I, cudaStream_t st);
 cudaError_t launch_acs_global(const Instance& I, cudaStream_t st);
 // The same for `count` colonies insts[slots[b]] per launch (one CTA each,
-// sized for the largest m and n among them).
+// sized for the largest m and n among them; lists: all of them construct
+// with their nearest-neighbour lists).
 cudaError_t launch_acs_construct_slots(const Instance* insts, const int* slots, int count,
-                                       int max_m, int max_n, cudaStream_t st);
+                                       int max_m, int max_n, bool lists, cudaStream_t st);
 cudaError_t launch_acs_global_slots(const Instance* insts, const int* slots, int count,
                                     cudaStream_t st);
 int gather_warps_per_cta(int ld);

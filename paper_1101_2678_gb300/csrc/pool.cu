@@ -131,6 +131,7 @@ struct aco_pool {
   // host mirrors of the lists
   std::vector<int> h_live, h_acs, h_cls_slots;
   int acs_max_m = 0, acs_max_n = 0;
+  int acs_dense = 0;  // h_acs holds the colonies without lists first, then those with
   // Multi-rate stepping: each class (and the colonies) runs `k` iterations
   // per step, chosen so that short instances keep pace with the longest.
   bool multirate = false;
@@ -261,12 +262,15 @@ static int pool_rebuild(aco_pool* p) {
   // Ant Colony System slots: one CTA per colony in one launch of their own
   // (MAX-MIN Ant System slots construct and update with the Ant System ones:
   // the best and row-update kernels follow each slot's rule)
-  for (int s : live) {
-    const PoolSlot& sl = p->slots[(size_t)s];
-    if (sl.I.variant != kVariantAcs) continue;
-    p->h_acs.push_back(s);
-    p->acs_max_m = std::max(p->acs_max_m, sl.m);
-    p->acs_max_n = std::max(p->acs_max_n, sl.n);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int s : live) {
+      const PoolSlot& sl = p->slots[(size_t)s];
+      if (sl.I.variant != kVariantAcs || (sl.I.nn > 0) != (pass == 1)) continue;
+      p->h_acs.push_back(s);
+      p->acs_max_m = std::max(p->acs_max_m, sl.m);
+      p->acs_max_n = std::max(p->acs_max_n, sl.n);
+    }
+    if (pass == 0) p->acs_dense = (int)p->h_acs.size();
   }
   // group the Ant System slots by tiling class, keeping the longest-first
   // order inside a class
@@ -449,10 +453,15 @@ static int pool_enqueue_step(aco_pool* p) {
   const int first = nacs > 0 ? 1 : 0;
   if (nacs > 0) {
     cudaStream_t st = nstreams > 1 ? p->class_stream[0] : p->stream;
+    const int nd = p->acs_dense;
     for (int r = 0; r < (mr ? p->acs_k : 1); ++r) {
-      e = launch_acs_construct_slots(p->d_inst, p->d_acs, nacs, p->acs_max_m, p->acs_max_n, st);
+      e = launch_acs_construct_slots(p->d_inst, p->d_acs, nd, p->acs_max_m, p->acs_max_n, false,
+                                     st);
+      if (e == cudaSuccess)
+        e = launch_acs_construct_slots(p->d_inst, p->d_acs + nd, nacs - nd, p->acs_max_m,
+                                       p->acs_max_n, true, st);
       if (e != cudaSuccess) return cuda_fail(e, "pool acs construct");
-      ++launches;
+      launches += (nd > 0 ? 1 : 0) + (nacs > nd ? 1 : 0);
       if (!mr) break;
       if ((e = launch_best_slots(p->d_inst, p->d_acs, nacs, st)) != cudaSuccess)
         return cuda_fail(e, "pool acs best");
@@ -753,8 +762,6 @@ int aco_pool_set_acs(aco_pool_handle p, int32_t slot, double q0, float xi) {
   const int m = p->slots[(size_t)slot].m;
   if (m > kAcsMaxAnts)
     return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants (m=%d)", kAcsMaxAnts, m);
-  if (p->slots[(size_t)slot].I.nn > 0)
-    return fail(ACO_EINVAL, "the Ant Colony System uses its own construction (no lists)");
   return pool_switch_rule(p, slot, [&](Instance& I) {
     I.variant = kVariantAcs;
     I.acs_threshold = acs_threshold_of(q0);
@@ -861,8 +868,6 @@ int aco_pool_set_nn(aco_pool_handle p, int32_t slot, int32_t nn) {
   const int most = std::min(sl.n - 1, kNnStride);
   if (nn < 0 || nn > most)
     return fail(ACO_EINVAL, "nearest-neighbour list length must be in [0, %d]", most);
-  if (nn > 0 && sl.I.variant == kVariantAcs)
-    return fail(ACO_EINVAL, "the Ant Colony System uses its own construction");
   Instance& I = sl.I;
   cudaError_t e = cudaSuccess;
   // on the side stream after the admission's setup (and any rule switch)
@@ -932,9 +937,8 @@ int aco_pool_restore_slot(aco_pool_handle p, int32_t slot, const void* buf, uint
   const int32_t* best = nullptr;
   int rc = checkpoint_parse(sl.I, buf, size, hd, st, tau, best);
   if (rc) return rc;
-  if (hd.variant == kVariantAcs && (sl.m > kAcsMaxAnts || sl.I.nn > 0))
-    return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants, without lists",
-                kAcsMaxAnts);
+  if (hd.variant == kVariantAcs && sl.m > kAcsMaxAnts)
+    return fail(ACO_EINVAL, "the Ant Colony System runs at most %d ants", kAcsMaxAnts);
   Instance& I = sl.I;
   I.variant = hd.variant;
   I.mmas_best_so_far = hd.mmas_best_so_far;

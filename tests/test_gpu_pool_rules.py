@@ -418,13 +418,6 @@ def test_nn_list_slot_errors(aco):
                 aco.aco_pool_set_nn(p, s, bad)
             assert e.value.code == aco.ACO_EINVAL
         aco.aco_pool_set_nn(p, s, 8)
-        with pytest.raises(aco.AcoError) as e:
-            aco.aco_pool_set_acs(p, s, 0.9, 0.1)
-        assert e.value.code == aco.ACO_EINVAL
-        c = aco.aco_pool_admit_acs(p, x.dist, 1.0, 2.0, 0.1, 10, 2, 3, 0.9, 0.1)
-        with pytest.raises(aco.AcoError) as e:
-            aco.aco_pool_set_nn(p, c, 8)
-        assert e.value.code == aco.ACO_EINVAL
         aco.aco_pool_step(p)
         with pytest.raises(aco.AcoError) as e:
             aco.aco_pool_set_nn(p, s, 4)
@@ -432,5 +425,39 @@ def test_nn_list_slot_errors(aco):
         with pytest.raises(aco.AcoError) as e:
             aco.aco_pool_tiling(p, s)
         assert e.value.code == aco.ACO_EINVAL
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+def test_colonies_with_lists_in_a_pool(aco, orc):
+    # colonies with and without lists in one pool (two colony launches per
+    # step), lists set before or after the switch: each equals the oracle's
+    # R16 / R14 run
+    cases = [(60, 10, 8, 5, 51, True), (97, 16, 20, 4, 52, False), (130, 10, 0, 4, 53, True),
+             (40, 8, 12, 6, 54, False)]
+    insts = {n: I.clustered_instance(n, seed=n + 11, clusters=5, sigma=150, side=3000)
+             for n, *_r in cases}
+    need = sum(aco.aco_pool_bytes_needed(n, m) for n, m, *_r in cases)
+    p = aco.aco_pool_create(8, need + (1 << 20))
+    try:
+        slots = {}
+        for n, m, nn, iters, seed, lists_first in cases:
+            s = aco.aco_pool_admit(p, insts[n].dist, 1.0, 2.0, 0.1, m, seed, iters)
+            if nn and lists_first:
+                aco.aco_pool_set_nn(p, s, nn)
+            aco.aco_pool_set_acs(p, s, 0.9, 0.1)
+            if nn and not lists_first:
+                aco.aco_pool_set_nn(p, s, nn)
+            slots[n] = s
+        aco.aco_pool_step(p)
+        assert aco.aco_pool_stats(p)["launches_last_step"] == 4
+        while aco.aco_pool_step(p) > 0:
+            pass
+        aco.aco_pool_synchronize(p)
+        for n, m, nn, iters, seed, _ in cases:
+            ref = orc.run_acs(insts[n].dist, m, iters, seed, rho=0.1, q0=0.9, xi=0.1, nn=nn)
+            assert np.array_equal(aco.aco_pool_pheromone(p, slots[n], n), ref["tau32"]), n
+            tour, length = aco.aco_pool_result(p, slots[n], n)
+            assert length == ref["best_len"] and np.array_equal(tour, ref["best_tour"]), n
     finally:
         aco.aco_pool_destroy(p)
