@@ -203,6 +203,54 @@ def test_heta_is_inverse_distance_power(orc):
         assert err.max() <= 2.0 ** -23
 
 
+# --------------------------------------------------------------------------
+# choice_info = tau^alpha * eta^beta (Section III-A, the choice kernel)
+# --------------------------------------------------------------------------
+
+# (tau, alpha, tau^alpha) with every power exactly representable, so the
+# expected value is exact whatever the pow implementation's rounding.
+_EXACT_POWERS = [
+    (4.0, 0.5, 2.0), (9.0, 0.5, 3.0), (0.25, 0.5, 0.5), (2.0 ** -4, 0.5, 2.0 ** -2),
+    (4.0, 1.5, 8.0), (2.0 ** -4, 1.5, 2.0 ** -6), (0.25, 1.5, 0.125), (9.0, 1.5, 27.0),
+    (3.0, 2.0, 9.0), (2.0 ** -4, 2.0, 2.0 ** -8), (5.0, 2.0, 25.0),
+    (3.0, 3.0, 27.0), (0.5, 3.0, 0.125), (16.0, 0.25, 2.0), (2.0 ** -8, 0.25, 0.25),
+]
+
+
+@pytest.mark.parametrize("alpha", sorted({a for _, a, _ in _EXACT_POWERS}))
+def test_choice_info_powers_of_tau(orc, alpha):
+    # Cells (i, j) with different tau and heta in the two halves, so that a
+    # swapped base and exponent, a dropped exponent, tau and heta read from
+    # different cells, or a missing heta factor all change some cell.
+    cases = [(t, p) for t, a, p in _EXACT_POWERS if a == alpha]
+    n = 2 * len(cases) + 1
+    tau = np.zeros((n, n), np.float32)
+    heta = np.zeros((n, n), np.float32)
+    want = np.zeros((n, n), np.float64)
+    hvals = [0.75, 1.25, 0.5, 3.0, 0.375]
+    for k, (t, p) in enumerate(cases):
+        i, j = 2 * k, 2 * k + 1
+        h = hvals[k % len(hvals)]
+        tau[i, j], heta[i, j], want[i, j] = t, h, p * h      # exact: p and h have short significands
+        tau[j, i], heta[j, i], want[j, i] = 1.0, 2.0 * h, 2.0 * h   # 1^alpha = 1
+    ch = orc.choice(tau, heta, alpha).astype(np.float64)
+    assert np.array_equal(ch, want)
+
+
+def test_choice_info_alpha_one_and_zero(orc):
+    # alpha = 1: the correctly rounded product tau * heta (the exact product
+    # of two floats fits in a double; one rounding to float).  alpha = 0:
+    # heta itself, whatever tau is (0^0 = 1 included).
+    rng = np.random.default_rng(7)
+    n = 64
+    tau = rng.uniform(1e-6, 3.0, (n, n)).astype(np.float32)
+    tau[0, :8] = 0.0
+    heta = rng.uniform(1e-8, 1.0, (n, n)).astype(np.float32)
+    exact = tau.astype(np.float64) * heta.astype(np.float64)
+    assert np.array_equal(orc.choice(tau, heta, 1.0), exact.astype(np.float32))
+    assert np.array_equal(orc.choice(tau, heta, 0.0), heta)
+
+
 def test_nearest_neighbour_tour_closed_forms(orc):
     # cities on a line at x = 0..n-1: the NN tour walks out and back, 2(n-1)
     n = 12
