@@ -7,8 +7,10 @@
  * path shares no code with it: nothing here is included by, linked into or
  * generated for the kernels, and nothing here reads anything the kernels wrote.
  *
- * It is deliberately plain and slow: single-threaded loops over cities and
- * ants, in the order the paper states the algorithm (Section II):
+ * It is deliberately plain and slow: loops over cities and ants, in the order
+ * the paper states the algorithm (Section II).  Only the independent ants of
+ * one construction may be spread over host threads (orc_set_threads; one by
+ * default); every other part is single-threaded:
  *
  *   repeat:  choice_info = tau^alpha * eta^beta          (Section III-A, "choice kernel")
  *            every ant builds a tour with Eq. 1          (Section II)
@@ -126,6 +128,8 @@
  * -ffp-contract=off matters: a fused multiply-add would change the rounding of
  * fl(fl(a*b)+c).
  */
+#include <pthread.h>
+#include <unistd.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -502,13 +506,72 @@ int64_t orc_construct_ant_nn(int n, const float *choice, const int32_t *d, uint6
     return len;
 }
 
+/* Ants are independent within an iteration (Section II: each builds its tour
+   from the same choice_info), so the construction may be split across host
+   threads, ant k always computed by the same code and with the same counters:
+   the result does not depend on the thread count.  One thread by default. */
+static int g_threads = 1;
+
+int orc_set_threads(int threads)
+{
+    if (threads < 1) threads = 1;
+    if (threads > 512) threads = 512;
+    g_threads = threads;
+    return g_threads;
+}
+
+int orc_get_threads(void) { return g_threads; }
+
+int orc_hardware_threads(void)
+{
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    return c < 1 ? 1 : (int)c;
+}
+
+struct construct_job {
+    int n, rule, nn, k0, k1;
+    const float *choice;
+    const int32_t *d, *lists;
+    uint64_t seed;
+    uint32_t iteration;
+    int32_t *tours;
+    int64_t *lens;
+};
+
+static void *construct_worker(void *arg)
+{
+    struct construct_job *j = (struct construct_job *)arg;
+    for (int k = j->k0; k < j->k1; ++k)
+        j->lens[k] = orc_construct_ant_nn(j->n, j->choice, j->d, j->seed, j->iteration,
+                                          (uint32_t)k, j->rule, j->nn, j->lists,
+                                          j->tours + (size_t)k * (j->n + 1));
+    return NULL;
+}
+
 void orc_construct_nn(int n, int m, const float *choice, const int32_t *d, uint64_t seed,
                       uint32_t iteration, int rule, int nn, const int32_t *lists,
                       int32_t *tours, int64_t *lens)
 {
-    for (int k = 0; k < m; ++k)
-        lens[k] = orc_construct_ant_nn(n, choice, d, seed, iteration, (uint32_t)k, rule, nn,
-                                       lists, tours + (size_t)k * (n + 1));
+    int t = g_threads < m ? g_threads : m;
+    struct construct_job jobs[512];
+    pthread_t th[512];
+    for (int i = 0; i < t; ++i) {
+        jobs[i] = (struct construct_job){n, rule, nn, (int)((int64_t)m * i / t),
+                                         (int)((int64_t)m * (i + 1) / t), choice, d, lists,
+                                         seed, iteration, tours, lens};
+    }
+    if (t <= 1) {
+        if (m > 0) construct_worker(&jobs[0]);
+        return;
+    }
+    int started = 0;
+    for (int i = 1; i < t; ++i) {
+        if (pthread_create(&th[i], NULL, construct_worker, &jobs[i]) != 0) break;
+        started = i;
+    }
+    construct_worker(&jobs[0]);
+    for (int i = started + 1; i < t; ++i) construct_worker(&jobs[i]);  /* threads not started */
+    for (int i = 1; i <= started; ++i) pthread_join(th[i], NULL);
 }
 
 void orc_construct_rule(int n, int m, const float *choice, const int32_t *d, uint64_t seed,

@@ -27,7 +27,7 @@ def build(force: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, SRC, "-lm"]
+           "-shared", "-o", tmp, SRC, "-lm", "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
@@ -47,6 +47,12 @@ def lib():
             f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
             f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
             L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = C.c_int
+            L.orc_get_threads.argtypes = []
+            L.orc_get_threads.restype = C.c_int
+            L.orc_hardware_threads.argtypes = []
+            L.orc_hardware_threads.restype = C.c_int
             L.orc_philox4x32_10.restype = None
             L.orc_ceil_log2.argtypes = [C.c_int64]
             L.orc_ceil_log2.restype = C.c_int
@@ -140,6 +146,21 @@ def lib():
 
 def _i32(a):
     return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def set_threads(threads: int) -> int:
+    """Host threads for the ants of one construction (1 = the plain loop).
+    The results do not depend on it.  Returns the count in effect."""
+    return int(lib().orc_set_threads(int(threads)))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def hardware_threads() -> int:
+    """Online host cores (sysconf), the count an all-core run uses."""
+    return int(lib().orc_hardware_threads())
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

@@ -304,6 +304,44 @@ def test_symmetric_update_full_size_equals_gather(aco, wl):
         assert np.array_equal(out["GATHER"][1], out[v][1]), v
 
 
+@pytest.fixture
+def orc_all_cores(orc):
+    # The ants of one oracle construction spread over every host core (the
+    # result does not depend on the thread count); back to one thread after.
+    orc.set_threads(orc.hardware_threads())
+    yield orc
+    orc.set_threads(1)
+
+
+@pytest.mark.parametrize("wl,checkpoints", [("workload_n1002", (1, 2, 50)),
+                                            ("workload_n2392", (1, 2, 20))])
+def test_full_size_pheromone_matches_oracle(aco, orc_all_cores, wl, checkpoints):
+    # The bench's configurations with the library's default update (the
+    # upper-triangle deposit), after the first iteration, the second, and the
+    # configuration's full count (Eqs. 2-4; tolerance of reading R5): tau and
+    # choice_info equal the oracle's FP32 mirror bit for bit, and tau lies
+    # within 1e-5 relative (+2^-126) of the FP64 recurrence on the same tours.
+    orc = orc_all_cores
+    w = getattr(I, wl)()
+    d, m, seed = w["inst"].dist, w["m"], w["seed"]
+    n = d.shape[0]
+    h = orc.heta(d, 2.0)
+    with aco.Colony(d, m, seed=seed) as c:
+        assert aco.aco_get_option(c.h, aco.ACO_OPT_DEPOSIT) == aco.ACO_DEPOSIT_SYMMETRIC
+        done = 0
+        for it in checkpoints:
+            aco.aco_iterate(c.h, it - done)
+            done = it
+            ref = orc.run(d, m, it, seed)
+            tau = aco.aco_get_pheromone(c.h, n)
+            assert np.array_equal(tau, ref["tau32"]), f"tau differs after {it} iterations"
+            r64 = ref["tau64"]
+            assert np.all(np.abs(tau.astype(np.float64) - r64) <= 1e-5 * np.abs(r64) + 2.0 ** -126)
+            assert np.array_equal(aco.aco_choice_info(c.h, n), orc.choice(ref["tau32"], h, 1.0))
+            tour, best = aco.aco_best_tour(c.h, n)
+            assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+
+
 def test_update_invariants_at_full_size(aco):
     # n = 1002 after two iterations: tau symmetric, valid tours, and one
     # update's deposit totals 2 n sum_k 1/C^k (Eqs. 3-4).

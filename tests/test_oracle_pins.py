@@ -865,3 +865,20 @@ def test_acs_lists_reach_brute_force_optimum(orc, n, seed):
     inst = I.uniform_instance(n, 1000, seed=seed)
     opt, _ = orc.brute_force(inst.dist)
     assert orc.run_acs(inst.dist, 10, 60, seed, nn=5)["best_len"] == opt
+
+
+def test_threaded_construction_equals_the_plain_loop(orc):
+    # Splitting the independent ants of a construction across host threads
+    # (the all-core timing mode) changes nothing in a run.
+    inst = I.uniform_instance(150, 1000, seed=41)
+    try:
+        orc.set_threads(1)
+        one = orc.run(inst.dist, 150, 3, 5)
+        assert orc.set_threads(7) == 7
+        many = orc.run(inst.dist, 150, 3, 5)
+    finally:
+        orc.set_threads(1)
+    for k in ("tau32", "tau64", "tours", "lens", "best_tour", "iter_best"):
+        assert np.array_equal(one[k], many[k]), k
+    assert one["best_len"] == many["best_len"]
+    assert orc.hardware_threads() >= 1
