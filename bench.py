@@ -6,11 +6,15 @@ graph through the C ABI with all state resident in HBM.  Between timed steps
 L2 is flushed by writing a 256 MB buffer (outside the timed region); each step
 is timed with CUDA events on the stream the library launches on.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n1002]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n2392]
                   [--deposit sym|gather|u64|f32] [--impl ours|reference]
 
---impl reference times the CPU oracle (the slow, plain restatement of the
-method used by the tests) on a bounded sample of the same workload.
+The default workload is 2392 clustered cities with m = 2392 ants (the size of
+the paper's largest instance, pr2392).  Its line also carries the batched
+workload (256 instances in one pool against the per-instance loop) and the
+CPU oracle on every host core.  --impl reference times the CPU oracle (the
+slow, plain restatement of the method used by the tests) on every host core,
+in steps of whole iterations or of a measured sample of ants.
 With N > 1 (torchrun) every rank runs an independent replica of the workload
 (no data-path collective: the instances are independent); the reported value
 is the sum over ranks divided by the slowest rank's time.
@@ -46,12 +50,18 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="n1002", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="n2392", choices=sorted(WORKLOADS))
     ap.add_argument("--deposit", default="sym", choices=["gather", "u64", "f32", "sym", "sort"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dist-timeout", type=float, default=600.0,
                     help="seconds a rank waits in a barrier or collective for the others")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="single-instance workloads: skip the batched line carried in the "
+                         "same JSON line (the 256-instance pool against the per-instance loop)")
+    ap.add_argument("--ants", type=int, default=0,
+                    help="override m (0 = the workload's m); for small profiling captures of "
+                         "the same kernel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--warps-per-ant", type=int, default=0, help="0 = library default")
     ap.add_argument("--ants-per-cta", type=int, default=0, help="0 = library default")
@@ -195,40 +205,50 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def measure_l2_copy_gbs(reps: int = 64, mib: int = 24, trials: int = 5) -> float:
-    """L2 copy bandwidth: torch copies between two L2-resident buffers.
+L2_PROBE_MIB = 24
 
-    Same method as the HBM figure of MEASURED_PEAKS.json (read + write bytes
-    of b.copy_(a), CUDA events), but on 2 x `mib` MiB, which stay in the
-    129 MB L2, with `reps` back-to-back copies replayed from one CUDA graph
-    so launch gaps do not count; best of `trials`."""
+
+def measure_l2_read_gbs(trials: int = 10, reps: int = 64):
+    """Read-only L2 bandwidth, measured in this run with the library's probe.
+
+    A 24 MiB buffer (L2-resident: the L2 holds 129 MB) is read `reps` times per
+    launch, either by 16-byte loads that bypass L1 or by 16 KB bulk copies into
+    shared memory (the construction kernel's route); each launch is timed with
+    CUDA events on its stream, best of `trials`, over a few grid sizes.
+    Returns {"float4": GB/s, "bulk": GB/s, "peak": the larger, ...}."""
     import torch
-    a = torch.empty(mib << 18, dtype=torch.float32, device="cuda").normal_()
-    b = torch.empty_like(a)
+    from paper_1101_2678_gb300 import aco
+    nbytes = L2_PROBE_MIB << 20
+    buf = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda").uniform_(0.0, 1.0)
+    sink = torch.zeros(4, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
     s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
+    out = {}
     with torch.cuda.stream(s):
-        for _ in range(3):
-            b.copy_(a)
-    torch.cuda.current_stream().wait_stream(s)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        for _ in range(reps):
-            b.copy_(a)
-    g.replay()
+        for mode, name, grids in ((0, "float4", (2, 4, 8)), (1, "bulk", (2, 3, 6))):
+            best = 0.0
+            for bps in grids:
+                for t in range(trials + 2):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    aco.aco_stream_read(buf.data_ptr(), nbytes, reps, mode, bps, s.cuda_stream,
+                                        sink.data_ptr(), status.data_ptr())
+                    e1.record(s)
+                    e1.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    if t >= 2 and ms > 0:  # the first two launches warm up
+                        best = max(best, reps * nbytes / (ms / 1e3) / 1e9)
+            out[name] = best
     torch.cuda.synchronize()
-    best = 0.0
-    for _ in range(trials):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        g.replay()
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        if ms > 0:
-            best = max(best, reps * 2 * a.numel() * 4 / (ms / 1e3) / 1e9)
-    return best
+    if int(status.item()) != 0:
+        raise RuntimeError("the bulk-copy read probe reported a timed-out wait")
+    out["peak"] = max(out["float4"], out["bulk"])
+    out["how"] = (f"aco_stream_read over a {L2_PROBE_MIB} MiB L2-resident buffer, {reps} "
+                  f"passes per launch, CUDA events, best of {trials} over grids of 2-8 CTAs "
+                  f"per SM; float4 = 16-byte ld.global.cg loads, bulk = 16 KB cp.async.bulk "
+                  f"copies into shared memory")
+    return out
 
 
 def measured_peaks():
@@ -242,85 +262,107 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample(w, ants: int):
-    """Time the oracle on `ants` ants of iteration 0 plus one full update.
+class OracleStep:
+    """Timed steps of the CPU oracle on a workload.
 
-    Returns (ant_steps_per_s, seconds, description)."""
-    import numpy as np
-    from oracle import oracle as orc
-    d = w["inst"].dist
-    n, m = d.shape[0], w["m"]
-    t0 = time.perf_counter()
-    h = orc.heta(d, w["beta"])
-    tau = np.full((n, n), orc.tau0(d, m), np.float32)
-    np.fill_diagonal(tau, 0)
-    ch = orc.choice(tau, h, w["alpha"])
-    t_setup = time.perf_counter() - t0
-    ants = max(1, min(ants, m))
-    t0 = time.perf_counter()
-    tours = np.zeros((m, n + 1), np.int32)
-    lens = np.zeros(m, np.int64)
-    for k in range(ants):
-        tours[k], lens[k] = orc.construct_ant(ch, d, w["seed"], 0, k)
-    t_con = time.perf_counter() - t0
-    # the other ants' tours are copies for the update (same work per edge)
-    for k in range(ants, m):
-        tours[k], lens[k] = tours[k % ants], lens[k % ants]
-    t0 = time.perf_counter()
-    tau = orc.update_mirror(tau, tours, lens, w["rho"])
-    ch = orc.choice(tau, h, w["alpha"])
-    t_upd = time.perf_counter() - t0
-    per_iter = t_con / ants * m + t_upd
-    value = m * (n - 1) / per_iter
-    desc = (f"oracle (C, 1 thread): {ants} of {m} ants of iteration 0 constructed plus one "
-            f"full pheromone update and choice_info; iteration time extrapolated as "
-            f"t_ant*m + t_update (setup {t_setup:.2f}s not counted)")
-    return value, t_con + t_upd, desc
+    A step builds the first `ants` ants of iteration 0 with Eq. 1 (ant k uses
+    the same counters as in a whole iteration) on `threads` host threads, then
+    runs the pheromone update (Eqs. 2-4) with their tours and choice_info.
+    With ants = m a step is one whole iteration.  Setup (eta^beta, tau0, the
+    first choice_info) happens once, outside the timed steps."""
+
+    def __init__(self, w):
+        import numpy as np
+        from oracle import oracle as orc
+        orc.build()
+        self.orc, self.w = orc, w
+        self.d = w["inst"].dist
+        self.n, self.m = self.d.shape[0], w["m"]
+        self.h = orc.heta(self.d, w["beta"])
+        self.tau = np.full((self.n, self.n), orc.tau0(self.d, self.m), np.float32)
+        np.fill_diagonal(self.tau, 0)
+        self.ch = orc.choice(self.tau, self.h, w["alpha"])
+
+    def run(self, ants: int, threads: int):
+        """(seconds, ant-steps) of one step."""
+        orc, w = self.orc, self.w
+        ants = max(1, min(ants, self.m))
+        orc.set_threads(threads)
+        try:
+            t0 = time.perf_counter()
+            tours, lens = orc.construct(self.ch, self.d, ants, w["seed"], 0)
+            tau = orc.update_mirror(self.tau, tours, lens, w["rho"])
+            orc.choice(tau, self.h, w["alpha"])
+            sec = time.perf_counter() - t0
+        finally:
+            orc.set_threads(1)
+        return sec, ants * (self.n - 1)
+
+    def ants_for(self, seconds: float, threads: int) -> int:
+        """Ants whose step takes about `seconds` (calibrated on a short step)."""
+        probe = min(self.m, 4 * max(threads, 1))
+        sec, _ = self.run(probe, threads)
+        per_ant = sec / probe
+        return max(1, min(self.m, int(seconds / max(per_ant, 1e-9))))
+
+    def describe(self, ants: int, threads: int) -> str:
+        what = ("whole iterations" if ants >= self.m else
+                f"the first {ants} of {self.m} ants of an iteration")
+        return (f"oracle (C, {threads} host thread{'s' if threads > 1 else ''}): {what} built "
+                f"with Eq. 1, then the full pheromone update and choice_info over their tours; "
+                f"value = ant-steps built / measured step time")
+
+
+def cpu_baseline(w):
+    """The oracle on every host core (whole iterations if one takes under
+    ~20 s, else a timed sample of ants of about that length) and on one core
+    (a timed sample of about 5 s); each figure is measured, not extrapolated."""
+    o = OracleStep(w)
+    hw = o.orc.hardware_threads()
+    ants = o.ants_for(20.0, hw)
+    sec, units = o.run(ants, hw)
+    one_ants = o.ants_for(5.0, 1)
+    sec1, units1 = o.run(one_ants, 1)
+    return {"value": units / sec, "unit": "ant-steps/s", "cores": hw, "kind": "oracle",
+            "sample": o.describe(ants, hw), "seconds": sec, "hardware_threads": hw,
+            "one_core": {"value": units1 / sec1, "unit": "ant-steps/s", "cores": 1,
+                         "sample": o.describe(one_ants, 1), "seconds": sec1}}
 
 
 def run_reference(args, w, rank, world):
+    """--impl reference: the CPU oracle on every host core, K timed steps after
+    W warm-up steps, each step sized so the whole run stays within ~3 minutes
+    (whole iterations when they fit)."""
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    from oracle import oracle as orc
-    orc.build()
-    d = w["inst"].dist
-    n, m = d.shape[0], w["m"]
-    ants = max(1, min(m, int(2.0 / max(_oracle_ant_seconds(w), 1e-6))))
+    o = OracleStep(w)
+    hw = o.orc.hardware_threads()
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    ants = o.ants_for(budget, hw)
     for _ in range(args.warmup):
-        oracle_sample(w, max(1, ants // 4))
-    vals, secs = [], 0.0
+        o.run(ants, hw)
+    secs, units = 0.0, 0
     for _ in range(args.steps):
-        v, s, desc = oracle_sample(w, ants)
-        vals.append(v)
-        secs += s
-    value = statistics.mean(vals)
+        sec, u = o.run(ants, hw)
+        secs += sec
+        units += u
+    value = units / secs
+    n, m = o.n, o.m
+    desc = o.describe(ants, hw)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ant-steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": m * (n - 1) / value * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "n": n, "m": m, "iterations": w["iterations"],
-                   "parallelism": "cpu-1-thread", "l2": "n/a (host)"},
-        "cpu_baseline": {"value": value, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
+                   "ants_per_step": ants, "parallelism": f"cpu-{hw}-threads",
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "ant-steps/s", "cores": hw, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "ant-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-def _oracle_ant_seconds(w):
-    import numpy as np
-    from oracle import oracle as orc
-    d = w["inst"].dist
-    n, m = d.shape[0], w["m"]
-    h = orc.heta(d, w["beta"])
-    tau = np.full((n, n), orc.tau0(d, m), np.float32)
-    ch = orc.choice(tau, h, w["alpha"])
-    t0 = time.perf_counter()
-    orc.construct_ant(ch, d, w["seed"], 0, 0)
-    return time.perf_counter() - t0
 
 
 # ---------------------------------------------------------------------------
@@ -336,6 +378,8 @@ def run_ours(args, w, rank, world, local):
     aco.load()
     d = w["inst"].dist
     n, m = d.shape[0], w["m"]
+    if args.ants:
+        m = args.ants
     if args.variant == "acs":
         m = min(m, 10)  # the Ant Colony System's usual colony (one CTA, m <= 32)
     dep = {"gather": aco.ACO_DEPOSIT_GATHER, "u64": aco.ACO_DEPOSIT_ATOMIC_U64,
@@ -416,6 +460,12 @@ def run_ours(args, w, rank, world, local):
     if not args.no_e2e:
         e2e = e2e_solve(aco, w, rank, m, configure)
 
+    # The batched workload (256 instances in one pool against the per-instance
+    # loop), carried in the same line.
+    batched = None
+    if not args.no_batched and args.variant == "as" and not args.ants:
+        batched = batched_measure(args, rank, world, local)
+
     if rank != 0:
         return
     peaks, peak_kind = measured_peaks()
@@ -425,21 +475,16 @@ def run_ours(args, w, rank, world, local):
         kernel = "construct_nn_kernel"
     else:
         kernel = "construct_kernel"
-    roof = construct_roofline(n, m, con_ms, peaks, peak_kind, kernel=kernel, nn=args.nn)
+    l2 = measure_l2_read_gbs()
+    roof = construct_roofline(n, m, con_ms, l2, peaks, peak_kind, kernel=kernel, nn=args.nn)
     if not (args.nn or args.selection != "eq1" or args.lanes_per_ant or args.warps_per_ant
             or args.ants_per_cta or args.variant != "as"):
-        roof["traffic"], roof["traffic_source"] = recorded_traffic(w["name"])
-    l2_gbs = measure_l2_copy_gbs()
-    algo = roof["algorithmic_bytes_per_launch"]
-    # bytes the kernel stages per launch: whole rows for the Eq. 1 kernels,
-    # one 128-byte line of list values plus the list for the NN-list kernel
-    dense = 4.0 * m * (n - 1) * n if not args.nn else 256.0 * m * (n - 1)
-    roof_l2 = {"bound": "l2", "peak": l2_gbs, "unit": "GB/s",
-               "peak_kind": "L2 copy bandwidth measured in this run (64 graph-replayed torch copies, 2 x 24 MiB)",
-               "achieved_algorithmic": algo / (con_ms / 1e3) / 1e9,
-               "frac_algorithmic": algo / (con_ms / 1e3) / 1e9 / l2_gbs,
-               "achieved_dense_rows": dense / (con_ms / 1e3) / 1e9,
-               "frac_dense_rows": dense / (con_ms / 1e3) / 1e9 / l2_gbs}
+        rec = recorded_traffic(w["name"], m)
+        if rec:
+            roof["traffic"] = rec["dram_bytes_per_launch"]
+            roof["l2_bytes_per_launch"] = rec.get("l2_bytes_per_launch")
+            roof["lts_throughput_pct"] = rec.get("lts_throughput_pct")
+            roof["traffic_source"] = rec["source"]
     line = {
         "metric": METRIC, "value": value, "unit": "ant-steps/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
@@ -458,15 +503,17 @@ def run_ours(args, w, rank, world, local):
         "phase_ms": {"construct": con_ms, "best": best_ms, "pheromone": upd_ms},
         "best_len": best_len,
         "roofline": roof,
-        "roofline_l2": roof_l2,
         "gpu_launches": launches * steps,
         "clocks": clk,
         "e2e": e2e,
     }
+    if batched is not None:
+        line["batched"] = {k: batched[k] for k in (
+            "value", "unit", "ms_per_step", "per_instance_loop_solves_per_s", "speedup_vs_loop",
+            "identical_best_lengths", "ant_steps_per_s", "gpu_launches", "clocks")}
+        line["batched"]["config"] = batched["config"]
     if not args.no_cpu_baseline:
-        v, s, desc = oracle_sample(w, max(1, int(10.0 / max(_oracle_ant_seconds(w), 1e-6))))
-        line["cpu_baseline"] = {"value": v, "unit": "ant-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": desc}
+        line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
 
 
@@ -485,13 +532,16 @@ def construct_sources_sha256() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes (read + write) per construct launch from a committed ncu capture.
+def recorded_traffic(workload: str, m: int):
+    """Memory traffic per construct launch from a committed ncu capture.
 
     The summaries under profiles/ carry a line
-    `traffic-record: workload=<name> dram_bytes_per_launch=<B> sources_sha256=<H>`;
-    the figure is used only if H equals the hash of the current sources (else
-    the counters describe another kernel and traffic is null)."""
+    `traffic-record: workload=<name> ants=<a> dram_bytes_per_launch=<B>
+    l2_bytes_per_launch=<L> lts_throughput_pct=<P> sources_sha256=<H>`.
+    It is used only if H equals the hash of the current sources (else the
+    counters describe another kernel and traffic stays null).  A capture of
+    the same kernel with fewer ants (a small case) is scaled to m ants: every
+    ant reads its own rows, so the bytes grow in proportion to the ants."""
     import glob
     sha = construct_sources_sha256()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "construct_kernel_*.md"))):
@@ -500,29 +550,49 @@ def recorded_traffic(workload: str):
                 if not line.startswith("traffic-record:"):
                     continue
                 kv = dict(x.split("=", 1) for x in line.split()[1:])
-                if kv.get("workload") == workload and kv.get("sources_sha256") == sha:
-                    return float(kv["dram_bytes_per_launch"]), os.path.relpath(path, ROOT)
-    return None, None
+                if kv.get("workload") != workload or kv.get("sources_sha256") != sha:
+                    continue
+                ants = int(kv.get("ants", m))
+                scale = m / ants
+                rec = {"source": os.path.relpath(path, ROOT), "captured_ants": ants,
+                       "dram_bytes_per_launch": float(kv["dram_bytes_per_launch"]) * scale}
+                if "l2_bytes_per_launch" in kv:
+                    rec["l2_bytes_per_launch"] = float(kv["l2_bytes_per_launch"]) * scale
+                if "lts_throughput_pct" in kv:
+                    rec["lts_throughput_pct"] = float(kv["lts_throughput_pct"])
+                return rec
+    return None
 
 
-def construct_roofline(n, m, con_ms, peaks, peak_kind, kernel="construct_kernel", nn=0):
+def construct_roofline(n, m, con_ms, l2, peaks, peak_kind, kernel="construct_kernel", nn=0):
     """Roofline entry for the construction kernel (the dominant kernel).
 
     Algorithmic bytes per launch: every ant reads, at each of its n-1 steps,
     the 4-byte choice_info entries of the cities it has not visited yet:
     4 * m * sum_{s=1}^{n-1} (n - s) = 4 m n (n-1) / 2.  With nearest-neighbour
     lists a step needs the current city's nn list entries and their
-    list-ordered choice_info values: 8 * nn bytes, m (n-1) steps."""
+    list-ordered choice_info values: 8 * nn bytes, m (n-1) steps.  The matrix
+    stays in L2, so the ceiling is the read-only L2 bandwidth measured in this
+    run; the HBM copy peak is given beside it for reference."""
     if nn:
         algo = 8.0 * nn * m * (n - 1)
+        dense = 256.0 * m * (n - 1)  # one 128-byte line of values plus the list row
     else:
         algo = 4.0 * m * n * (n - 1) / 2.0
+        dense = 4.0 * m * (n - 1) * ((n + 3) // 4 * 4)  # whole padded rows, as staged
     achieved = algo / (con_ms / 1e3) / 1e9
-    peak = float(peaks["hbm_gbs"])
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    peak = float(l2["peak"])
+    hbm = float(peaks["hbm_gbs"])
+    return {"bound": "l2", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None,
-            "peak_kind": f"{peak_kind} HBM copy bandwidth",
+            "peak_kind": "read-only L2 bandwidth measured in this run (" + l2["how"] + ")",
+            "l2_read_gbs": {"float4": l2["float4"], "bulk": l2["bulk"]},
             "kernel": kernel, "algorithmic_bytes_per_launch": algo,
+            "staged_bytes_per_launch": dense,
+            "achieved_staged": dense / (con_ms / 1e3) / 1e9,
+            "frac_staged": dense / (con_ms / 1e3) / 1e9 / peak,
+            "hbm": {"peak": hbm, "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                    "frac": achieved / hbm},
             "avg_launch_ms": con_ms}
 
 
@@ -554,6 +624,13 @@ def e2e_solve(aco, w, rank, m, configure):
 def run_batched(args, rank, world, local):
     """256 independent instances x 100 iterations: one pool (graph per step) vs the
     plain per-instance loop over the same kernels."""
+    line = batched_measure(args, rank, world, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def batched_measure(args, rank, world, local):
+    """The batched line's fields (rank 0; None on the other ranks)."""
     import numpy as np
     import torch
     from paper_1101_2678_gb300 import aco, instances
@@ -629,7 +706,7 @@ def run_batched(args, rank, world, local):
         "ant_steps_per_s": ant_steps / t_batch,
         "gpu_launches": launches * iters, "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batched_rule(args, rank, world, local):

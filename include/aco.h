@@ -632,6 +632,29 @@ int aco_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, i
  */
 int aco_race_exponential(const uint32_t *x, float *out, int32_t count);
 
+/*
+ * aco_stream_read - read-bandwidth probe for the construction kernel's
+ * roofline (measurement infrastructure; no counterpart in the paper).  The
+ * construction of Section III-A reads the rows of choice_info, which stay in
+ * L2 at the benchmark sizes, so its ceiling is the rate at which the SMs read
+ * an L2-resident buffer.  One launch on `stream` (a cudaStream_t as an
+ * integer; 0 = the legacy default stream) reads the caller's device buffer
+ * `buf` (16-byte aligned, `bytes` long) `reps` times:
+ *   mode 0: 16-byte loads that bypass L1, 256 threads per CTA;
+ *   mode 1: 16 KB bulk copies (cp.async.bulk) into shared memory, one warp
+ *           per CTA with four stages, as the construction kernel stages rows.
+ * The grid is blocks_per_sm (1..32) CTAs per SM.  The call returns after the
+ * launch; the caller times it with CUDA events on `stream`.  `sink` (device,
+ * one float) keeps the loads live and is written only in a case that does not
+ * occur in practice; `status` (device, one uint32) receives bit 1 if a bulk
+ * copy's bounded wait gave up (the CTA then waits, again bounded, for its
+ * copies in flight and ends).  The caller owns every buffer.
+ * ACO_EINVAL: NULL pointers, misalignment, bytes not a positive multiple of
+ * 16 (mode 0) or 16384 (mode 1), reps outside [1, 2^20], an unknown mode.
+ */
+int aco_stream_read(const void *buf, uint64_t bytes, int32_t reps, int32_t mode,
+                    int32_t blocks_per_sm, uint64_t stream, float *sink, uint32_t *status);
+
 #ifdef __cplusplus
 }
 #endif

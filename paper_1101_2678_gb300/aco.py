@@ -80,6 +80,8 @@ SIGNATURES = [
     ("aco_restore_state", C.c_int, [_vp, _vp, C.c_uint64]),
     ("aco_philox4x32_10", C.c_int, [_vp, _vp, _vp, C.c_int32]),
     ("aco_race_exponential", C.c_int, [_vp, _vp, C.c_int32]),
+    ("aco_stream_read", C.c_int, [_vp, C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                                  _vp, _vp]),
     ("aco_set_option", C.c_int, [_vp, C.c_int32, C.c_int64]),
     ("aco_get_option", C.c_int, [_vp, C.c_int32, _i64p]),
     ("aco_get_kernel_times", C.c_int, [_vp, _vp]),
@@ -256,6 +258,14 @@ def aco_race_exponential(x) -> np.ndarray:
     out = np.empty(xs.shape, np.float32)
     _check(load().aco_race_exponential(_ptr(xs), _ptr(out), xs.size), "aco_race_exponential")
     return out
+
+
+def aco_stream_read(buf_ptr: int, nbytes: int, reps: int, mode: int, blocks_per_sm: int,
+                    stream: int, sink_ptr: int, status_ptr: int) -> None:
+    """Launch the read-bandwidth probe on device memory (raw device pointers;
+    the caller times the launch on `stream`)."""
+    _check(load().aco_stream_read(C.c_void_p(buf_ptr), nbytes, reps, mode, blocks_per_sm, stream,
+                                  C.c_void_p(sink_ptr), C.c_void_p(status_ptr)), "aco_stream_read")
 
 
 def aco_save_state(h) -> bytes:

@@ -651,6 +651,10 @@ static int pool_switch_rule(aco_pool* p, int32_t slot, Apply apply) {
   if (e == cudaSuccess)
     e = I.variant == kVariantAcs ? launch_acs_init(I, p->sms, p->side)
                                  : launch_mmas_init(I, p->sms, p->side);
+  // A slot that already has nearest-neighbour lists builds its first tours
+  // from the list-ordered copy of choice_info: refresh it from the new rule's
+  // start trails (the Ant Colony System reads the dense row instead).
+  if (e == cudaSuccess && I.nn > 0 && I.variant != kVariantAcs) e = launch_nn_choice(I, p->side);
   if (e == cudaSuccess) e = cudaEventRecord(sl.ready, p->side);
   if (e != cudaSuccess) return cuda_fail(e, "pool rule switch");
   sl.wait_ready = true;

@@ -56,3 +56,30 @@ def test_tour_check_option_passes_on_valid_runs(aco, orc):
             aco.aco_set_option(c.h, aco.ACO_OPT_CHECK, 1)
             aco.aco_iterate(c.h, 3)
             aco.aco_synchronize(c.h)
+
+
+def test_read_probe_runs_both_modes_and_rejects_bad_arguments(aco):
+    # The roofline's read-bandwidth probe: both modes complete with a clear
+    # status word (the bulk-copy mode's waits are bounded like the
+    # construction kernel's), and invalid arguments are refused on the host.
+    import torch
+    nbytes = 4 << 20
+    buf = torch.rand(nbytes // 4, device="cuda")
+    sink = torch.zeros(4, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    for mode in (0, 1):
+        for bps in (1, 3):
+            aco.aco_stream_read(buf.data_ptr(), nbytes, 3, mode, bps, s.cuda_stream,
+                                sink.data_ptr(), status.data_ptr())
+    s.synchronize()
+    assert int(status.item()) == 0
+    lib = aco.load()
+    assert lib.aco_stream_read(buf.data_ptr() + 4, 64, 1, 0, 1, 0, sink.data_ptr(),
+                               status.data_ptr()) == aco.ACO_EINVAL  # misaligned
+    assert lib.aco_stream_read(buf.data_ptr(), 1000, 1, 1, 1, 0, sink.data_ptr(),
+                               status.data_ptr()) == aco.ACO_EINVAL  # not whole 16 KB chunks
+    assert lib.aco_stream_read(buf.data_ptr(), 64, 1, 2, 1, 0, sink.data_ptr(),
+                               status.data_ptr()) == aco.ACO_EINVAL  # unknown mode
+    assert lib.aco_stream_read(buf.data_ptr(), 64, 0, 0, 1, 0, sink.data_ptr(),
+                               status.data_ptr()) == aco.ACO_EINVAL  # no passes

@@ -429,10 +429,11 @@ def test_nn_list_slot_errors(aco):
         aco.aco_pool_destroy(p)
 
 
-def test_colonies_with_lists_in_a_pool(aco, orc):
+@pytest.mark.parametrize("multirate", [False, True])
+def test_colonies_with_lists_in_a_pool(aco, orc, multirate):
     # colonies with and without lists in one pool (two colony launches per
-    # step), lists set before or after the switch: each equals the oracle's
-    # R16 / R14 run
+    # step), lists set before or after the switch, with and without
+    # multi-rate stepping: each equals the oracle's R16 / R14 run
     cases = [(60, 10, 8, 5, 51, True), (97, 16, 20, 4, 52, False), (130, 10, 0, 4, 53, True),
              (40, 8, 12, 6, 54, False)]
     insts = {n: I.clustered_instance(n, seed=n + 11, clusters=5, sigma=150, side=3000)
@@ -440,6 +441,7 @@ def test_colonies_with_lists_in_a_pool(aco, orc):
     need = sum(aco.aco_pool_bytes_needed(n, m) for n, m, *_r in cases)
     p = aco.aco_pool_create(8, need + (1 << 20))
     try:
+        aco.aco_pool_set_multirate(p, multirate)
         slots = {}
         for n, m, nn, iters, seed, lists_first in cases:
             s = aco.aco_pool_admit(p, insts[n].dist, 1.0, 2.0, 0.1, m, seed, iters)
@@ -450,7 +452,8 @@ def test_colonies_with_lists_in_a_pool(aco, orc):
                 aco.aco_pool_set_nn(p, s, nn)
             slots[n] = s
         aco.aco_pool_step(p)
-        assert aco.aco_pool_stats(p)["launches_last_step"] == 4
+        if not multirate:
+            assert aco.aco_pool_stats(p)["launches_last_step"] == 4
         while aco.aco_pool_step(p) > 0:
             pass
         aco.aco_pool_synchronize(p)
@@ -459,5 +462,31 @@ def test_colonies_with_lists_in_a_pool(aco, orc):
             assert np.array_equal(aco.aco_pool_pheromone(p, slots[n], n), ref["tau32"]), n
             tour, length = aco.aco_pool_result(p, slots[n], n)
             assert length == ref["best_len"] and np.array_equal(tour, ref["best_tour"]), n
+    finally:
+        aco.aco_pool_destroy(p)
+
+
+@pytest.mark.parametrize("lists_first", [True, False])
+def test_max_min_list_slot_either_order_matches_oracle(aco, orc, lists_first):
+    # Lists set before or after the MAX-MIN switch: the slot's first tours
+    # come from the list-ordered choice_info of the tau_max trails, so the
+    # run equals the oracle's MAX-MIN run with lists (readings R13 + R9).
+    n, m, nn, iters, seed = 150, 40, 16, 5, 61
+    x = I.clustered_instance(n, seed=67, clusters=6, side=4000)
+    p = aco.aco_pool_create(2, aco.aco_pool_bytes_needed(n, m) + (1 << 20))
+    try:
+        s = aco.aco_pool_admit(p, x.dist, 1.0, 2.0, 0.02, m, seed, iters)
+        if lists_first:
+            aco.aco_pool_set_nn(p, s, nn)
+        aco.aco_pool_set_mmas(p, s, 0.05, False)
+        if not lists_first:
+            aco.aco_pool_set_nn(p, s, nn)
+        while aco.aco_pool_step(p) > 0:
+            pass
+        aco.aco_pool_synchronize(p)
+        ref = orc.run_mmas(x.dist, m, iters, seed, rho=0.02, p_best=0.05, rule=2, nn=nn)
+        assert np.array_equal(aco.aco_pool_pheromone(p, s, n), ref["tau32"])
+        tour, length = aco.aco_pool_result(p, s, n)
+        assert length == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
     finally:
         aco.aco_pool_destroy(p)
