@@ -517,9 +517,10 @@ def run_ours(args, w, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
-CONSTRUCT_SOURCES = ("aco_device.cuh", "construct.cuh", "construct_g1h8.cu", "construct_g1h16.cu",
-                     "construct_g1h32.cu", "construct_g2h32.cu", "construct_g4h32.cu",
-                     "construct_rule.cuh", "construct_rule1.cu", "construct_rule2.cu")
+CONSTRUCT_SOURCES = ("aco_device.cuh", "construct.cuh", "construct_chunks.h", "construct_dispatch.cuh",
+                     "construct_g1h8.cu", "construct_g1h16.cu", "construct_g1h32.cu",
+                     "construct_g2h32.cu", "construct_g4h32.cu", "construct_rule.cuh",
+                     "construct_rule1.cu", "construct_rule2.cu")
 
 
 def construct_sources_sha256() -> str:

@@ -8,6 +8,7 @@
 
 #include "../../include/aco.h"
 #include "aco_device.cuh"
+#include "construct_chunks.h"
 #include "kernels.h"
 #include "runtime.h"
 #include "checkpoint.h"
@@ -39,24 +40,19 @@ int cuda_fail(cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 // Construction tilings
 // ---------------------------------------------------------------------------
-// Cities per thread: multiples of 4 with C/4 odd (conflict-free chunk reads
-// from the staged row).
-static const int kC1[] = {4, 12, 20, 28, 36, 44, 52, 60, 68, 76};
-static const int kC2[] = {12, 20, 28, 36, 44, 52, 60, 68};
-static const int kC4[] = {4, 12, 20, 28, 36};
-
+// Cities per thread: the widths each tiling's launch table compiles.
 static const int* c_set(int G, int H, int* cnt) {
   if (G == 1 && (H == 8 || H == 16 || H == 32)) {
-    *cnt = 10;
-    return kC1;
+    *cnt = chunk_count(ChunksOneWarp{});
+    return chunk_values(ChunksOneWarp{});
   }
   if (H == 32 && G == 2) {
-    *cnt = 8;
-    return kC2;
+    *cnt = chunk_count(ChunksTwoWarps{});
+    return chunk_values(ChunksTwoWarps{});
   }
   if (H == 32 && G == 4) {
-    *cnt = 5;
-    return kC4;
+    *cnt = chunk_count(ChunksFourWarps{});
+    return chunk_values(ChunksFourWarps{});
   }
   *cnt = 0;
   return nullptr;
