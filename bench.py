@@ -847,16 +847,17 @@ def run_served(args, rank, world, local):
     # per-request loop) against the server on the same sample, all admitted at once
     sample = reqs[:args.serve_loop_sample]
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    loop_lens = []
+    loop_lens, loop_times = [], []
     for r in sample:
+        t1 = time.perf_counter()
         h = aco.aco_create_coords(r.coords, r.alpha, r.beta, r.rho, r.m, r.seed)
         if r.nn:
             aco.aco_set_option(h, aco.ACO_OPT_NN_LIST, r.nn)
         aco.aco_iterate(h, r.iterations)
         loop_lens.append(aco.aco_best_tour(h, r.n)[1])
         aco.aco_destroy(h)
-    t_loop = time.perf_counter() - t0
+        loop_times.append(time.perf_counter() - t1)
+    t_loop = sum(loop_times)
     loop = None
     if sample:
         with serve.Server(budget_bytes=64 << 30, max_slots=4096, max_step_work=1 << 62,
@@ -868,6 +869,12 @@ def run_served(args, rank, world, local):
             "server_solves_per_s": st3["solves_per_s"],
             "speedup_vs_loop": st3["solves_per_s"] * t_loop / len(sample),
             "identical_best_lengths": same,
+            "loop_seconds_per_request": [round(x, 4) for x in loop_times],
+            "request_n": [r.n for r in sample],
+            # A request in the mix runs no faster than alone, so the server's
+            # makespan on the sample is at least the longest request's time:
+            # its speedup over the loop cannot exceed sum / max.
+            "makespan_bound_speedup": t_loop / max(loop_times),
             "what": "the first requests of the stream solved one at a time (aco_create_coords "
                     "+ aco_iterate(200) + aco_best_tour) vs the server with all of them "
                     "admitted at once"}
@@ -882,6 +889,9 @@ def run_served(args, rank, world, local):
                    "window_s": args.serve_seconds, "budget_gb": 64, "iterations": 200,
                    "multirate": mr, "max_step_work": work, "nn_list": args.serve_nn},
         "configured_stream": st,
+        # throughput against the loop on the stream's own request mix (the
+        # loop's rate from the timed sample)
+        "saturated_vs_loop": (st["solves_per_s"] / (len(sample) / t_loop)) if sample else None,
         "sustainable_stream": dict(st2, rate_per_s=rate),
         "loop_comparison": loop,
     }

@@ -464,15 +464,22 @@ int aco_pool_step(aco_pool_handle p, int32_t *live_after);
 int aco_pool_finished(aco_pool_handle p, int32_t *slots, int32_t capacity, int32_t *count);
 
 /*
- * aco_pool_result - best-so-far tour (n+1 int32) and length of a slot (live
- * or finished; synchronises the pool).  Either output may be NULL.
+ * aco_pool_result - best-so-far tour (n+1 int32) and length of a slot, live
+ * or finished.  For a finished slot it waits only for the step that ran the
+ * slot's last iterations and reads on a stream of its own, so steps launched
+ * since keep running; for a live slot it synchronises the pool.  Either
+ * output may be NULL.
  */
 int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t *tour, int64_t *len);
 
 /* aco_pool_pheromone - copy a slot's tau (n*n float) to the host. */
 int aco_pool_pheromone(aco_pool_handle p, int32_t slot, float *tau);
 
-/* aco_pool_release - return a finished (or live) slot and its memory. */
+/*
+ * aco_pool_release - return a finished (or live) slot and its memory.  A
+ * finished slot waits only for its last step (no later step reads it); a
+ * live slot first waits for all work in flight.
+ */
 int aco_pool_release(aco_pool_handle p, int32_t slot);
 
 /*

@@ -19,9 +19,11 @@
 //      -> Q;
 //   4. T = floor(r Q / 2^64) with r from Philox (one Philox call per lane per
 //      H steps, broadcast by shuffle);
-//   5. the thread whose prefix range holds T is found by ballot; its chunk is
-//      rescanned by all lanes of its warp segment (P = ceil(C/H) cities
-//      each), a second scan and ballot give the city.
+//   5. the thread whose prefix range holds T is found by ballot; it finds
+//      the part of its chunk (up to four parts of whole 4-city groups, from
+//      per-part sums kept in step 3) that holds the target, which is
+//      rescanned by all lanes of its warp segment (about one city each); a
+//      second scan and ballot give the city.
 // Every operation is an exact max or an exact integer sum, so the chosen city
 // is the same for every (C, G, H) tiling and equals the CPU oracle's choice.
 // Every warp-level intrinsic names only the segment's lanes, so segments of
@@ -125,6 +127,76 @@ __device__ __forceinline__ unsigned long long chunk_sum(const uint32_t (&v)[C], 
   const uint32_t off = (uint32_t)C * kTwo23Bits;
   const uint32_t hi = hi0 + hi1 - off, lo = lo0 + lo1 - off;
   return ((unsigned long long)hi << 23) + lo;
+}
+
+// A lane's chunk split into K parts of whole 4-city groups: part k holds the
+// groups [k*NG/K, (k+1)*NG/K), NG = C/4.  After the warp has found the lane
+// whose range holds the target, that lane finds the part from these sums,
+// and only the part's cities are searched city by city.
+template <int C, int K>
+struct ChunkParts {
+  static constexpr int NG = C / 4;
+  static_assert(K >= 1 && K <= NG, "1 <= K <= C/4 parts");
+  __host__ __device__ static constexpr int first_group(int k) { return k * NG / K; }
+  __host__ __device__ static constexpr int cities(int k) {
+    return 4 * (first_group(k + 1) - first_group(k));
+  }
+  static constexpr int max_cities() { return 4 * ((NG + K - 1) / K); }
+};
+
+// Per-part sums of q over the thread's C weights (already scaled by f2),
+// as hi/lo bit-pattern sums with their offsets still in (removed by
+// part_value).  Parts accumulate independently; a single part uses two
+// chains so that the adds still overlap.
+template <int C, int K>
+__device__ __forceinline__ void chunk_sum_parts(const uint32_t (&v)[C], float f1, float f1s,
+                                                uint32_t (&phi)[K], uint32_t (&plo)[K]) {
+  using Pt = ChunkParts<C, K>;
+  uint32_t hi2 = 0, lo2 = 0;  // second chain of a single part
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    phi[k] = 0;
+    plo[k] = 0;
+  }
+#pragma unroll
+  for (int g = 0; g < C / 4; ++g) {
+    int k = 0;
+#pragma unroll
+    for (int j = 1; j < K; ++j)
+      if (g >= Pt::first_group(j)) k = j;
+    const QuantParts a = quant_parts(v[4 * g], f1, f1s), b = quant_parts(v[4 * g + 1], f1, f1s);
+    const QuantParts c = quant_parts(v[4 * g + 2], f1, f1s),
+                     d = quant_parts(v[4 * g + 3], f1, f1s);
+    if (K == 1 && (g & 1)) {
+      hi2 += a.hi_bits + b.hi_bits;
+      lo2 += a.lo_bits + b.lo_bits;
+      hi2 += c.hi_bits + d.hi_bits;
+      lo2 += c.lo_bits + d.lo_bits;
+    } else {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (j == k) {
+          phi[j] += a.hi_bits + b.hi_bits;
+          plo[j] += a.lo_bits + b.lo_bits;
+          phi[j] += c.hi_bits + d.hi_bits;
+          plo[j] += c.lo_bits + d.lo_bits;
+        }
+    }
+  }
+  if (K == 1) {
+    phi[0] += hi2;
+    plo[0] += lo2;
+  }
+}
+
+// The value of part k's sum: its bit-pattern sums minus the offsets of its
+// cities; the true sums are below C * 2^23 <= 2^30, so the modular sums are
+// exact.  k must be a compile-time constant (an unrolled loop index).
+template <int C, int K>
+__device__ __forceinline__ unsigned long long part_value(const uint32_t (&phi)[K],
+                                                         const uint32_t (&plo)[K], int k) {
+  const uint32_t off = (uint32_t)ChunkParts<C, K>::cities(k) * kTwo23Bits;
+  return ((unsigned long long)(phi[k] - off) << 23) + (plo[k] - off);
 }
 
 // Same sum, also keeping each group of four weights' hi/lo part sums (with
@@ -246,7 +318,9 @@ __device__ __forceinline__ float race_exponential(uint32_t x) {
 // E_j, the smallest key wins (ties to the lower index; zero weights and
 // overflowing keys are +inf, so with every weight 0 the lowest unvisited
 // city wins).
-template <int C, int G, int H, int R = 0>
+// kPool: the ant belongs to a many-instance launch, where the GPU is full and
+// issue-bound (fewer instructions per step pay even at a longer chain).
+template <int C, int G, int H, int R = 0, bool kPool = false>
 __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, const int tg,
                                               const Seg<H> seg, GroupSmem* gs, const int bar_id,
                                               float* srow, const bool lane_copy) {
@@ -257,12 +331,22 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   static_assert(H == 8 || H == 16 || H == 32, "H must be 8, 16 or 32");
   static_assert(H == 32 || G == 1, "segments smaller than a warp serve one ant each");
   constexpr int NW = (C + 31) / 32;  // tabu words per thread
-  constexpr int P = (C + H - 1) / H;  // cities per lane in the rescan
   // The smallest chunk (4 cities) keeps its sums in registers and the
   // selected lane finds the city alone; larger chunks are rescanned by the
   // whole segment, which measured faster than a serial in-lane search.
   constexpr bool kGroupPick = C <= 4;
   constexpr int NG = kGroupPick ? C / 4 : 1;
+  // Larger chunks keep per-part sums (K parts of whole 4-city groups) so the
+  // rescan covers one part: at most about one city per lane.  This cuts the
+  // instructions of a step but lengthens its dependent chain (the selected
+  // lane picks the part first), so a single instance, whose ants may not
+  // fill the GPU, splits only chunks of more than two cities per lane in the
+  // rescan (measured: 2.8 % faster at C = 76, 2.4 % slower at C = 36).
+  constexpr int KW = (C + H - 1) / H;  // cities per lane in an unsplit rescan
+  constexpr int KP = (kGroupPick || (!kPool && KW <= 2)) ? 1 : (KW < 4 ? KW : 4);
+  using Parts = ChunkParts<C, (KP < C / 4 ? KP : C / 4)>;
+  constexpr int K = KP < C / 4 ? KP : C / 4;
+  constexpr int PP = (Parts::max_cities() + H - 1) / H;  // cities per lane in the rescan
   constexpr int NT = H == 32 ? 32 * G : H;  // threads per ant
   const int n = I.n, ld = I.ld;
   const int hl = seg.hl;          // lane within the segment
@@ -505,11 +589,21 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
         for (int i = 0; i < C; ++i) v[i] = __float_as_uint(__fmul_rn(__uint_as_float(v[i]), f2));
       }
       uint32_t ghi[NG], glo[NG];
+      uint32_t phi[K], plo[K];
       unsigned long long mine;
-      if constexpr (kGroupPick)
+      if constexpr (kGroupPick) {
         mine = chunk_sum_groups<C>(v, f1, f1s, ghi, glo);
-      else
-        mine = chunk_sum<C>(v, f1, f1s);
+      } else {
+        chunk_sum_parts<C, K>(v, f1, f1s, phi, plo);
+        uint32_t hs = phi[0], ls = plo[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) {
+          hs += phi[k];
+          ls += plo[k];
+        }
+        const uint32_t off = (uint32_t)C * kTwo23Bits;
+        mine = ((unsigned long long)(hs - off) << 23) + (ls - off);
+      }
       const unsigned long long incl = seg.inclusive_scan(mine);
       const unsigned long long wtot = seg.shfl(incl, H - 1);
       unsigned long long woff = 0, Q = wtot;
@@ -561,38 +655,65 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
           }
           next = baseL + seg.shfl(pick, L);
         } else {
+          // Lane L finds the part of its chunk that holds the target.
+          int part = 0;
+          unsigned long long t3 = t2;
+          if constexpr (K > 1) {
+            if (hl == L) {
+              unsigned long long cum = 0;
+              bool found = false;
+#pragma unroll
+              for (int k = 0; k < K; ++k) {
+                const unsigned long long pv = part_value<C, K>(phi, plo, k);
+                if (!found && (k == K - 1 || cum + pv > t2)) {
+                  found = true;
+                  part = k;
+                  t3 = t2 - cum;
+                }
+                cum += pv;
+              }
+            }
+            part = seg.shfl(part, L);
+            t3 = seg.shfl(t3, L);
+          }
+          // The segment rescans that part, PP cities per lane.
+          const int pstart = 4 * (part * Parts::NG / K);
+          const int psz = 4 * ((part + 1) * Parts::NG / K) - pstart;
           uint32_t visL[NW];
 #pragma unroll
           for (int w = 0; w < NW; ++w) visL[w] = seg.shfl(vis[w], L);
-          unsigned long long qv[P];
+          unsigned long long qv[PP];
           unsigned long long ps = 0;
 #pragma unroll
-          for (int p = 0; p < P; ++p) {
-            const int li = hl * P + p;
+          for (int p = 0; p < PP; ++p) {
+            const int pi = hl * PP + p;  // position within the part
+            const int li = pstart + pi;  // position within lane L's chunk
             uint32_t word = FULL;
 #pragma unroll
             for (int w = 0; w < NW; ++w)
               if (w == (li >> 5)) word = visL[w];
             uint32_t w8 = 0u;
-            if (li < C && baseL + li < ld && !((word >> (li & 31)) & 1u))
+            if (pi < psz && baseL + li < ld && !((word >> (li & 31)) & 1u))
               w8 = __float_as_uint(row[baseL + li]);
             qv[p] = quant_value(w8, f1, f1s, f2);
             ps += qv[p];
           }
           const unsigned long long incl2 = seg.inclusive_scan(ps);
-          const int L2 = max(__ffs(seg.ballot(incl2 > t2)) - 1, 0);
+          const int L2 = max(__ffs(seg.ballot(incl2 > t3)) - 1, 0);
           int pick = 0;
-          if (hl == L2) {
-            unsigned long long c = incl2 - ps;
-            pick = -1;
+          if constexpr (PP > 1) {
+            if (hl == L2) {
+              unsigned long long c = incl2 - ps;
+              pick = -1;
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-              c += qv[p];
-              if (pick < 0 && c > t2) pick = p;
+              for (int p = 0; p < PP; ++p) {
+                c += qv[p];
+                if (pick < 0 && c > t3) pick = p;
+              }
             }
+            pick = max(seg.shfl(pick, L2), 0);
           }
-          pick = max(seg.shfl(pick, L2), 0);
-          next = baseL + L2 * P + pick;
+          next = baseL + pstart + L2 * PP + pick;
         }
         if (G > 1 && hl == 0) gs->next = next;
       }
@@ -687,7 +808,8 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
   // A reference into the descriptor table (read-only, L1-cached) rather than
   // a register copy of the whole descriptor, which cost ~40 registers.
   const Instance& I = insts[it.x];
-  construct_ant<C, G, H>(I, it.y, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
+  construct_ant<C, G, H, 0, true>(I, it.y, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0],
+                                  1 + grp,
                          reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes),
                          lane_copy != 0);
 }

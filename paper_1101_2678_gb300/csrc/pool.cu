@@ -107,6 +107,7 @@ struct PoolSlot {
   bool restored = false; // state loaded from a checkpoint (rule fixed as well)
   int rate = 1;          // iterations per step (multi-rate stepping)
   bool nn_built = false; // nearest-neighbour lists built (aco_pool_set_nn)
+  long long finish_step = -1;  // the step that ran the slot's last iterations
 };
 
 struct aco_pool {
@@ -164,6 +165,15 @@ struct aco_pool {
   cudaStream_t class_stream[kClassStreams] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kClassStreams] = {};
+  // Completion of recent steps (ring; entry k % kStepEvents is recorded
+  // after step k's graph), so a finished slot's result is read as soon as
+  // its last step is done, on the io stream, while later steps run.  An
+  // entry re-recorded by a later step only makes the wait longer, never
+  // wrong: the steps run in order on one stream.
+  static constexpr int kStepEvents = 8;
+  cudaEvent_t step_ev[kStepEvents] = {};
+  long long steps_launched = 0;
+  cudaStream_t io = nullptr;
 };
 
 static void pool_drop_graph(aco_pool* p) {
@@ -628,11 +638,12 @@ static int pool_admit_common(aco_pool* p, int32_t n, const int32_t* dist, const 
   return ACO_OK;
 }
 
-static int pool_check_status(aco_pool* p, int slot) {
+static int pool_check_status(aco_pool* p, int slot, cudaStream_t st = nullptr) {
+  if (!st) st = p->stream;
   int status = 0;
   cudaError_t e = cudaMemcpyAsync(&status, &p->slots[(size_t)slot].I.st->status, sizeof(int),
-                                  cudaMemcpyDeviceToHost, p->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "pool synchronize");
   if (status & kStatusTimeout) return fail(ACO_ETIMEOUT, "a device-side wait gave up");
   if (status) return fail(ACO_ECUDA, "device status 0x%x in slot %d", status, slot);
@@ -702,6 +713,9 @@ int aco_pool_create(int32_t max_slots, uint64_t budget_bytes, aco_pool_handle* o
     if ((e = cudaMalloc(&p->d_acs, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaMalloc(&p->d_cls_slots, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess) break;
+    if ((e = cudaStreamCreateWithFlags(&p->io, cudaStreamNonBlocking)) != cudaSuccess) break;
+    for (int i = 0; i < aco_pool::kStepEvents && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&p->step_ev[i], cudaEventDisableTiming);
     for (int i = 0; i < aco_pool::kClassStreams && e == cudaSuccess; ++i) {
       e = cudaStreamCreateWithFlags(&p->class_stream[i], cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming);
@@ -739,6 +753,12 @@ int aco_pool_destroy(aco_pool_handle p) {
     if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
   }
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  for (int i = 0; i < aco_pool::kStepEvents; ++i)
+    if (p->step_ev[i]) cudaEventDestroy(p->step_ev[i]);
+  if (p->io) {
+    cudaStreamSynchronize(p->io);
+    cudaStreamDestroy(p->io);
+  }
   if (p->stream) cudaStreamDestroy(p->stream);
   if (p->side) cudaStreamDestroy(p->side);
   delete p;
@@ -813,6 +833,9 @@ int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
       }
     }
     if ((e = cudaGraphLaunch(p->exec, p->stream)) != cudaSuccess) return cuda_fail(e, "pool launch");
+    const long long step = p->steps_launched++;
+    if ((e = cudaEventRecord(p->step_ev[step % aco_pool::kStepEvents], p->stream)) != cudaSuccess)
+      return cuda_fail(e, "pool step event");
     for (int s : p->h_live) {
       PoolSlot& sl = p->slots[(size_t)s];
       sl.started = true;
@@ -821,6 +844,7 @@ int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
         if (sl.iters_left == 0) {
           sl.live = false;
           sl.finished = true;
+          sl.finish_step = step;
           p->finished_order.push_back(s);
           p->dirty = true;
         } else if (sl.iters_left < sl.rate) {
@@ -852,6 +876,19 @@ int aco_pool_result(aco_pool_handle p, int32_t slot, int32_t* tour, int64_t* len
   if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].used)
     return fail(ACO_EINVAL, "slot %d is not in use", slot);
   const PoolSlot& sl = p->slots[(size_t)slot];
+  if (sl.finished && sl.finish_step >= 0) {
+    // Its last step is known: wait for that step only and read on the io
+    // stream, without waiting for the steps launched since.
+    cudaError_t e = cudaStreamWaitEvent(
+        p->io, p->step_ev[sl.finish_step % aco_pool::kStepEvents], 0);
+    if (e == cudaSuccess && tour)
+      e = cudaMemcpyAsync(tour, sl.I.best_tour, ((size_t)sl.n + 1) * 4, cudaMemcpyDeviceToHost,
+                          p->io);
+    if (e == cudaSuccess && len)
+      e = cudaMemcpyAsync(len, &sl.I.st->best_len, 8, cudaMemcpyDeviceToHost, p->io);
+    if (e != cudaSuccess) return cuda_fail(e, "pool result");
+    return pool_check_status(p, slot, p->io);
+  }
   cudaError_t e = cudaStreamSynchronize(p->side);
   if (e == cudaSuccess && tour)
     e = cudaMemcpyAsync(tour, sl.I.best_tour, ((size_t)sl.n + 1) * 4, cudaMemcpyDeviceToHost,
@@ -1099,10 +1136,20 @@ int aco_pool_release(aco_pool_handle p, int32_t slot) {
   if (slot < 0 || slot >= p->max_slots || !p->slots[(size_t)slot].used)
     return fail(ACO_EINVAL, "slot %d is not in use", slot);
   // Work that still reads the slot must finish before its memory is reused.
-  cudaError_t e = cudaStreamSynchronize(p->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->side);
-  if (e != cudaSuccess) return cuda_fail(e, "pool release");
+  // A finished slot is read by no step after its last one (its class lists
+  // are rebuilt without it), so waiting for that step is enough; other slots
+  // wait for everything in flight.
   PoolSlot& sl = p->slots[(size_t)slot];
+  cudaError_t e;
+  if (sl.finished && sl.finish_step >= 0) {
+    e = cudaEventSynchronize(p->step_ev[sl.finish_step % aco_pool::kStepEvents]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);
+  } else {
+    e = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->side);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->io);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "pool release");
   if (sl.live) p->dirty = true;
   pool_free(p, sl.off, sl.bytes);
   cudaEvent_t ev = sl.ready;

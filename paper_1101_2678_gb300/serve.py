@@ -10,7 +10,11 @@ request finishes after its own number of iterations; its latency is
 completion time minus arrival time (queueing included).
 
 All compute happens in the library's kernels (aco_pool_step); this module only
-decides which request enters which slot and when.
+decides which request enters which slot and when.  The host keeps one step
+ahead of the device: a step is launched before the results of the previous
+step's finished requests are read (each read waits only for the step that
+ran the request's last iterations), and admissions and the next step's
+graph are prepared while the device runs.
 """
 from __future__ import annotations
 
@@ -128,6 +132,20 @@ class Server:
         depth_max = 0
         bytes_max = 0
         t0 = time.perf_counter()
+        seen = set()   # finished slots already noted
+        pending = []   # slots whose last step is in flight: read after the next launch
+
+        def drain(slots):
+            nonlocal live_work
+            for slot in slots:
+                ri, tadm = live.pop(slot)
+                live_work -= step_work(requests[ri])
+                tour, length = aco.aco_pool_result(pool, slot, requests[ri].n)
+                tfin = time.perf_counter() - t0
+                outcomes.append(Outcome(ri, float(arrivals[ri]), tadm, tfin, length, tour))
+                aco.aco_pool_release(pool, slot)
+                seen.discard(slot)
+
         while len(outcomes) < total:
             now = time.perf_counter() - t0
             if deadline is not None and now >= deadline:
@@ -154,28 +172,31 @@ class Server:
                     aco.aco_pool_set_nn(pool, slot, r.nn)
                 live[slot] = (queue.popleft(), time.perf_counter() - t0)
                 live_work += w
-            if not live:
-                if nxt < total:
+            running = len(live) - len(pending)
+            if running == 0:
+                # nothing left to step: collect what the last step finished
+                drain(pending)
+                pending = []
+                if not live and nxt < total:
                     time.sleep(max(0.0, min(0.01, arrivals[order[nxt]] - now)))
                 continue
-            max_live = max(max_live, len(live))
+            max_live = max(max_live, running)
             queued_now = len(queue)  # arrived and waiting for admission
             in_use = aco.aco_pool_stats(pool)["bytes_in_use"]
             depth_sum += queued_now
             depth_max = max(depth_max, queued_now)
             bytes_max = max(bytes_max, in_use)
             if now >= next_sample:
-                timeline.append([round(now, 3), queued_now, len(live), round(in_use / 2 ** 30, 3)])
+                timeline.append([round(now, 3), queued_now, running, round(in_use / 2 ** 30, 3)])
                 next_sample = now + 1.0
             aco.aco_pool_step(pool)
             steps += 1
-            for slot in aco.aco_pool_finished(pool):
-                ri, tadm = live.pop(slot)
-                live_work -= step_work(requests[ri])
-                tour, length = aco.aco_pool_result(pool, slot, requests[ri].n)
-                tfin = time.perf_counter() - t0
-                outcomes.append(Outcome(ri, float(arrivals[ri]), tadm, tfin, length, tour))
-                aco.aco_pool_release(pool, slot)
+            # the requests that finished in the step before this one: their
+            # last step is done or about to be, while this one runs on
+            drain(pending)
+            pending = [s for s in aco.aco_pool_finished(pool) if s not in seen]
+            seen.update(pending)
+        drain([s for s in pending if s in live])
         aco.aco_pool_synchronize(pool)
         elapsed = time.perf_counter() - t0
         lat = np.array([o.latency for o in outcomes]) if outcomes else np.zeros(1)

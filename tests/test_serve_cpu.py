@@ -71,10 +71,12 @@ class FakeAco:
     def aco_pool_step(self, p):
         p.log.append(("step", sorted(sl["n"] for s, sl in p.slots.items()
                                      if s not in p.finished)))
+        p.nsteps = getattr(p, "nsteps", 0) + 1
         for s in list(p.slots):
             p.slots[s]["left"] -= 1
             if p.slots[s]["left"] == 0:
                 p.finished.append(s)
+                p.slots[s]["finish_step"] = p.nsteps
         return sum(1 for s in p.slots if s not in p.finished)
 
     def aco_pool_finished(self, p):
@@ -82,6 +84,7 @@ class FakeAco:
 
     def aco_pool_result(self, p, slot, n):
         sl = p.slots[slot]
+        p.log.append(("result", sl["finish_step"], p.nsteps))
         return np.arange(n + 1, dtype=np.int32) % n, 1000 * sl["n"] + sl["seed"]
 
     def aco_pool_release(self, p, slot):
@@ -178,3 +181,21 @@ def test_live_cap(fake):
     steps = [e[1] for e in fake.pools[0].log if e[0] == "step"]
     assert st["completed"] == 7 and st["max_live"] == 3
     assert max(len(s) for s in steps) == 3
+
+
+def test_results_are_read_while_the_next_step_runs(fake):
+    # A request's result is read after the following step has been launched
+    # (the host stays a step ahead of the device), unless nothing else was
+    # left to run; every request is still read exactly once.
+    reqs = [req(40 + 10 * i, 2 + i, seed=i) for i in range(5)]
+    with serve.Server(budget_bytes=1 << 30, max_slots=8, max_step_work=10**12) as srv:
+        outs, st = srv.run(reqs, np.zeros(5), realtime=False)
+    pool = fake.pools[0]
+    reads = [e for e in pool.log if e[0] == "result"]
+    assert st["completed"] == 5 and len(reads) == 5
+    last = max(r[1] for r in reads)
+    for _, fin, launched in reads:
+        if fin < last:
+            assert launched == fin + 1   # read once the next step was in flight
+        else:
+            assert launched == fin       # the final step: nothing left to overlap
