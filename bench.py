@@ -483,8 +483,11 @@ def run_ours(args, w, rank, world, local):
         if rec:
             roof["traffic"] = rec["dram_bytes_per_launch"]
             roof["l2_bytes_per_launch"] = rec.get("l2_bytes_per_launch")
-            roof["lts_throughput_pct"] = rec.get("lts_throughput_pct")
             roof["traffic_source"] = rec["source"]
+            roof["ncu_capture"] = {"ants": rec["captured_ants"],
+                                   "lts_throughput_pct": rec.get("lts_throughput_pct"),
+                                   "note": "bytes scaled to m ants; the percentage is the "
+                                           "captured launch's own"}
     line = {
         "metric": METRIC, "value": value, "unit": "ant-steps/s", "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
