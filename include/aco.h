@@ -585,8 +585,12 @@ int aco_batch_destroy(aco_batch b);
  * and choice_info, on device arrays, without allocating.
  *   n, m    cities (3..ACO_NOALLOC_MAX_N) and ants (1..ACO_NOALLOC_MAX_M);
  *           larger sizes are rejected with ACO_EINVAL.
- *   tours   device, m rows of n+1 int32 cities (closed tours); entries
- *           outside [0, n) are ignored.
+ *   tours   device, m rows of n+1 int32 cities: closed tours that visit
+ *           every city once (tour[n] == tour[0]), as the construction
+ *           builds them.  Entries outside [0, n) are ignored.  The deposit
+ *           is summed in 64-bit fixed point scaled so that m ants' deposits
+ *           on one edge fit; a row that repeats an edge adds it again and
+ *           can overflow that sum without an error being reported.
  *   lens    device, m int64 tour lengths C^k (>= 1).
  *   heta    device, n*n float eta^beta, row-major.
  *   tau     device, n*n float, updated in place.

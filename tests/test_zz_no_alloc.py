@@ -16,13 +16,17 @@ from paper_1101_2678_gb300 import instances as I
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_update_matches_regular_update_twice():
+# A size in the middle of the range, and the largest the static scratch holds
+# (the whole n x n accumulator, and the per-ant deposits and the scale slot at
+# the end of the array).
+@pytest.mark.parametrize("n,m", [(300, 257), (1024, 4096)])
+def test_noalloc_update_matches_regular_update_twice(n, m):
     torch = pytest.importorskip("torch")
     from paper_1101_2678_gb300 import build
     build.build()
     from paper_1101_2678_gb300 import aco
     aco.load()
-    n, m = 300, 257
+    assert n <= aco.ACO_NOALLOC_MAX_N and m <= aco.ACO_NOALLOC_MAX_M
     inst = I.uniform_instance(n, 1000, seed=77)
     dev = torch.device("cuda", torch.cuda.current_device())
     with aco.Colony(inst.dist, m, seed=5) as c:
