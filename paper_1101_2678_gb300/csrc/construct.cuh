@@ -268,12 +268,27 @@ struct Seg {
   __device__ __forceinline__ void sync() const { __syncwarp(mask); }
 };
 
+// Cities per lane before and after the compactions of the Eq. 1 walk (see
+// construct_phased.cuh): C, then 4*ceil(C/8), then 4*ceil(C/16).  One warp
+// (or segment) per ant with C >= kCompactMinC compacts; other tilings never
+// do.
+constexpr int kCompactMinC = 20;
+template <int C, int G>
+struct Compaction {
+  static constexpr bool kOn = G == 1 && C >= kCompactMinC;
+  static constexpr int kC1 = 4 * ((C + 7) / 8);
+  static constexpr int kC2 = 4 * ((C + 15) / 16);
+};
+
 // Shared memory of one ant group: the staged row (H*G*C floats, 16-byte
-// aligned) followed by its mbarrier.
+// aligned), its mbarrier, and (when the walk compacts) the list of unvisited
+// cities, up to H * 4*ceil(C/8) 16-bit entries.
 template <int C, int G, int H>
 struct StageLayout {
   static constexpr int kRowFloats = H * G * C;
-  static constexpr int kBytes = ((kRowFloats * 4 + 8) + 15) / 16 * 16;
+  static constexpr int kListOffset = kRowFloats * 4 + 16;
+  static constexpr int kListEntries = Compaction<C, G>::kOn ? H * Compaction<C, G>::kC1 : 0;
+  static constexpr int kBytes = ((kListOffset + 2 * kListEntries) + 15) / 16 * 16;
 };
 
 // Ant groups per CTA of `warps` warps.
@@ -762,6 +777,12 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
   if (tg == 0) I.lens[ant] = len;
 }
 
+}  // namespace aco
+
+#include "construct_phased.cuh"
+
+namespace aco {
+
 // Placement of one thread: its ant group within the CTA and its index tg
 // within the group.
 template <int G, int H>
@@ -786,9 +807,9 @@ __global__ void __launch_bounds__(256) construct_kernel(Instance I) {
   group_of_thread<G, H>(grp, tg);
   const int ant = blockIdx.x * groups_per_cta<G, H>(blockDim.x >> 5) + grp;
   if (ant >= I.m) return;
+  float* srow = reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes);
   construct_ant<C, G, H, R>(I, ant, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
-                            reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes),
-                            I.stage != 0);
+                            srow, I.stage != 0);
 }
 
 // Batched form: group g of block b builds ant items[b*A + g].y of instance
@@ -808,10 +829,47 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
   // A reference into the descriptor table (read-only, L1-cached) rather than
   // a register copy of the whole descriptor, which cost ~40 registers.
   const Instance& I = insts[it.x];
+  float* srow = reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes);
   construct_ant<C, G, H, 0, true>(I, it.y, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0],
-                                  1 + grp,
-                         reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes),
-                         lane_copy != 0);
+                                  1 + grp, srow, lane_copy != 0);
+}
+
+// The Eq. 1 walk with compaction (construct_phased.cuh), one group of H lanes
+// per ant.  Its three phases are inlined into one body; without a ceiling the
+// register allocator adds their needs up instead of sharing them, so the
+// ceiling is the larger of what the phases need on their own (measured with
+// ptxas: phase 0 at C = 76 needs 128, the gathering phases at C = 28 about
+// 80).
+template <int C>
+struct PhasedRegs {
+  static constexpr int v = C <= 20 ? 64 : (C <= 36 ? 80 : 128);
+};
+
+template <int C, int H>
+__global__ void __maxnreg__((PhasedRegs<C>::v)) construct_phased_kernel(Instance I) {
+  extern __shared__ __align__(16) unsigned char stage[];
+  int grp, tg;
+  group_of_thread<1, H>(grp, tg);
+  const int ant = blockIdx.x * groups_per_cta<1, H>(blockDim.x >> 5) + grp;
+  if (ant >= I.m) return;
+  construct_ant_phased<C, H, false>(
+      I, ant, Seg<H>(threadIdx.x & 31),
+      reinterpret_cast<float*>(stage + grp * StageLayout<C, 1, H>::kBytes), I.stage != 0);
+}
+
+template <int C, int H>
+__global__ void __maxnreg__((PhasedRegs<C>::v))
+    construct_phased_items_kernel(const Instance* __restrict__ insts,
+                                  const int2* __restrict__ items, int count, int lane_copy) {
+  extern __shared__ __align__(16) unsigned char stage[];
+  int grp, tg;
+  group_of_thread<1, H>(grp, tg);
+  const int idx = blockIdx.x * groups_per_cta<1, H>(blockDim.x >> 5) + grp;
+  if (idx >= count) return;
+  const int2 it = items[idx];
+  construct_ant_phased<C, H, true>(
+      insts[it.x], it.y, Seg<H>(threadIdx.x & 31),
+      reinterpret_cast<float*>(stage + grp * StageLayout<C, 1, H>::kBytes), lane_copy != 0);
 }
 
 // Dynamic shared memory for a CTA of `warps` warps, with the opt-in above
@@ -822,8 +880,15 @@ inline size_t construct_smem_setup(int warps) {
   static std::atomic<unsigned long long> done{0};
   once_per_device(done, [] {
     const int most = groups_per_cta<G, H>(8) * StageLayout<C, G, H>::kBytes;
-    if constexpr (kItems)
+    constexpr bool kPhased = R == 0 && Compaction<C, G>::kOn;
+    if constexpr (kItems && kPhased)
+      return cudaFuncSetAttribute(construct_phased_items_kernel<C, H>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    else if constexpr (kItems)
       return cudaFuncSetAttribute(construct_items_kernel<C, G, H>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    else if constexpr (kPhased)
+      return cudaFuncSetAttribute(construct_phased_kernel<C, H>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     else
       return cudaFuncSetAttribute(construct_kernel<C, G, H, R>,

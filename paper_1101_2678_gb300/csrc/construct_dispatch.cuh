@@ -16,7 +16,10 @@ template <int C, int G, int H, int R>
 inline bool launch_one(int c, const Instance& I, int grid, int warps, cudaStream_t st) {
   if (c != C) return false;
   const size_t smem = construct_smem_setup<C, G, H, false, R>(warps);
-  construct_kernel<C, G, H, R><<<grid, 32 * warps, smem, st>>>(I);
+  if constexpr (R == 0 && Compaction<C, G>::kOn)
+    construct_phased_kernel<C, H><<<grid, 32 * warps, smem, st>>>(I);
+  else
+    construct_kernel<C, G, H, R><<<grid, 32 * warps, smem, st>>>(I);
   return true;
 }
 
@@ -25,7 +28,12 @@ inline bool launch_items_one(int c, const Instance* insts, const int2* items, in
                              int warps, int lane_copy, cudaStream_t st) {
   if (c != C) return false;
   const size_t smem = construct_smem_setup<C, G, H, true>(warps);
-  construct_items_kernel<C, G, H><<<grid, 32 * warps, smem, st>>>(insts, items, count, lane_copy);
+  if constexpr (Compaction<C, G>::kOn)
+    construct_phased_items_kernel<C, H><<<grid, 32 * warps, smem, st>>>(insts, items, count,
+                                                                        lane_copy);
+  else
+    construct_items_kernel<C, G, H><<<grid, 32 * warps, smem, st>>>(insts, items, count,
+                                                                    lane_copy);
   return true;
 }
 

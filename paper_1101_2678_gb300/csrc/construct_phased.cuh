@@ -1,0 +1,370 @@
+// Tour construction by Eq. 1 (Section II; the integer roulette of reading R2)
+// for one warp or warp segment per ant, with the unvisited cities compacted
+// twice along the walk.
+//
+// A step of the plain kernel (construct_ant) handles every city of the row,
+// visited or not: lane t owns the cities [tC, tC + C), zeroes the visited
+// ones and still pays the max, the quantisation and the sum for them.  Half
+// way through a tour half of that work is spent on visited cities.  Here the
+// walk runs in three phases:
+//   phase 0  (at most 32*C1 unvisited cities not yet reached): as the plain
+//            kernel, lane t owns the contiguous chunk [tC, tC + C) of the row;
+//   phase 1  the unvisited cities, in ascending order, are listed in shared
+//            memory and dealt out C1 = 4*ceil(C/8) per lane (lane t takes
+//            entries [t*C1, t*C1 + C1)); each step reads their weights from
+//            the staged row by index;
+//   phase 2  the same with C2 = 4*ceil(C/16) per lane.
+// Phase p starts at the first step at which the unvisited cities fit in the
+// segment's H*Cp slots.  Every phase keeps the cities of the segment in
+// ascending order, lane after lane and slot after slot, so the integer
+// roulette (first city whose inclusive prefix sum exceeds T) chooses the same
+// city as the plain kernel and the CPU oracle.  The row is still staged
+// whole (bulk copy), so the L2 bytes do not change; the per-candidate work
+// of the later steps halves and quarters.
+#pragma once
+
+namespace aco {
+
+struct WalkState {
+  int cur;       // current city
+  int s;         // next step (1 .. n-1)
+  int live;      // unvisited cities listed for the current phase (gather phases)
+  unsigned long long rwin;  // this lane's Philox words for the steps of the window
+  uint32_t parity;          // mbarrier phase of the row copy
+  bool waits_ok;
+};
+
+// Steps [w.s, s_end) of one phase.  CP: slots per lane.  kGather = false:
+// slot i of lane t is city t*C + i (phase 0); true: slot i holds the city
+// listed at ulist[t*CP + i].  CPN > 0: afterwards, list the unvisited cities
+// for a phase of CPN slots per lane.
+template <int C, int CP, int CPN, int H, bool kGather, bool kPool>
+__device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, const Seg<H> seg,
+                                          float* srow, uint16_t* ulist, const int start,
+                                          const int s_end, WalkState& w, const bool lane_copy) {
+  static_assert(CP % 4 == 0 && CP >= 4 && CP <= 128, "CP must be a multiple of 4 in [4,128]");
+  static_assert(kGather || CP == C, "the direct phase reads whole chunks");
+  constexpr int NW = (CP + 31) / 32;  // tabu words per lane
+  constexpr int KW = (CP + H - 1) / H;
+  constexpr int KP = (!kPool && KW <= 2) ? 1 : (KW < 4 ? KW : 4);
+  constexpr int K = KP < CP / 4 ? KP : CP / 4;
+  using Parts = ChunkParts<CP, K>;
+  constexpr int PP = (Parts::max_cities() + H - 1) / H;  // cities per lane in the rescan
+  constexpr int kListCap = StageLayout<C, 1, H>::kListEntries;
+  const int n = I.n, ld = I.ld;
+  const int hl = seg.hl;
+  const int base = hl * C;  // phase 0: the lane's chunk in the row
+  const uint32_t iter = (uint32_t)I.st->iteration;
+  const unsigned long long seed = I.seed;
+  const uint32_t srow_a = smem_u32(srow);
+  const uint32_t bar = srow_a + (uint32_t)StageLayout<C, 1, H>::kRowFloats * 4u;
+  const uint32_t row_bytes = (uint32_t)ld * 4u;
+  int32_t* tour = I.tours + (size_t)ant * I.ldt;
+
+  // Tabu bits (1 = visited, or no city in the slot) and, when gathering, the
+  // city of each slot.
+  uint32_t vis[NW];
+  uint32_t city[kGather ? CP : 1];
+  if constexpr (!kGather) {
+#pragma unroll
+    for (int wd = 0; wd < NW; ++wd) {
+      const int real = n - (base + 32 * wd);  // local cities of word wd below n
+      uint32_t word = real <= 0 ? FULL : (real >= 32 ? 0u : (FULL << real));
+      const int inchunk = C - 32 * wd;
+      if (inchunk < 32) word |= FULL << inchunk;
+      vis[wd] = word;
+    }
+    const int li = start - base;
+    if (li >= 0 && li < C) {
+#pragma unroll
+      for (int wd = 0; wd < NW; ++wd)
+        if (wd == (li >> 5)) vis[wd] |= 1u << (li & 31);
+    }
+  } else {
+#pragma unroll
+    for (int wd = 0; wd < NW; ++wd) vis[wd] = (wd == NW - 1 && CP % 32) ? (FULL << (CP % 32)) : 0u;
+#pragma unroll
+    for (int i = 0; i < CP; ++i) {
+      const int k = hl * CP + i;
+      const bool ok = k < w.live;
+      city[i] = ok ? (uint32_t)ulist[k] : 0u;
+      if (!ok) vis[i >> 5] |= 1u << (i & 31);
+    }
+  }
+
+  for (; w.s < s_end; ++w.s) {
+    const int s = w.s;
+    const int cur = w.cur;
+    // Everyone is done with the previous row (the segment agreed on `cur`).
+    if (lane_copy) {
+      const float4* src = reinterpret_cast<const float4*>(I.choice + (size_t)cur * ld);
+      float4* dst = reinterpret_cast<float4*>(srow);
+      for (int i = hl; i < (ld >> 2); i += H) dst[i] = src[i];
+    } else if (hl == 0) {
+      fence_proxy_async_smem();
+      bulk_load(srow_a, I.choice + (size_t)cur * ld, row_bytes, bar);
+    }
+    const int off = (s - 1) % H;
+    if (off == 0) {
+      const Philox4 x = step_draw(seed, (uint32_t)(s + hl), (uint32_t)ant, iter);
+      w.rwin = ((unsigned long long)x.x1 << 32) | x.x0;
+    }
+    const unsigned long long r = seg.shfl(w.rwin, off);
+    if (lane_copy) {
+      seg.sync();
+    } else {
+      if (w.waits_ok && !mbar_wait_bounded(bar, w.parity)) {
+        w.waits_ok = false;  // stale data from here on; the status word says so
+        if (hl == 0) atomicOr(&I.st->status, kStatusTimeout);
+      }
+      w.parity ^= 1u;
+    }
+    const float* row = srow;
+
+    uint32_t v[CP];  // weight bits of the slots; w >= 0 orders like its bit pattern
+    if constexpr (!kGather) {
+#pragma unroll
+      for (int i = 0; i < CP; i += 4) {
+        const uint4 t = *reinterpret_cast<const uint4*>(row + base + i);
+        v[i] = t.x;
+        v[i + 1] = t.y;
+        v[i + 2] = t.z;
+        v[i + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < CP; ++i) v[i] = __float_as_uint(row[city[i]]);
+    }
+    uint32_t m4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < CP; ++i) {
+      if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+      m4[i & 3] = max(m4[i & 3], v[i]);
+    }
+    const uint32_t mx = seg.max_u32(max(max(m4[0], m4[1]), max(m4[2], m4[3])));
+
+    int next;
+    int chosen_lane = -1, chosen_slot = 0;  // gather phases: the slot to mark
+    if (mx == 0u) {
+      // Every unvisited weight is zero: the lowest unvisited city.
+      uint32_t cand = 0xffffffffu;
+      if constexpr (!kGather) {
+#pragma unroll
+        for (int wd = NW - 1; wd >= 0; --wd) {
+          const uint32_t fr = ~vis[wd];
+          if (fr) cand = (uint32_t)(base + 32 * wd + __ffs(fr) - 1);
+        }
+      } else {
+#pragma unroll
+        for (int i = CP - 1; i >= 0; --i)
+          if (!((vis[i >> 5] >> (i & 31)) & 1u)) cand = city[i];
+      }
+      cand = seg.min_u32(cand);
+      next = (int)cand;
+      if constexpr (kGather) {
+        // the owner of that city marks its slot below
+        int mine = -1;
+#pragma unroll
+        for (int i = CP - 1; i >= 0; --i)
+          if (!((vis[i >> 5] >> (i & 31)) & 1u) && city[i] == cand) mine = i;
+        const uint32_t own = seg.ballot(mine >= 0);
+        chosen_lane = own ? __ffs(own) - 1 : -1;
+        chosen_slot = chosen_lane >= 0 ? seg.shfl(mine, chosen_lane) : 0;
+      }
+    } else {
+      const int sc = kRouletteBits - 1 - exponent_of_bits(mx);
+      float f1, f1s, f2;
+      quant_factors(sc, f1, f1s, f2);
+      if (f2 != 1.0f) {
+#pragma unroll
+        for (int i = 0; i < CP; ++i) v[i] = __float_as_uint(__fmul_rn(__uint_as_float(v[i]), f2));
+      }
+      uint32_t phi[K], plo[K];
+      chunk_sum_parts<CP, K>(v, f1, f1s, phi, plo);
+      uint32_t hs = phi[0], ls = plo[0];
+#pragma unroll
+      for (int k = 1; k < K; ++k) {
+        hs += phi[k];
+        ls += plo[k];
+      }
+      const uint32_t offb = (uint32_t)CP * kTwo23Bits;
+      const unsigned long long mine = ((unsigned long long)(hs - offb) << 23) + (ls - offb);
+      const unsigned long long incl = seg.inclusive_scan(mine);
+      const unsigned long long Q = seg.shfl(incl, H - 1);
+      const unsigned long long T = __umul64hi(r, Q);
+      const int L = max(__ffs(seg.ballot(incl > T)) - 1, 0);
+      const unsigned long long t2 = T - seg.shfl(incl - mine, L);
+      // Lane L finds the part of its slots that holds the target.
+      int part = 0;
+      unsigned long long t3 = t2;
+      if constexpr (K > 1) {
+        if (hl == L) {
+          unsigned long long cum = 0;
+          bool found = false;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const unsigned long long pv = part_value<CP, K>(phi, plo, k);
+            if (!found && (k == K - 1 || cum + pv > t2)) {
+              found = true;
+              part = k;
+              t3 = t2 - cum;
+            }
+            cum += pv;
+          }
+        }
+        part = seg.shfl(part, L);
+        t3 = seg.shfl(t3, L);
+      }
+      // The segment rescans that part, PP slots per lane.
+      const int pstart = 4 * (part * Parts::NG / K);
+      const int psz = 4 * ((part + 1) * Parts::NG / K) - pstart;
+      uint32_t visL[NW];
+#pragma unroll
+      for (int wd = 0; wd < NW; ++wd) visL[wd] = seg.shfl(vis[wd], L);
+      unsigned long long qv[PP];
+      int cc[PP];
+      unsigned long long ps = 0;
+#pragma unroll
+      for (int p = 0; p < PP; ++p) {
+        const int pi = hl * PP + p;  // position within the part
+        const int li = pstart + pi;  // slot within lane L's slots
+        uint32_t word = FULL;
+#pragma unroll
+        for (int wd = 0; wd < NW; ++wd)
+          if (wd == (li >> 5)) word = visL[wd];
+        uint32_t w8 = 0u;
+        int c = 0;
+        const bool open = pi < psz && !((word >> (li & 31)) & 1u);
+        if constexpr (!kGather) {
+          c = L * C + li;
+          if (open && c < ld) w8 = __float_as_uint(row[c]);
+        } else {
+          if (open) {
+            c = (int)ulist[L * CP + li];
+            w8 = __float_as_uint(row[c]);
+          }
+        }
+        cc[p] = c;
+        qv[p] = quant_value(w8, f1, f1s, f2);
+        ps += qv[p];
+      }
+      const unsigned long long incl2 = seg.inclusive_scan(ps);
+      const int L2 = max(__ffs(seg.ballot(incl2 > t3)) - 1, 0);
+      int pick = 0;
+      if constexpr (PP > 1) {
+        if (hl == L2) {
+          unsigned long long c = incl2 - ps;
+          pick = -1;
+#pragma unroll
+          for (int p = 0; p < PP; ++p) {
+            c += qv[p];
+            if (pick < 0 && c > t3) pick = p;
+          }
+        }
+        pick = max(seg.shfl(pick, L2), 0);
+      }
+      int pc = cc[0];
+#pragma unroll
+      for (int p = 1; p < PP; ++p)
+        if (p == pick) pc = cc[p];
+      next = seg.shfl(pc, L2);
+      chosen_lane = L;
+      chosen_slot = pstart + L2 * PP + pick;
+    }
+
+    // A city outside [0, n) can only come from a defect; record it and stay
+    // in bounds instead of reading past the matrix.
+    if ((unsigned)next >= (unsigned)n) {
+      if (hl == 0) atomicOr(&I.st->status, kStatusBadTour);
+      next = start;
+      chosen_lane = -1;
+    }
+    if constexpr (!kGather) {
+      const int li = next - base;
+      if (li >= 0 && li < C) {
+#pragma unroll
+        for (int wd = 0; wd < NW; ++wd)
+          if (wd == (li >> 5)) vis[wd] |= 1u << (li & 31);
+      }
+    } else {
+      if (hl == chosen_lane) {
+#pragma unroll
+        for (int wd = 0; wd < NW; ++wd)
+          if (wd == (chosen_slot >> 5)) vis[wd] |= 1u << (chosen_slot & 31);
+      }
+    }
+    if (hl == 0) tour[s] = next;
+    w.cur = next;
+    seg.sync();
+  }
+
+  if constexpr (CPN > 0) {
+    // List the unvisited cities for the next phase, ascending: lane after
+    // lane, each lane's slots in order.
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int wd = 0; wd < NW; ++wd) cnt += __popc(~vis[wd]);
+    const unsigned long long incl = seg.inclusive_scan((unsigned long long)cnt);
+    const int total = (int)seg.shfl(incl, H - 1);
+    int k = (int)(incl - cnt);
+    seg.sync();  // the list of this phase is no longer read
+#pragma unroll
+    for (int i = 0; i < CP; ++i) {
+      if (!((vis[i >> 5] >> (i & 31)) & 1u)) {
+        // a defect can leave more entries than the list holds: keep in bounds
+        if (k < kListCap) ulist[k] = (uint16_t)(kGather ? city[i] : (uint32_t)(base + i));
+        ++k;
+      }
+    }
+    w.live = total < H * CPN ? total : H * CPN;
+    seg.sync();
+  }
+}
+
+// The whole walk of one ant (G = 1) and its length and neighbour buckets.
+template <int C, int H, bool kPool>
+__device__ __forceinline__ void construct_ant_phased(const Instance& I, const int ant,
+                                                     const Seg<H> seg, float* srow,
+                                                     const bool lane_copy) {
+  using Cm = Compaction<C, 1>;
+  static_assert(Cm::kOn, "compaction needs one group per ant and C >= kCompactMinC");
+  uint16_t* ulist =
+      reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(srow) + StageLayout<C, 1, H>::kListOffset);
+  const int n = I.n;
+  const int hl = seg.hl;
+  const uint32_t iter = (uint32_t)I.st->iteration;
+  const Philox4 x0 = step_draw(I.seed, 0u, (uint32_t)ant, iter);
+  const int start = (int)__umulhi(x0.x0, (uint32_t)n);
+  int32_t* tour = I.tours + (size_t)ant * I.ldt;
+  if (hl == 0) tour[0] = start;
+  const uint32_t bar = smem_u32(srow) + (uint32_t)StageLayout<C, 1, H>::kRowFloats * 4u;
+  if (hl == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  seg.sync();
+
+  WalkState w{start, 1, 0, 0ull, 0u, true};
+  const int s1 = max(1, n - H * Cm::kC1);
+  const int s2 = max(s1, n - H * Cm::kC2);
+  eq1_phase<C, C, Cm::kC1, H, false, kPool>(I, ant, seg, srow, ulist, start, s1, w, lane_copy);
+  eq1_phase<C, Cm::kC1, Cm::kC2, H, true, kPool>(I, ant, seg, srow, ulist, start, s2, w,
+                                                  lane_copy);
+  eq1_phase<C, Cm::kC2, 0, H, true, kPool>(I, ant, seg, srow, ulist, start, n, w, lane_copy);
+  if (hl == 0) tour[n] = start;
+  seg.sync();
+
+  // C^k (Section II) and the per-city neighbour buckets.
+  long long len = 0;
+  for (int s = hl; s < n; s += H) {
+    const int a = tour[s], b = tour[s + 1];
+    const int p = tour[s == 0 ? n - 1 : s - 1];
+    len += I.dist[(size_t)a * I.ld + b];
+    I.nbr[(size_t)a * I.ldm + ant] = ((uint32_t)p << 16) | (uint32_t)b;
+  }
+#pragma unroll
+  for (int o = H / 2; o > 0; o >>= 1) len += seg.shfl_xor(len, o);
+  if (hl == 0) I.lens[ant] = len;
+}
+
+}  // namespace aco
