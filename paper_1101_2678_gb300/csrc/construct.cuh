@@ -836,13 +836,15 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
 
 // The Eq. 1 walk with compaction (construct_phased.cuh), one group of H lanes
 // per ant.  Its three phases are inlined into one body; without a ceiling the
-// register allocator adds their needs up instead of sharing them, so the
-// ceiling is the larger of what the phases need on their own (measured with
-// ptxas: phase 0 at C = 76 needs 128, the gathering phases at C = 28 about
-// 80).
+// register allocator adds their needs up instead of sharing them (233
+// registers at C = 76, where phase 0 alone needs 128).  The ceilings were
+// chosen by measurement on the GB300: 128 from C = 44 (no spills); 80 at
+// C = 36 (one instance of n = 1002: 1.159 ms, against 1.186 ms at 64 or 72);
+// 64 up to C = 28 (a pool of the batched workload: 22.38 ms per step, against
+// 22.91 ms at 80).
 template <int C>
 struct PhasedRegs {
-  static constexpr int v = C <= 20 ? 64 : (C <= 36 ? 80 : 128);
+  static constexpr int v = C <= 28 ? 64 : (C <= 36 ? 80 : 128);
 };
 
 template <int C, int H>
