@@ -93,6 +93,36 @@ def test_first_iteration_tours_match_oracle(aco, orc, n):
             aco.aco_set_option(c.h, aco.ACO_OPT_STAGING, 0)
 
 
+# The walk with compaction (one warp or segment per ant, C >= 20): the
+# largest size without it and the smallest with it for whole warps (n = 384,
+# C = 12; n = 385, C = 20), the widest size of two chunk widths (n = 640,
+# C = 20; n = 1152, C = 36), the widest chunk of whole warps (C = 76,
+# n = 2432) and of 16- and 8-lane segments, with both row stagings.  The
+# tours of the first iteration, and a second iteration on the updated
+# trails, equal the oracle's.
+@pytest.mark.parametrize("n,lanes", [(384, 32), (385, 32), (640, 32), (700, 16), (1152, 32),
+                                     (1216, 16), (600, 8), (2432, 32)])
+def test_compacting_walk_matches_oracle(aco, orc, n, lanes):
+    inst = I.clustered_instance(n, seed=n + lanes, clusters=16, sigma=400, side=20000)
+    m = 40
+    ref = orc.run(inst.dist, m, 2, 11)
+    with aco.Colony(inst.dist, m, seed=11) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_LANES_PER_ANT, lanes)
+        for stage in (0, 1):
+            aco.aco_set_option(c.h, aco.ACO_OPT_STAGING, stage)
+            tours, lens = aco.aco_construct_tours(c.h, n, m)
+            ch = oracle_initial_choice(orc, inst.dist, m)
+            otours, olens = orc.construct(ch, inst.dist, m, seed=11, iteration=0)
+            assert np.array_equal(tours, otours), stage
+            assert np.array_equal(lens, olens), stage
+        aco.aco_set_option(c.h, aco.ACO_OPT_STAGING, 0)
+        aco.aco_update_pheromone(c.h)
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+        aco.aco_update_pheromone(c.h)
+        assert np.array_equal(tours, ref["tours"]) and np.array_equal(lens, ref["lens"])
+        assert np.array_equal(aco.aco_get_pheromone(c.h, n), ref["tau32"])
+
+
 @pytest.mark.parametrize("wl,ants", [("n1002", 12), ("n2392", 6)])
 def test_full_size_first_iteration_sampled(aco, orc, wl, ants):
     w = getattr(I, "workload_" + wl)()
