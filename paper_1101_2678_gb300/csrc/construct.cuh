@@ -269,15 +269,16 @@ struct Seg {
 };
 
 // Cities per lane before and after the compactions of the Eq. 1 walk (see
-// construct_phased.cuh): C, then 4*ceil(C/8), then 4*ceil(C/16).  One warp
-// (or segment) per ant with C >= kCompactMinC compacts; other tilings never
-// do.
+// construct_phased.cuh): C, then 4*ceil(C/8), 4*ceil(C/16) and 4*ceil(C/32).
+// One warp (or segment) per ant with C >= kCompactMinC compacts; other
+// tilings never do.
 constexpr int kCompactMinC = 20;
 template <int C, int G>
 struct Compaction {
   static constexpr bool kOn = G == 1 && C >= kCompactMinC;
   static constexpr int kC1 = 4 * ((C + 7) / 8);
   static constexpr int kC2 = 4 * ((C + 15) / 16);
+  static constexpr int kC3 = 4 * ((C + 31) / 32);
 };
 
 // Shared memory of one ant group: the staged row (H*G*C floats, 16-byte

@@ -1,26 +1,27 @@
 // Tour construction by Eq. 1 (Section II; the integer roulette of reading R2)
 // for one warp or warp segment per ant, with the unvisited cities compacted
-// twice along the walk.
+// up to three times along the walk.
 //
 // A step of the plain kernel (construct_ant) handles every city of the row,
 // visited or not: lane t owns the cities [tC, tC + C), zeroes the visited
 // ones and still pays the max, the quantisation and the sum for them.  Half
 // way through a tour half of that work is spent on visited cities.  Here the
-// walk runs in three phases:
+// walk runs in up to four phases:
 //   phase 0  (at most 32*C1 unvisited cities not yet reached): as the plain
 //            kernel, lane t owns the contiguous chunk [tC, tC + C) of the row;
 //   phase 1  the unvisited cities, in ascending order, are listed in shared
 //            memory and dealt out C1 = 4*ceil(C/8) per lane (lane t takes
 //            entries [t*C1, t*C1 + C1)); each step reads their weights from
 //            the staged row by index;
-//   phase 2  the same with C2 = 4*ceil(C/16) per lane.
+//   phase 2  the same with C2 = 4*ceil(C/16) per lane;
+//   phase 3  the same with C3 = 4*ceil(C/32) per lane (when smaller than C2).
 // Phase p starts at the first step at which the unvisited cities fit in the
 // segment's H*Cp slots.  Every phase keeps the cities of the segment in
 // ascending order, lane after lane and slot after slot, so the integer
 // roulette (first city whose inclusive prefix sum exceeds T) chooses the same
 // city as the plain kernel and the CPU oracle.  The row is still staged
 // whole (bulk copy), so the L2 bytes do not change; the per-candidate work
-// of the later steps halves and quarters.
+// of the later steps halves, quarters and eighths.
 #pragma once
 
 namespace aco {
@@ -347,10 +348,17 @@ __device__ __forceinline__ void construct_ant_phased(const Instance& I, const in
   WalkState w{start, 1, 0, 0ull, 0u, true};
   const int s1 = max(1, n - H * Cm::kC1);
   const int s2 = max(s1, n - H * Cm::kC2);
+  const int s3 = max(s2, n - H * Cm::kC3);
   eq1_phase<C, C, Cm::kC1, H, false, kPool>(I, ant, seg, srow, ulist, start, s1, w, lane_copy);
   eq1_phase<C, Cm::kC1, Cm::kC2, H, true, kPool>(I, ant, seg, srow, ulist, start, s2, w,
                                                   lane_copy);
-  eq1_phase<C, Cm::kC2, 0, H, true, kPool>(I, ant, seg, srow, ulist, start, n, w, lane_copy);
+  if constexpr (Cm::kC3 < Cm::kC2) {
+    eq1_phase<C, Cm::kC2, Cm::kC3, H, true, kPool>(I, ant, seg, srow, ulist, start, s3, w,
+                                                    lane_copy);
+    eq1_phase<C, Cm::kC3, 0, H, true, kPool>(I, ant, seg, srow, ulist, start, n, w, lane_copy);
+  } else {
+    eq1_phase<C, Cm::kC2, 0, H, true, kPool>(I, ant, seg, srow, ulist, start, n, w, lane_copy);
+  }
   if (hl == 0) tour[n] = start;
   seg.sync();
 
