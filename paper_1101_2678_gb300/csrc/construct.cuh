@@ -400,6 +400,7 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     }
   }
   int32_t* tour = I.tours + (size_t)ant * I.ldt;
+  const float* const choice = I.choice;
   if (tg == 0) tour[0] = start;
   int cur = start;
   unsigned long long rwin = 0;
@@ -420,12 +421,12 @@ __device__ __forceinline__ void construct_ant(const Instance& I, const int ant, 
     if (lane_copy) {
       // The group copies the row with coalesced 16-byte loads (through L1,
       // so a row another group of this SM read recently may hit there).
-      const float4* src = reinterpret_cast<const float4*>(I.choice + (size_t)cur * ld);
+      const float4* src = reinterpret_cast<const float4*>(choice + (size_t)cur * ld);
       float4* dst = reinterpret_cast<float4*>(srow);
       for (int i = tg; i < (ld >> 2); i += NT) dst[i] = src[i];
     } else if (tg == 0) {
       fence_proxy_async_smem();
-      bulk_load(srow_a, I.choice + (size_t)cur * ld, row_bytes, bar);
+      bulk_load(srow_a, choice + (size_t)cur * ld, row_bytes, bar);
     }
     const int off = (s - 1) % H;
     if (off == 0) {

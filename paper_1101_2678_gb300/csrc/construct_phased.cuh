@@ -61,6 +61,7 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
   const uint32_t bar = srow_a + (uint32_t)StageLayout<C, 1, H>::kRowFloats * 4u;
   const uint32_t row_bytes = (uint32_t)ld * 4u;
   int32_t* tour = I.tours + (size_t)ant * I.ldt;
+  const float* const choice = I.choice;
 
   // Tabu bits (1 = visited, or no city in the slot) and, when gathering, the
   // city of each slot.
@@ -98,12 +99,12 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
     const int cur = w.cur;
     // Everyone is done with the previous row (the segment agreed on `cur`).
     if (lane_copy) {
-      const float4* src = reinterpret_cast<const float4*>(I.choice + (size_t)cur * ld);
+      const float4* src = reinterpret_cast<const float4*>(choice + (size_t)cur * ld);
       float4* dst = reinterpret_cast<float4*>(srow);
       for (int i = hl; i < (ld >> 2); i += H) dst[i] = src[i];
     } else if (hl == 0) {
       fence_proxy_async_smem();
-      bulk_load(srow_a, I.choice + (size_t)cur * ld, row_bytes, bar);
+      bulk_load(srow_a, choice + (size_t)cur * ld, row_bytes, bar);
     }
     const int off = (s - 1) % H;
     if (off == 0) {
