@@ -372,6 +372,25 @@ def test_full_size_pheromone_matches_oracle(aco, orc_all_cores, wl, checkpoints)
             assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
 
 
+@pytest.mark.parametrize("wl,iters", [("workload_n1002", 7), ("workload_n2392", 3)])
+def test_replayed_choice_info_gives_the_same_tours(aco, orc_all_cores, wl, iters):
+    # Replay mode: after some iterations the GPU's own choice_info, handed to
+    # the oracle with the same Philox counters (seed, iteration, ant, step),
+    # must yield every ant's tour and length bit for bit (Eq. 1 by reading R2).
+    orc = orc_all_cores
+    w = getattr(I, wl)()
+    d, m, seed = w["inst"].dist, w["m"], w["seed"]
+    n = d.shape[0]
+    with aco.Colony(d, m, seed=seed) as c:
+        aco.aco_iterate(c.h, iters)
+        assert aco.aco_get_iteration(c.h) == iters
+        ch = aco.aco_choice_info(c.h, n)
+        tours, lens = aco.aco_construct_tours(c.h, n, m)
+    otours, olens = orc.construct(ch, d, m, seed=seed, iteration=iters)
+    assert np.array_equal(tours, otours)
+    assert np.array_equal(lens, olens)
+
+
 def test_update_invariants_at_full_size(aco):
     # n = 1002 after two iterations: tau symmetric, valid tours, and one
     # update's deposit totals 2 n sum_k 1/C^k (Eqs. 3-4).
