@@ -473,6 +473,10 @@ def run_ours(args, w, rank, world, local):
         kernel = "acs_construct_kernel"
     elif args.nn:
         kernel = "construct_nn_kernel"
+    elif args.selection == "eq1" and tiling[0] == 1 and n > 12 * tiling[2]:
+        # one warp or segment per ant with at least 20 cities per lane: the
+        # walk with compaction
+        kernel = "construct_phased_kernel"
     else:
         kernel = "construct_kernel"
     l2 = measure_l2_read_gbs()
