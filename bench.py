@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-iterations", type=int, default=0,
                     help="0 = the workload's 100; fewer for profiling runs")
+    ap.add_argument("--single-launch", action="store_true",
+                    help="batched: every construction class in one persistent launch")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched: default tiling for every class (profiling runs)")
     ap.add_argument("--no-loop-baseline", action="store_true",
@@ -661,6 +663,8 @@ def batched_measure(args, rank, world, local):
     aco.aco_pool_synchronize(b)
     if args.no_autotune:
         aco.aco_pool_set_autotune(b, False)
+    if args.single_launch:
+        aco.aco_pool_set_single_launch(b, True)
     # choose each class's construction tiling before the timed run (the
     # choice does not change any result); reported in config
     t_tune = time.perf_counter()

@@ -458,6 +458,17 @@ int aco_pool_restore_slot(aco_pool_handle p, int32_t slot, const void *buf, uint
 int aco_pool_step(aco_pool_handle p, int32_t *live_after);
 
 /*
+ * aco_pool_set_single_launch - on = 1: each step builds the tours of every
+ * construction class in one persistent launch (warps take (instance, ant)
+ * items from a global ticket, widest chunks first, each with its class's
+ * chunk width) instead of one launch per class; only when every class uses
+ * whole warps with at most 36 cities per lane, one iteration per step and no
+ * lists, else the step keeps one launch per class.  Results are identical
+ * either way.  on = 0 (default): one launch per class.
+ */
+int aco_pool_set_single_launch(aco_pool_handle p, int32_t on);
+
+/*
  * aco_pool_finished - slots that are finished but not yet released, in
  * completion order; writes at most `capacity` of them and the total count.
  */

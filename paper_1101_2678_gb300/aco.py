@@ -104,6 +104,7 @@ SIGNATURES = [
     ("aco_pool_restore_slot", C.c_int, [_vp, C.c_int32, _vp, C.c_uint64]),
     ("aco_pool_set_nn", C.c_int, [_vp, C.c_int32, C.c_int32]),
     ("aco_pool_step", C.c_int, [_vp, _i32p]),
+    ("aco_pool_set_single_launch", C.c_int, [_vp, C.c_int32]),
     ("aco_pool_finished", C.c_int, [_vp, _vp, C.c_int32, _i32p]),
     ("aco_pool_result", C.c_int, [_vp, C.c_int32, _vp, _vp]),
     ("aco_pool_pheromone", C.c_int, [_vp, C.c_int32, _vp]),
@@ -436,6 +437,10 @@ def aco_pool_admit_coords(p, xy, alpha, beta, rho, m, seed, iterations):
         return None
     _check(rc, "aco_pool_admit_coords")
     return slot.value
+
+
+def aco_pool_set_single_launch(p, on: bool) -> None:
+    _check(load().aco_pool_set_single_launch(p, int(bool(on))), "aco_pool_set_single_launch")
 
 
 def aco_pool_step(p) -> int:

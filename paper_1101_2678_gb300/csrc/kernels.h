@@ -83,6 +83,17 @@ cudaError_t launch_construct_rule1(const Instance& I, ConstructTiling t, cudaStr
 cudaError_t launch_construct_rule2(const Instance& I, ConstructTiling t, cudaStream_t st);
 cudaError_t launch_construct_items(const Instance* insts, const int2* items, int count,
                                    ConstructTiling t, cudaStream_t st);
+// One persistent launch over the items of several classes (whole warps per
+// ant): class k holds items [begin[k], begin[k] + count[k]) of chunk width
+// C[k]; the classes are taken in the order listed.
+struct SingleClasses {
+  int begin[8], count[8], C[8], lane_copy[8];
+  int n;
+};
+bool single_launch_supports(int C);
+cudaError_t launch_construct_single(const Instance* insts, const int2* items,
+                                    const SingleClasses& cls, int total, int* ticket, int sms,
+                                    cudaStream_t st);
 
 // Nearest-neighbour lists: build list(i) (nn <= kNnStride), refresh their
 // choice_info values, and the list-restricted construction.

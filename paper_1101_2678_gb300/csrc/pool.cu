@@ -170,6 +170,8 @@ struct aco_pool {
   // its last step is done, on the io stream, while later steps run.  An
   // entry re-recorded by a later step only makes the wait longer, never
   // wrong: the steps run in order on one stream.
+  bool single_launch = false;  // all classes in one construction launch
+  int* d_ticket = nullptr;
   static constexpr int kStepEvents = 8;
   cudaEvent_t step_ev[kStepEvents] = {};
   long long steps_launched = 0;
@@ -480,7 +482,38 @@ static int pool_enqueue_step(aco_pool* p) {
       launches += 2;
     }
   }
-  for (int ci = 0; ci < ncls; ++ci) {
+  // One launch for every class: only for plain classes (whole warps, one
+  // iteration per step, no lists) of supported widths.
+  bool single = p->single_launch && !mr && ncls > 0 && ncls <= 8;
+  for (int ci = 0; single && ci < ncls; ++ci) {
+    const auto& c = p->classes[(size_t)ci];
+    single = !c.nn && std::get<0>(c.key) == 1 && std::get<1>(c.key) == 32 &&
+             single_launch_supports(std::get<2>(c.key));
+  }
+  if (single) {
+    SingleClasses sc{};
+    std::vector<int> order((size_t)ncls);
+    for (int ci = 0; ci < ncls; ++ci) order[(size_t)ci] = ci;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+      return std::get<2>(p->classes[(size_t)a].key) > std::get<2>(p->classes[(size_t)b].key);
+    });
+    int total = 0;
+    for (int j = 0; j < ncls; ++j) {
+      const auto& c = p->classes[(size_t)order[(size_t)j]];
+      sc.begin[j] = c.begin;
+      sc.count[j] = c.count;
+      sc.C[j] = std::get<2>(c.key);
+      sc.lane_copy[j] = c.t.S;
+      total += c.count;
+    }
+    sc.n = ncls;
+    cudaStream_t st = nstreams > 1 ? p->class_stream[first % nstreams] : p->stream;
+    if ((e = launch_construct_single(p->d_inst, p->d_items, sc, total, p->d_ticket, p->sms, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "pool construct (one launch)");
+    launches += 2;  // the ticket reset and the kernel
+  }
+  for (int ci = 0; ci < ncls && !single; ++ci) {
     const auto& c = p->classes[(size_t)ci];
     cudaStream_t st = nstreams > 1 ? p->class_stream[(ci + first) % nstreams] : p->stream;
     for (int r = 0; r < (mr ? c.k : 1); ++r) {
@@ -714,6 +747,7 @@ int aco_pool_create(int32_t max_slots, uint64_t budget_bytes, aco_pool_handle* o
     if ((e = cudaMalloc(&p->d_cls_slots, sizeof(int) * (size_t)max_slots)) != cudaSuccess) break;
     if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess) break;
     if ((e = cudaStreamCreateWithFlags(&p->io, cudaStreamNonBlocking)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&p->d_ticket, sizeof(int))) != cudaSuccess) break;
     for (int i = 0; i < aco_pool::kStepEvents && e == cudaSuccess; ++i)
       e = cudaEventCreateWithFlags(&p->step_ev[i], cudaEventDisableTiming);
     for (int i = 0; i < aco_pool::kClassStreams && e == cudaSuccess; ++i) {
@@ -743,6 +777,7 @@ int aco_pool_destroy(aco_pool_handle p) {
   if (p->d_live) cudaFree(p->d_live);
   if (p->d_acs) cudaFree(p->d_acs);
   if (p->d_cls_slots) cudaFree(p->d_cls_slots);
+  if (p->d_ticket) cudaFree(p->d_ticket);
   if (p->d_items) cudaFree(p->d_items);
   if (p->d_rows) cudaFree(p->d_rows);
   for (int i = 0; i < aco_pool::kClassStreams; ++i) {
@@ -860,6 +895,14 @@ int aco_pool_step(aco_pool_handle p, int32_t* live_after) {
     for (const auto& sl : p->slots) live += sl.live ? 1 : 0;
     *live_after = live;
   }
+  return ACO_OK;
+}
+
+int aco_pool_set_single_launch(aco_pool_handle p, int32_t on) {
+  if (!p) return fail(ACO_EINVAL, "NULL pool");
+  if (on != 0 && on != 1) return fail(ACO_EINVAL, "on must be 0 or 1");
+  p->single_launch = on != 0;
+  p->dirty = true;
   return ACO_OK;
 }
 

@@ -268,3 +268,32 @@ def test_tuning_table_round_trips_through_json(aco, tmp_path):
         assert aco.aco_pool_get_tuning(b) == table
     finally:
         aco.aco_batch_destroy(b)
+
+
+def test_single_construction_launch_equals_alone(aco):
+    # Every class of the batch in one persistent construction launch (items
+    # from a global ticket, each with its class's chunk width): the instances
+    # end as when run alone, and the step has fewer launches than with one
+    # launch per class.
+    ns = [48, 130, 300, 517, 700, 1000, 77, 900]
+    insts = [I.uniform_instance(n, 1000, seed=700 + n) for n in ns]
+    ms = [min(n, 160) for n in ns]
+    seeds = [40 + i for i in range(len(ns))]
+    launches = {}
+    for single in (False, True):
+        b = aco.aco_batch_create([x.dist for x in insts], ms, seeds)
+        try:
+            aco.aco_pool_set_single_launch(b, single)
+            aco.aco_batch_iterate(b, 4)
+            launches[single] = aco.aco_pool_stats(b)["launches_last_step"]
+            for i, x in enumerate(insts):
+                tau_a, (tour_a, len_a) = alone(aco, x.dist, ms[i], seeds[i], 4)
+                tour_b, len_b = aco.aco_batch_best(b, i, x.n)
+                assert len_b == len_a and np.array_equal(tour_b, tour_a), (single, i)
+                assert np.array_equal(aco.aco_pool_pheromone(b, i, x.n), tau_a), (single, i)
+        finally:
+            aco.aco_batch_destroy(b)
+    assert launches[True] < launches[False]
+    with pytest.raises(aco.AcoError) as e:
+        aco.aco_pool_set_single_launch(None, True)
+    assert e.value.code == aco.ACO_EINVAL
