@@ -527,7 +527,7 @@ def run_ours(args, w, rank, world, local):
 
 
 CONSTRUCT_SOURCES = ("aco_device.cuh", "construct.cuh", "construct_chunks.h", "construct_dispatch.cuh",
-                     "construct_g1h8.cu", "construct_g1h16.cu", "construct_g1h32.cu",
+                     "construct_phased.cuh", "construct_g1h8.cu", "construct_g1h16.cu", "construct_g1h32.cu",
                      "construct_g2h32.cu", "construct_g4h32.cu", "construct_rule.cuh",
                      "construct_rule1.cu", "construct_rule2.cu")
 

@@ -270,12 +270,12 @@ struct Seg {
 
 // Cities per lane before and after the compactions of the Eq. 1 walk (see
 // construct_phased.cuh): C, then 4*ceil(C/8), 4*ceil(C/16) and 4*ceil(C/32).
-// One warp (or segment) per ant with C >= kCompactMinC compacts; other
-// tilings never do.
+// One warp (or segment) or two warps per ant with C >= kCompactMinC compact;
+// four warps per ant never do.
 constexpr int kCompactMinC = 20;
 template <int C, int G>
 struct Compaction {
-  static constexpr bool kOn = G == 1 && C >= kCompactMinC;
+  static constexpr bool kOn = (G == 1 || G == 2) && C >= kCompactMinC;
   static constexpr int kC1 = 4 * ((C + 7) / 8);
   static constexpr int kC2 = 4 * ((C + 15) / 16);
   static constexpr int kC3 = 4 * ((C + 31) / 32);
@@ -288,7 +288,7 @@ template <int C, int G, int H>
 struct StageLayout {
   static constexpr int kRowFloats = H * G * C;
   static constexpr int kListOffset = kRowFloats * 4 + 16;
-  static constexpr int kListEntries = Compaction<C, G>::kOn ? H * Compaction<C, G>::kC1 : 0;
+  static constexpr int kListEntries = Compaction<C, G>::kOn ? H * G * Compaction<C, G>::kC1 : 0;
   static constexpr int kBytes = ((kListOffset + 2 * kListEntries) + 15) / 16 * 16;
 };
 
@@ -849,31 +849,33 @@ struct PhasedRegs {
   static constexpr int v = C <= 28 ? 64 : (C <= 36 ? 80 : 128);
 };
 
-template <int C, int H>
+template <int C, int G, int H>
 __global__ void __maxnreg__((PhasedRegs<C>::v)) construct_phased_kernel(Instance I) {
+  __shared__ GroupSmem gs[kMaxGroupsPerCta];
   extern __shared__ __align__(16) unsigned char stage[];
   int grp, tg;
-  group_of_thread<1, H>(grp, tg);
-  const int ant = blockIdx.x * groups_per_cta<1, H>(blockDim.x >> 5) + grp;
+  group_of_thread<G, H>(grp, tg);
+  const int ant = blockIdx.x * groups_per_cta<G, H>(blockDim.x >> 5) + grp;
   if (ant >= I.m) return;
-  construct_ant_phased<C, H, false>(
-      I, ant, Seg<H>(threadIdx.x & 31),
-      reinterpret_cast<float*>(stage + grp * StageLayout<C, 1, H>::kBytes), I.stage != 0);
+  construct_ant_phased<C, G, H, false>(
+      I, ant, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
+      reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes), I.stage != 0);
 }
 
-template <int C, int H>
+template <int C, int G, int H>
 __global__ void __maxnreg__((PhasedRegs<C>::v))
     construct_phased_items_kernel(const Instance* __restrict__ insts,
                                   const int2* __restrict__ items, int count, int lane_copy) {
+  __shared__ GroupSmem gs[kMaxGroupsPerCta];
   extern __shared__ __align__(16) unsigned char stage[];
   int grp, tg;
-  group_of_thread<1, H>(grp, tg);
-  const int idx = blockIdx.x * groups_per_cta<1, H>(blockDim.x >> 5) + grp;
+  group_of_thread<G, H>(grp, tg);
+  const int idx = blockIdx.x * groups_per_cta<G, H>(blockDim.x >> 5) + grp;
   if (idx >= count) return;
   const int2 it = items[idx];
-  construct_ant_phased<C, H, true>(
-      insts[it.x], it.y, Seg<H>(threadIdx.x & 31),
-      reinterpret_cast<float*>(stage + grp * StageLayout<C, 1, H>::kBytes), lane_copy != 0);
+  construct_ant_phased<C, G, H, true>(
+      insts[it.x], it.y, tg, Seg<H>(threadIdx.x & 31), &gs[H == 32 ? grp : 0], 1 + grp,
+      reinterpret_cast<float*>(stage + grp * StageLayout<C, G, H>::kBytes), lane_copy != 0);
 }
 
 // Dynamic shared memory for a CTA of `warps` warps, with the opt-in above
@@ -886,13 +888,13 @@ inline size_t construct_smem_setup(int warps) {
     const int most = groups_per_cta<G, H>(8) * StageLayout<C, G, H>::kBytes;
     constexpr bool kPhased = R == 0 && Compaction<C, G>::kOn;
     if constexpr (kItems && kPhased)
-      return cudaFuncSetAttribute(construct_phased_items_kernel<C, H>,
+      return cudaFuncSetAttribute(construct_phased_items_kernel<C, G, H>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     else if constexpr (kItems)
       return cudaFuncSetAttribute(construct_items_kernel<C, G, H>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     else if constexpr (kPhased)
-      return cudaFuncSetAttribute(construct_phased_kernel<C, H>,
+      return cudaFuncSetAttribute(construct_phased_kernel<C, G, H>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     else
       return cudaFuncSetAttribute(construct_kernel<C, G, H, R>,

@@ -17,7 +17,7 @@ inline bool launch_one(int c, const Instance& I, int grid, int warps, cudaStream
   if (c != C) return false;
   const size_t smem = construct_smem_setup<C, G, H, false, R>(warps);
   if constexpr (R == 0 && Compaction<C, G>::kOn)
-    construct_phased_kernel<C, H><<<grid, 32 * warps, smem, st>>>(I);
+    construct_phased_kernel<C, G, H><<<grid, 32 * warps, smem, st>>>(I);
   else
     construct_kernel<C, G, H, R><<<grid, 32 * warps, smem, st>>>(I);
   return true;
@@ -29,7 +29,7 @@ inline bool launch_items_one(int c, const Instance* insts, const int2* items, in
   if (c != C) return false;
   const size_t smem = construct_smem_setup<C, G, H, true>(warps);
   if constexpr (Compaction<C, G>::kOn)
-    construct_phased_items_kernel<C, H><<<grid, 32 * warps, smem, st>>>(insts, items, count,
+    construct_phased_items_kernel<C, G, H><<<grid, 32 * warps, smem, st>>>(insts, items, count,
                                                                         lane_copy);
   else
     construct_items_kernel<C, G, H><<<grid, 32 * warps, smem, st>>>(insts, items, count,

@@ -47,13 +47,13 @@ __global__ void __maxnreg__(80)
         construct_ant<12, 1, 32, 0, true>(I, it.y, lane, seg, &gs[warp], 1 + warp, srow, lc);
         break;
       case 20:
-        construct_ant_phased<20, 32, true>(I, it.y, seg, srow, lc);
+        construct_ant_phased<20, 1, 32, true>(I, it.y, lane, seg, &gs[warp], 1 + warp, srow, lc);
         break;
       case 28:
-        construct_ant_phased<28, 32, true>(I, it.y, seg, srow, lc);
+        construct_ant_phased<28, 1, 32, true>(I, it.y, lane, seg, &gs[warp], 1 + warp, srow, lc);
         break;
       case 36:
-        construct_ant_phased<36, 32, true>(I, it.y, seg, srow, lc);
+        construct_ant_phased<36, 1, 32, true>(I, it.y, lane, seg, &gs[warp], 1 + warp, srow, lc);
         break;
       default:
         break;

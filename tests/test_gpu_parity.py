@@ -93,21 +93,29 @@ def test_first_iteration_tours_match_oracle(aco, orc, n):
             aco.aco_set_option(c.h, aco.ACO_OPT_STAGING, 0)
 
 
-# The walk with compaction (one warp or segment per ant, C >= 20): the
+# The walk with compaction (one warp, segment or two warps per ant, C >= 20): the
 # largest size without it and the smallest with it for whole warps (n = 384,
 # C = 12; n = 385, C = 20), the widest size of two chunk widths (n = 640,
 # C = 20; n = 1152, C = 36), the widest chunk of whole warps (C = 76,
 # n = 2432) and of 16- and 8-lane segments, with both row stagings.  The
 # tours of the first iteration, and a second iteration on the updated
 # trails, equal the oracle's.
-@pytest.mark.parametrize("n,lanes", [(384, 32), (385, 32), (640, 32), (700, 16), (1152, 32),
-                                     (1216, 16), (600, 8), (2432, 32)])
-def test_compacting_walk_matches_oracle(aco, orc, n, lanes):
+# Two warps per ant (the default above n = 2432) compact as well: n from just
+# above a single warp's reach to the largest n, and a small n forced to two
+# warps.
+@pytest.mark.parametrize("n,lanes,warps", [(384, 32, 1), (385, 32, 1), (640, 32, 1), (700, 16, 1),
+                                           (1152, 32, 1), (1216, 16, 1), (600, 8, 1),
+                                           (2432, 32, 1), (2433, 32, 2), (3100, 32, 2),
+                                           (4096, 32, 2), (900, 32, 2)])
+def test_compacting_walk_matches_oracle(aco, orc_all_cores, n, lanes, warps):
+    orc = orc_all_cores
     inst = I.clustered_instance(n, seed=n + lanes, clusters=16, sigma=400, side=20000)
     m = 40
     ref = orc.run(inst.dist, m, 2, 11)
     with aco.Colony(inst.dist, m, seed=11) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_WARPS_PER_ANT, warps)
         aco.aco_set_option(c.h, aco.ACO_OPT_LANES_PER_ANT, lanes)
+        assert aco.aco_get_option(c.h, aco.ACO_OPT_WARPS_PER_ANT) == warps
         for stage in (0, 1):
             aco.aco_set_option(c.h, aco.ACO_OPT_STAGING, stage)
             tours, lens = aco.aco_construct_tours(c.h, n, m)
@@ -121,6 +129,28 @@ def test_compacting_walk_matches_oracle(aco, orc, n, lanes):
         aco.aco_update_pheromone(c.h)
         assert np.array_equal(tours, ref["tours"]) and np.array_equal(lens, ref["lens"])
         assert np.array_equal(aco.aco_get_pheromone(c.h, n), ref["tau32"])
+
+
+# rho = 1 leaves pheromone only on the edges the last ants used, so in the
+# compacted phases every unvisited weight is often zero and the walk takes
+# the lowest unvisited city (the zero-weight rule); the slot that holds it is
+# marked by its own lane (one warp, segments) or thread (two warps).
+@pytest.mark.parametrize("n,lanes,warps", [(900, 32, 1), (600, 8, 1), (900, 32, 2),
+                                           (2433, 32, 2)])
+def test_compacting_walk_zero_weights(aco, orc_all_cores, n, lanes, warps):
+    orc = orc_all_cores
+    inst = I.clustered_instance(n, seed=n + 7 * warps, clusters=12, sigma=300, side=20000)
+    m, iters = 24, 3
+    ref = orc.run(inst.dist, m, iters, 5, rho=1.0)
+    with aco.Colony(inst.dist, m, seed=5, rho=1.0) as c:
+        aco.aco_set_option(c.h, aco.ACO_OPT_WARPS_PER_ANT, warps)
+        aco.aco_set_option(c.h, aco.ACO_OPT_LANES_PER_ANT, lanes)
+        aco.aco_iterate(c.h, iters)
+        tau = aco.aco_get_pheromone(c.h, n)
+        tour, best = aco.aco_best_tour(c.h, n)
+    assert (tau == 0).mean() > 0.85  # most weights really are zero
+    assert np.array_equal(tau, ref["tau32"])
+    assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
 
 
 @pytest.mark.parametrize("wl,ants", [("n1002", 12), ("n2392", 6)])
