@@ -220,6 +220,14 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
         hs += phi[k];
         ls += plo[k];
       }
+      // Inclusive sums of the thread's first K - 1 parts (they overlap the
+      // scan below; the selected lane's are used for the part choice).
+      unsigned long long pincl[K > 1 ? K - 1 : 1];
+      if constexpr (K > 1) {
+        pincl[0] = part_value<CP, K>(phi, plo, 0);
+#pragma unroll
+        for (int k = 1; k < K - 1; ++k) pincl[k] = pincl[k - 1] + part_value<CP, K>(phi, plo, k);
+      }
       const uint32_t offb = (uint32_t)CP * kTwo23Bits;
       const unsigned long long mine = ((unsigned long long)(hs - offb) << 23) + (ls - offb);
       const unsigned long long incl = seg.inclusive_scan(mine);
@@ -242,26 +250,22 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
       const unsigned long long t1 = T - woff;
       const int L = max(__ffs(seg.ballot(incl > t1)) - 1, 0);
       const unsigned long long t2 = t1 - seg.shfl(incl - mine, L);
-      // Lane L finds the part of its slots that holds the target.
+      // The part of lane L's slots that holds the target: the first whose
+      // inclusive sum exceeds t2 (the sums ascend, so it is the count of
+      // those at most t2).  Every lane takes lane L's sums and decides alike.
       int part = 0;
       unsigned long long t3 = t2;
       if constexpr (K > 1) {
-        if (hl == L) {
-          unsigned long long cum = 0;
-          bool found = false;
+        unsigned long long before = 0;
 #pragma unroll
-          for (int k = 0; k < K; ++k) {
-            const unsigned long long pv = part_value<CP, K>(phi, plo, k);
-            if (!found && (k == K - 1 || cum + pv > t2)) {
-              found = true;
-              part = k;
-              t3 = t2 - cum;
-            }
-            cum += pv;
+        for (int k = 0; k < K - 1; ++k) {
+          const unsigned long long pk = seg.shfl(pincl[k], L);
+          if (pk <= t2) {
+            part = k + 1;
+            before = pk;
           }
         }
-        part = seg.shfl(part, L);
-        t3 = seg.shfl(t3, L);
+        t3 = t2 - before;
       }
       // The segment rescans that part, PP slots per lane.
       const int pstart = 4 * (part * Parts::NG / K);
