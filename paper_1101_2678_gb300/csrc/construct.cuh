@@ -288,6 +288,9 @@ template <int C, int G, int H>
 struct StageLayout {
   static constexpr int kRowFloats = H * G * C;
   static constexpr int kListOffset = kRowFloats * 4 + 16;
+  // A float index beside the row (after the mbarrier, before the list) that
+  // holds 0: the list entry of a visited slot of the walk with compaction.
+  static constexpr int kZeroSlot = kRowFloats + 2;
   static constexpr int kListEntries = Compaction<C, G>::kOn ? H * G * Compaction<C, G>::kC1 : 0;
   static constexpr int kBytes = ((kListOffset + 2 * kListEntries) + 15) / 16 * 16;
 };

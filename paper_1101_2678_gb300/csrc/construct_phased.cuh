@@ -11,8 +11,10 @@
 //            kernel, lane t owns the contiguous chunk [tC, tC + C) of the row;
 //   phase 1  the unvisited cities, in ascending order, are listed in shared
 //            memory and dealt out C1 = 4*ceil(C/8) per lane (lane t takes
-//            entries [t*C1, t*C1 + C1)); each step reads their weights from
-//            the staged row by index;
+//            entries [t*C1, t*C1 + C1)); each step reads the entries and
+//            then their weights from the staged row by index.  A visited
+//            slot's entry is set to the index of a float beside the row that
+//            stays 0, so these phases keep no tabu bits and mask nothing;
 //   phase 2  the same with C2 = 4*ceil(C/16) per lane;
 //   phase 3  the same with C3 = 4*ceil(C/32) per lane (when smaller than C2).
 // Phase p starts at the first step at which the unvisited cities fit in the
@@ -76,10 +78,13 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
   int32_t* tour = I.tours + (size_t)ant * I.ldt;
   const float* const choice = I.choice;
 
-  // Tabu bits (1 = visited, or no city in the slot) and, when gathering, the
-  // city of each slot.
-  uint32_t vis[NW];
-  uint32_t city[kGather ? CP : 1];
+  // Direct phase: tabu bits (1 = visited, or no city in the slot).  Gather
+  // phases keep no tabu bits: a slot's list entry is its city while it is
+  // unvisited, and kZeroSlot (the index of a float that stays 0 beside the
+  // staged row) once it is visited or holds no city, so a visited slot
+  // reads weight 0 and is never chosen.
+  constexpr uint32_t kZeroSlot = StageLayout<C, G, H>::kZeroSlot;
+  uint32_t vis[kGather ? 1 : NW];
   if constexpr (!kGather) {
 #pragma unroll
     for (int wd = 0; wd < NW; ++wd) {
@@ -96,15 +101,13 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
         if (wd == (li >> 5)) vis[wd] |= 1u << (li & 31);
     }
   } else {
-#pragma unroll
-    for (int wd = 0; wd < NW; ++wd) vis[wd] = (wd == NW - 1 && CP % 32) ? (FULL << (CP % 32)) : 0u;
+    // The thread's slots past the listed cities point at the zero weight.
 #pragma unroll
     for (int i = 0; i < CP; ++i) {
       const int k = tg * CP + i;
-      const bool ok = k < w.live;
-      city[i] = ok ? (uint32_t)ulist[k] : 0u;
-      if (!ok) vis[i >> 5] |= 1u << (i & 31);
+      if (k >= w.live) ulist[k] = (uint16_t)kZeroSlot;
     }
+    group_wait();  // other lanes read these entries in the rescan
   }
 
   for (; w.s < s_end; ++w.s) {
@@ -125,6 +128,8 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
       w.rwin = ((unsigned long long)x.x1 << 32) | x.x0;
     }
     const unsigned long long r = seg.shfl(w.rwin, off);
+    // Gather phases: the thread's list entries, read while the row is in
+    // flight (only this thread has written them since the last barrier).
     if (lane_copy) {
       group_wait();
     } else {
@@ -147,13 +152,22 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
         v[i + 3] = t.w;
       }
     } else {
+      const uint2* lw = reinterpret_cast<const uint2*>(ulist + tg * CP);
 #pragma unroll
-      for (int i = 0; i < CP; ++i) v[i] = __float_as_uint(row[city[i]]);
+      for (int i = 0; i < CP; i += 4) {
+        const uint2 e = lw[i >> 2];
+        v[i] = __float_as_uint(row[e.x & 0xffffu]);
+        v[i + 1] = __float_as_uint(row[e.x >> 16]);
+        v[i + 2] = __float_as_uint(row[e.y & 0xffffu]);
+        v[i + 3] = __float_as_uint(row[e.y >> 16]);
+      }
     }
     uint32_t m4[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int i = 0; i < CP; ++i) {
-      if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+      if constexpr (!kGather) {
+        if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+      }
       m4[i & 3] = max(m4[i & 3], v[i]);
     }
     uint32_t mx = seg.max_u32(max(max(m4[0], m4[1]), max(m4[2], m4[3])));
@@ -176,9 +190,13 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
           if (fr) cand = (uint32_t)(base + 32 * wd + __ffs(fr) - 1);
         }
       } else {
+        // the smallest entry: kZeroSlot is above every city
+        const uint2* lw = reinterpret_cast<const uint2*>(ulist + tg * CP);
 #pragma unroll
-        for (int i = CP - 1; i >= 0; --i)
-          if (!((vis[i >> 5] >> (i & 31)) & 1u)) cand = city[i];
+        for (int i = 0; i < CP; i += 4) {
+          const uint2 e = lw[i >> 2];
+          cand = min(cand, min(min(e.x & 0xffffu, e.x >> 16), min(e.y & 0xffffu, e.y >> 16)));
+        }
       }
       cand = seg.min_u32(cand);
       if constexpr (G > 1) {
@@ -188,21 +206,12 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
         for (int k = 0; k < G; ++k) cand = min(cand, (uint32_t)gs->wmin[k]);
       }
       next = (int)cand;
-      if constexpr (kGather && G > 1) {
-        // the thread whose slot holds that city marks it
+      if constexpr (kGather) {
+        // the thread whose slot holds that city points the slot at the zero
+        // weight (no other thread reads the list until the step's end)
 #pragma unroll
         for (int i = 0; i < CP; ++i)
-          if (city[i] == cand) vis[i >> 5] |= 1u << (i & 31);
-      } else if constexpr (kGather) {
-        // one warp: its lowest lane holding the city marks it below
-        // (measured 1.3 % faster at C = 36 than the two-warp marking)
-        int mine = -1;
-#pragma unroll
-        for (int i = CP - 1; i >= 0; --i)
-          if (!((vis[i >> 5] >> (i & 31)) & 1u) && city[i] == cand) mine = i;
-        const uint32_t own = seg.ballot(mine >= 0);
-        chosen = own ? __ffs(own) - 1 : -1;
-        chosen_slot = chosen >= 0 ? seg.shfl(mine, chosen) : 0;
+          if (ulist[tg * CP + i] == cand) ulist[tg * CP + i] = (uint16_t)kZeroSlot;
       }
     } else {
       const int sc = kRouletteBits - 1 - exponent_of_bits(mx);
@@ -270,9 +279,13 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
       // The segment rescans that part, PP slots per lane.
       const int pstart = 4 * (part * Parts::NG / K);
       const int psz = 4 * ((part + 1) * Parts::NG / K) - pstart;
-      uint32_t visL[NW];
+      // lane L's tabu bits (direct phase; gather phases read them from the
+      // list: a visited slot reads weight 0)
+      uint32_t visL[kGather ? 1 : NW];
+      if constexpr (!kGather) {
 #pragma unroll
-      for (int wd = 0; wd < NW; ++wd) visL[wd] = seg.shfl(vis[wd], L);
+        for (int wd = 0; wd < NW; ++wd) visL[wd] = seg.shfl(vis[wd], L);
+      }
       unsigned long long qv[PP];
       int cc[PP];
       unsigned long long ps = 0;
@@ -280,19 +293,19 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
       for (int p = 0; p < PP; ++p) {
         const int pi = hl * PP + p;  // position within the part
         const int li = pstart + pi;  // slot within lane L's slots
-        uint32_t word = FULL;
-#pragma unroll
-        for (int wd = 0; wd < NW; ++wd)
-          if (wd == (li >> 5)) word = visL[wd];
         uint32_t w8 = 0u;
         int c = 0;
-        const bool open = pi < psz && !((word >> (li & 31)) & 1u);
         const int tL = wg * 32 + L;  // thread of lane L within the group
         if constexpr (!kGather) {
+          uint32_t word = FULL;
+#pragma unroll
+          for (int wd = 0; wd < NW; ++wd)
+            if (wd == (li >> 5)) word = visL[wd];
+          const bool open = pi < psz && !((word >> (li & 31)) & 1u);
           c = (G > 1 ? tL : L) * C + li;
           if (open && c < ld) w8 = __float_as_uint(row[c]);
         } else {
-          if (open) {
+          if (pi < psz) {
             c = (int)ulist[(G > 1 ? tL : L) * CP + li];
             w8 = __float_as_uint(row[c]);
           }
@@ -354,9 +367,9 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
           if (wd == (li >> 5)) vis[wd] |= 1u << (li & 31);
       }
     } else if (tg == chosen) {
-#pragma unroll
-      for (int wd = 0; wd < NW; ++wd)
-        if (wd == (chosen_slot >> 5)) vis[wd] |= 1u << (chosen_slot & 31);
+      // every read of this entry in this step came before the shuffle that
+      // decided it
+      ulist[tg * CP + chosen_slot] = (uint16_t)kZeroSlot;
     }
     if (tg == 0) tour[s] = next;
     w.cur = next;
@@ -367,8 +380,23 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
     // List the unvisited cities for the next phase, ascending: lane after
     // lane, each lane's slots in order.
     uint32_t cnt = 0;
+    uint32_t own[kGather ? CP : 1];  // gather phases: the thread's entries
+    if constexpr (kGather) {
+      const uint2* lw = reinterpret_cast<const uint2*>(ulist + tg * CP);
 #pragma unroll
-    for (int wd = 0; wd < NW; ++wd) cnt += __popc(~vis[wd]);
+      for (int i = 0; i < CP; i += 4) {
+        const uint2 e = lw[i >> 2];
+        own[i] = e.x & 0xffffu;
+        own[i + 1] = e.x >> 16;
+        own[i + 2] = e.y & 0xffffu;
+        own[i + 3] = e.y >> 16;
+      }
+#pragma unroll
+      for (int i = 0; i < CP; ++i) cnt += own[i] != kZeroSlot ? 1u : 0u;
+    } else {
+#pragma unroll
+      for (int wd = 0; wd < NW; ++wd) cnt += __popc(~vis[wd]);
+    }
     const unsigned long long incl = seg.inclusive_scan((unsigned long long)cnt);
     int total = (int)seg.shfl(incl, H - 1);
     int k = (int)(incl - cnt);
@@ -386,9 +414,14 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
     group_wait();  // the list of this phase is no longer read
 #pragma unroll
     for (int i = 0; i < CP; ++i) {
-      if (!((vis[i >> 5] >> (i & 31)) & 1u)) {
+      bool live;
+      if constexpr (kGather)
+        live = own[i] != kZeroSlot;
+      else
+        live = !((vis[i >> 5] >> (i & 31)) & 1u);
+      if (live) {
         // a defect can leave more entries than the list holds: keep in bounds
-        if (k < kListCap) ulist[k] = (uint16_t)(kGather ? city[i] : (uint32_t)(base + i));
+        if (k < kListCap) ulist[k] = (uint16_t)(kGather ? own[i] : (uint32_t)(base + i));
         ++k;
       }
     }
@@ -427,6 +460,7 @@ __device__ __forceinline__ void construct_ant_phased(const Instance& I, const in
   if (tg == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
+    srow[StageLayout<C, G, H>::kZeroSlot] = 0.0f;  // the weight of a visited list slot
   }
   group_wait();
 
