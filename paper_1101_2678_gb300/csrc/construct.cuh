@@ -268,17 +268,34 @@ struct Seg {
   __device__ __forceinline__ void sync() const { __syncwarp(mask); }
 };
 
-// Cities per lane before and after the compactions of the Eq. 1 walk (see
-// construct_phased.cuh): C, then 4*ceil(C/8), 4*ceil(C/16) and 4*ceil(C/32).
-// One warp (or segment) or two warps per ant with C >= kCompactMinC compact;
-// four warps per ant never do.
+// Cities per thread before and after the compactions of the Eq. 1 walk (see
+// construct_phased.cuh): C, then 4*ceil(C/8), 4*ceil(C/16) and 4*ceil(C/32)
+// (about C/2, C/4 and C/8 in whole 4-city groups), repeats dropped.  Adding
+// 4*ceil(3C/16), or that and 4*ceil(3C/32), measured slower at every size:
+// 0.2-2 % for one instance, 10 % for the batched step.  One warp (or
+// segment) or two warps per ant with C >= kCompactMinC compact; four warps
+// per ant never do.
 constexpr int kCompactMinC = 20;
 template <int C, int G>
 struct Compaction {
   static constexpr bool kOn = (G == 1 || G == 2) && C >= kCompactMinC;
-  static constexpr int kC1 = 4 * ((C + 7) / 8);
-  static constexpr int kC2 = 4 * ((C + 15) / 16);
-  static constexpr int kC3 = 4 * ((C + 31) / 32);
+  // candidate count i: C * kSixteenths[i] / 16 rounded up to a multiple of 4
+  __host__ __device__ static constexpr int raw(int i) {
+    constexpr int kSixteenths[4] = {16, 8, 4, 2};
+    return kSixteenths[i] == 16 ? C : 4 * ((kSixteenths[i] * C + 63) / 64);
+  }
+  // Slot count of phase j (0 = the direct phase, C), or 0 past the last.
+  __host__ __device__ static constexpr int slots(int j) {
+    int prev = 1 << 30, k = -1;
+    for (int i = 0; i < 4; ++i) {
+      const int v = raw(i);
+      if (v > 0 && v < prev) {
+        if (++k == j) return v;
+        prev = v;
+      }
+    }
+    return 0;
+  }
 };
 
 // Shared memory of one ant group: the staged row (H*G*C floats, 16-byte
@@ -291,7 +308,7 @@ struct StageLayout {
   // A float index beside the row (after the mbarrier, before the list) that
   // holds 0: the list entry of a visited slot of the walk with compaction.
   static constexpr int kZeroSlot = kRowFloats + 2;
-  static constexpr int kListEntries = Compaction<C, G>::kOn ? H * G * Compaction<C, G>::kC1 : 0;
+  static constexpr int kListEntries = Compaction<C, G>::kOn ? H * G * Compaction<C, G>::slots(1) : 0;
   static constexpr int kBytes = ((kListOffset + 2 * kListEntries) + 15) / 16 * 16;
 };
 

@@ -31,6 +31,16 @@
 
 namespace aco {
 
+// The weight bits a list entry points at: entry = city * kUnit (kUnit 1: a
+// city index; 4: a byte offset into the staged row).
+template <uint32_t kUnit>
+__device__ __forceinline__ uint32_t entry_weight(const float* row, uint32_t e) {
+  if constexpr (kUnit == 4u)
+    return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(row) + e);
+  else
+    return __float_as_uint(row[e]);
+}
+
 struct WalkState {
   int cur;       // current city
   int s;         // next step (1 .. n-1)
@@ -79,11 +89,17 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
   const float* const choice = I.choice;
 
   // Direct phase: tabu bits (1 = visited, or no city in the slot).  Gather
-  // phases keep no tabu bits: a slot's list entry is its city while it is
-  // unvisited, and kZeroSlot (the index of a float that stays 0 beside the
-  // staged row) once it is visited or holds no city, so a visited slot
-  // reads weight 0 and is never chosen.
+  // phases keep no tabu bits: a slot's list entry points at its city's
+  // weight in the staged row while it is unvisited, and at kZeroSlot (a
+  // float beside the row that stays 0) once it is visited or holds no city,
+  // so a visited slot reads weight 0 and is never chosen.
   constexpr uint32_t kZeroSlot = StageLayout<C, G, H>::kZeroSlot;
+  // A single instance lists byte offsets into the staged row (city * 4: no
+  // address arithmetic per read), pools list city indices (measured faster
+  // for the batched classes, slower for one instance).
+  constexpr uint32_t kUnit = kPool ? 1u : 4u;
+  constexpr uint32_t kZeroEntry = kZeroSlot * kUnit;
+  static_assert(kZeroEntry <= 0xffffu, "list entries are 16-bit");
   uint32_t vis[kGather ? 1 : NW];
   if constexpr (!kGather) {
 #pragma unroll
@@ -105,7 +121,7 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
 #pragma unroll
     for (int i = 0; i < CP; ++i) {
       const int k = tg * CP + i;
-      if (k >= w.live) ulist[k] = (uint16_t)kZeroSlot;
+      if (k >= w.live) ulist[k] = (uint16_t)kZeroEntry;
     }
     group_wait();  // other lanes read these entries in the rescan
   }
@@ -156,10 +172,10 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
 #pragma unroll
       for (int i = 0; i < CP; i += 4) {
         const uint2 e = lw[i >> 2];
-        v[i] = __float_as_uint(row[e.x & 0xffffu]);
-        v[i + 1] = __float_as_uint(row[e.x >> 16]);
-        v[i + 2] = __float_as_uint(row[e.y & 0xffffu]);
-        v[i + 3] = __float_as_uint(row[e.y >> 16]);
+        v[i] = entry_weight<kUnit>(row, e.x & 0xffffu);
+        v[i + 1] = entry_weight<kUnit>(row, e.x >> 16);
+        v[i + 2] = entry_weight<kUnit>(row, e.y & 0xffffu);
+        v[i + 3] = entry_weight<kUnit>(row, e.y >> 16);
       }
     }
     uint32_t m4[4] = {0u, 0u, 0u, 0u};
@@ -190,7 +206,7 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
           if (fr) cand = (uint32_t)(base + 32 * wd + __ffs(fr) - 1);
         }
       } else {
-        // the smallest entry: kZeroSlot is above every city
+        // the smallest entry: kZeroEntry is above every city's
         const uint2* lw = reinterpret_cast<const uint2*>(ulist + tg * CP);
 #pragma unroll
         for (int i = 0; i < CP; i += 4) {
@@ -205,13 +221,15 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
 #pragma unroll
         for (int k = 0; k < G; ++k) cand = min(cand, (uint32_t)gs->wmin[k]);
       }
+      const uint32_t cand_entry = cand;  // gather phases: the list entry
+      if constexpr (kGather) cand /= kUnit;
       next = (int)cand;
       if constexpr (kGather) {
         // the thread whose slot holds that city points the slot at the zero
         // weight (no other thread reads the list until the step's end)
 #pragma unroll
         for (int i = 0; i < CP; ++i)
-          if (ulist[tg * CP + i] == cand) ulist[tg * CP + i] = (uint16_t)kZeroSlot;
+          if (ulist[tg * CP + i] == cand_entry) ulist[tg * CP + i] = (uint16_t)kZeroEntry;
       }
     } else {
       const int sc = kRouletteBits - 1 - exponent_of_bits(mx);
@@ -306,8 +324,9 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
           if (open && c < ld) w8 = __float_as_uint(row[c]);
         } else {
           if (pi < psz) {
-            c = (int)ulist[(G > 1 ? tL : L) * CP + li];
-            w8 = __float_as_uint(row[c]);
+            const uint32_t e = ulist[(G > 1 ? tL : L) * CP + li];
+            w8 = entry_weight<kUnit>(row, e);
+            c = (int)(e / kUnit);
           }
         }
         cc[p] = c;
@@ -369,7 +388,7 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
     } else if (tg == chosen) {
       // every read of this entry in this step came before the shuffle that
       // decided it
-      ulist[tg * CP + chosen_slot] = (uint16_t)kZeroSlot;
+      ulist[tg * CP + chosen_slot] = (uint16_t)kZeroEntry;
     }
     if (tg == 0) tour[s] = next;
     w.cur = next;
@@ -392,7 +411,7 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
         own[i + 3] = e.y >> 16;
       }
 #pragma unroll
-      for (int i = 0; i < CP; ++i) cnt += own[i] != kZeroSlot ? 1u : 0u;
+      for (int i = 0; i < CP; ++i) cnt += own[i] != kZeroEntry ? 1u : 0u;
     } else {
 #pragma unroll
       for (int wd = 0; wd < NW; ++wd) cnt += __popc(~vis[wd]);
@@ -416,18 +435,37 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
     for (int i = 0; i < CP; ++i) {
       bool live;
       if constexpr (kGather)
-        live = own[i] != kZeroSlot;
+        live = own[i] != kZeroEntry;
       else
         live = !((vis[i >> 5] >> (i & 31)) & 1u);
       if (live) {
         // a defect can leave more entries than the list holds: keep in bounds
-        if (k < kListCap) ulist[k] = (uint16_t)(kGather ? own[i] : (uint32_t)(base + i));
+        if (k < kListCap) ulist[k] = (uint16_t)(kGather ? own[i] : kUnit * (uint32_t)(base + i));
         ++k;
       }
     }
     w.live = total < NT * CPN ? total : NT * CPN;
     group_wait();
   }
+}
+
+// Phase J of the walk and the ones after it.  Phase J runs while the
+// unvisited cities do not fit in the next phase's slots, then lists them for
+// it; the last phase runs to the end of the tour.
+template <int C, int G, int H, bool kPool, int J>
+__device__ __forceinline__ void eq1_phases(const Instance& I, const int ant, const int tg,
+                                           const Seg<H> seg, GroupSmem* gs, const int bar_id,
+                                           float* srow, uint16_t* ulist, const int start,
+                                           WalkState& w, const bool lane_copy) {
+  using Cm = Compaction<C, G>;
+  constexpr int CP = Cm::slots(J);
+  constexpr int CPN = Cm::slots(J + 1);
+  const int s_end = CPN > 0 ? max(w.s, I.n - G * H * CPN) : I.n;
+  eq1_phase<C, CP, CPN, G, H, (J > 0), kPool>(I, ant, tg, seg, gs, bar_id, srow, ulist, start,
+                                              s_end, w, lane_copy);
+  if constexpr (CPN > 0)
+    eq1_phases<C, G, H, kPool, J + 1>(I, ant, tg, seg, gs, bar_id, srow, ulist, start, w,
+                                      lane_copy);
 }
 
 // The whole walk of one ant (G warps or one H-lane segment) and its length
@@ -465,22 +503,7 @@ __device__ __forceinline__ void construct_ant_phased(const Instance& I, const in
   group_wait();
 
   WalkState w{start, 1, 0, 0ull, 0u, true};
-  const int s1 = max(1, n - NT * Cm::kC1);
-  const int s2 = max(s1, n - NT * Cm::kC2);
-  const int s3 = max(s2, n - NT * Cm::kC3);
-  eq1_phase<C, C, Cm::kC1, G, H, false, kPool>(I, ant, tg, seg, gs, bar_id, srow, ulist, start,
-                                                s1, w, lane_copy);
-  eq1_phase<C, Cm::kC1, Cm::kC2, G, H, true, kPool>(I, ant, tg, seg, gs, bar_id, srow, ulist,
-                                                     start, s2, w, lane_copy);
-  if constexpr (Cm::kC3 < Cm::kC2) {
-    eq1_phase<C, Cm::kC2, Cm::kC3, G, H, true, kPool>(I, ant, tg, seg, gs, bar_id, srow, ulist,
-                                                       start, s3, w, lane_copy);
-    eq1_phase<C, Cm::kC3, 0, G, H, true, kPool>(I, ant, tg, seg, gs, bar_id, srow, ulist, start,
-                                                 n, w, lane_copy);
-  } else {
-    eq1_phase<C, Cm::kC2, 0, G, H, true, kPool>(I, ant, tg, seg, gs, bar_id, srow, ulist, start,
-                                                 n, w, lane_copy);
-  }
+  eq1_phases<C, G, H, kPool, 0>(I, ant, tg, seg, gs, bar_id, srow, ulist, start, w, lane_copy);
   if (tg == 0) tour[n] = start;
   group_wait();
 

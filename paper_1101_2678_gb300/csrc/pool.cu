@@ -380,7 +380,12 @@ static int pool_rebuild(aco_pool* p) {
 // the class's tours twice on the pool stream and the second run is timed;
 // the fastest is kept for the class from then on.  Every tiling builds the
 // same tours (the selection is exact integer arithmetic), so the trial runs
-// change nothing: the step that follows rebuilds the same tours.
+// change nothing: the step that follows rebuilds the same tours.  A tiling
+// with warp segments (several ants per warp) must beat the fastest
+// whole-warp tiling by kSegmentMargin: timed alone a class gains from the
+// segments' fewer instructions per ant more than it does in the step, where
+// the other classes share the SMs (the n 897-1019 class of the batched
+// workload: 16-lane segments 0.5 % faster alone, 2 % slower in the step).
 static int pool_autotune(aco_pool* p) {
   // (warps per ant, lanes per ant, ants per CTA): CTA widths of 2-8 warps
   static const int kCand[][3] = {{1, 32, 4}, {1, 32, 2}, {1, 32, 8}, {2, 32, 2},
@@ -391,8 +396,9 @@ static int pool_autotune(aco_pool* p) {
   for (auto& c : p->classes) {
     if (e != cudaSuccess) break;
     if (c.nn || p->tuned.count(c.key)) continue;
-    float best_ms = 0.0f;
-    int bi = -1;
+    constexpr float kSegmentMargin = 0.95f;
+    float best_ms = 0.0f, warp_ms = 0.0f;
+    int bi = -1, bw = -1;  // fastest overall, fastest with whole warps
     const ConstructTiling d = batched_construct_tiling(c.max_n);
     const int ncand = (int)(sizeof kCand / sizeof kCand[0]);
     for (int i = 0; i < 2 * ncand && e == cudaSuccess; ++i) {
@@ -416,7 +422,13 @@ static int pool_autotune(aco_pool* p) {
         best_ms = ms;
         bi = i;
       }
+      if (e == cudaSuccess && t.H == 32 && (bw < 0 || ms < warp_ms)) {
+        warp_ms = ms;
+        bw = i;
+      }
     }
+    if (bi >= 0 && bw >= 0 && kCand[bi % ncand][1] != 32 && best_ms > kSegmentMargin * warp_ms)
+      bi = bw;
     if (e == cudaSuccess && bi >= 0) {
       const int* k = kCand[bi % ncand];
       p->tuned[c.key] = std::make_tuple(k[0], k[1], k[2], bi / ncand);
