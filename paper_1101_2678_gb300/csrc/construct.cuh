@@ -857,16 +857,16 @@ __global__ void __launch_bounds__(256) construct_items_kernel(const Instance* __
 }
 
 // The Eq. 1 walk with compaction (construct_phased.cuh), one group of H lanes
-// per ant.  Its three phases are inlined into one body; without a ceiling the
-// register allocator adds their needs up instead of sharing them (233
-// registers at C = 76, where phase 0 alone needs 128).  The ceilings were
-// chosen by measurement on the GB300: 128 from C = 44 (no spills); 80 at
-// C = 36 (one instance of n = 1002: 1.159 ms, against 1.186 ms at 64 or 72);
-// 64 up to C = 28 (a pool of the batched workload: 22.38 ms per step, against
-// 22.91 ms at 80).
+// (or two warps) per ant.  Its phases are inlined into one body; without a
+// ceiling the register allocator adds their needs up instead of sharing them
+// (233 registers at C = 76, where phase 0 alone needs 128).  The ceilings were
+// chosen by measurement on the GB300: 128 from C = 44 (no spills); 72 at
+// C = 36 (no spills; the batched step 0.9 % faster than at 80, one instance
+// of n = 1002 the same); 64 up to C = 28 (the batched step 22.38 ms against
+// 22.91 ms at 80; 56 spills and was 2.5 % slower).
 template <int C>
 struct PhasedRegs {
-  static constexpr int v = C <= 28 ? 64 : (C <= 36 ? 80 : 128);
+  static constexpr int v = C <= 28 ? 64 : (C <= 36 ? 72 : 128);
 };
 
 template <int C, int G, int H>
