@@ -51,6 +51,39 @@ def test_static_batch_equals_alone(aco, orc):
         assert np.array_equal(tau_a, ref["tau32"]) and len_a == ref["best_len"]
 
 
+def test_compacting_pool_zero_weights_equal_alone(aco, orc):
+    # rho = 1 leaves pheromone only on the last iteration's edges, so the
+    # compacted phases of the pool's construction (city-index list entries,
+    # one and two warps per ant) often meet the zero-weight rule; every
+    # instance must still match its run alone, and the smallest the oracle
+    ns = [520, 900, 1000, 2500]
+    insts = [I.clustered_instance(n, seed=40 + n, clusters=10, sigma=300, side=20000) for n in ns]
+    ms = [24] * len(ns)
+    seeds = [70 + i for i in range(len(ns))]
+    b = aco.aco_batch_create([x.dist for x in insts], ms, seeds, rho=1.0)
+    try:
+        aco.aco_pool_set_autotune(b, False)  # default tilings: the compacting walk
+        aco.aco_batch_iterate(b, 3)
+        for i, x in enumerate(insts):
+            g, h, c, _ = aco.aco_pool_tiling(b, i)
+            assert c >= 20 and (g, h) == ((1, 32) if x.n <= 2432 else (2, 32)), (i, g, h, c)
+            with aco.Colony(x.dist, ms[i], seed=seeds[i], rho=1.0) as col:
+                aco.aco_iterate(col.h, 3)
+                tau_a = aco.aco_get_pheromone(col.h, x.n)
+                tour_a, len_a = aco.aco_best_tour(col.h, x.n)
+            tau_b = aco.aco_pool_pheromone(b, i, x.n)
+            assert (tau_b == 0).mean() > 0.85, i
+            tour_b, len_b = aco.aco_batch_best(b, i, x.n)
+            assert len_b == len_a and np.array_equal(tour_b, tour_a), i
+            assert np.array_equal(tau_b, tau_a), i
+    finally:
+        aco.aco_batch_destroy(b)
+    ref = orc.run(insts[0].dist, ms[0], 3, seeds[0], rho=1.0)
+    with aco.Colony(insts[0].dist, ms[0], seed=seeds[0], rho=1.0) as col:
+        aco.aco_iterate(col.h, 3)
+        assert np.array_equal(aco.aco_get_pheromone(col.h, ns[0]), ref["tau32"])
+
+
 def test_coordinates_build_the_same_instance(aco, orc):
     inst = I.clustered_instance(333, seed=4)
     h = aco.aco_create_coords(inst.coords, 1.0, 2.0, 0.5, 64, 3)
