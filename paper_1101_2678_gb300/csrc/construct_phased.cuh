@@ -12,9 +12,10 @@
 //   phase 1  the unvisited cities, in ascending order, are listed in shared
 //            memory and dealt out C1 = 4*ceil(C/8) per lane (lane t takes
 //            entries [t*C1, t*C1 + C1)); each step reads the entries and
-//            then their weights from the staged row by index.  A visited
-//            slot's entry is set to the index of a float beside the row that
-//            stays 0, so these phases keep no tabu bits and mask nothing;
+//            then their weights from the staged row through them.  A visited
+//            slot's entry is pointed at a float beside the row that stays 0,
+//            so these phases keep no tabu bits and mask nothing (entries are
+//            byte offsets for a single instance, city indices in pools);
 //   phase 2  the same with C2 = 4*ceil(C/16) per lane;
 //   phase 3  the same with C3 = 4*ceil(C/32) per lane (when smaller than C2).
 // Phase p starts at the first step at which the unvisited cities fit in the
@@ -50,10 +51,10 @@ struct WalkState {
   bool waits_ok;
 };
 
-// Steps [w.s, s_end) of one phase.  CP: slots per lane.  kGather = false:
-// slot i of lane t is city t*C + i (phase 0); true: slot i holds the city
-// listed at ulist[t*CP + i].  CPN > 0: afterwards, list the unvisited cities
-// for a phase of CPN slots per lane.
+// Steps [w.s, s_end) of one phase.  CP: slots per thread.  kGather = false:
+// slot i of thread t is city t*C + i (phase 0); true: slot i holds the entry
+// ulist[t*CP + i] (its city's weight, or the zero slot once visited).  CPN > 0:
+// afterwards, list the unvisited cities for a phase of CPN slots per thread.
 template <int C, int CP, int CPN, int G, int H, bool kGather, bool kPool>
 __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, const int tg,
                                           const Seg<H> seg, GroupSmem* gs, const int bar_id,
@@ -63,7 +64,7 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
   static_assert(kGather || CP == C, "the direct phase reads whole chunks");
   static_assert(G == 1 || (G == 2 && H == 32), "two warps per ant use whole warps");
   constexpr int NT = G * H;  // threads per ant
-  constexpr int NW = (CP + 31) / 32;  // tabu words per lane
+  constexpr int NW = (CP + 31) / 32;  // tabu words per lane (direct phase)
   constexpr int KW = (CP + H - 1) / H;
   constexpr int KP = (!kPool && KW <= 2) ? 1 : (KW < 4 ? KW : 4);
   constexpr int K = KP < CP / 4 ? KP : CP / 4;
@@ -144,8 +145,6 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
       w.rwin = ((unsigned long long)x.x1 << 32) | x.x0;
     }
     const unsigned long long r = seg.shfl(w.rwin, off);
-    // Gather phases: the thread's list entries, read while the row is in
-    // flight (only this thread has written them since the last barrier).
     if (lane_copy) {
       group_wait();
     } else {
