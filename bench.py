@@ -489,6 +489,13 @@ def run_ours(args, w, rank, world, local):
         if rec:
             roof["traffic"] = rec["dram_bytes_per_launch"]
             roof["l2_bytes_per_launch"] = rec.get("l2_bytes_per_launch")
+            if rec.get("l2_bytes_per_launch"):
+                # L2 bytes the kernel moved (ncu lts__t_bytes, scaled to the
+                # full launch) per second of the launch timed here, against
+                # the same measured read peak
+                l2_gbs = rec["l2_bytes_per_launch"] / (con_ms / 1e3) / 1e9
+                roof["achieved_l2_traffic"] = l2_gbs
+                roof["frac_l2_traffic"] = l2_gbs / roof["peak"]
             roof["traffic_source"] = rec["source"]
             roof["ncu_capture"] = {"ants": rec["captured_ants"],
                                    "lts_throughput_pct": rec.get("lts_throughput_pct"),
