@@ -180,15 +180,34 @@ __device__ __forceinline__ void eq1_phase(const Instance& I, const int ant, cons
         v[i + 3] = entry_weight<kUnit>(row, e.y >> 16);
       }
     }
-    uint32_t m4[4] = {0u, 0u, 0u, 0u};
+    // The max pass.  A float max equals the integer max of the bit patterns
+    // for weights >= 0 (no NaN; subnormals kept: no flush to zero); it
+    // measured faster in the compacted phases and for direct chunks of 44
+    // cities or more (n = 2392 0.6 %, n = 1002 0.45 %), slower for a direct
+    // chunk of 36 (0.6 %).
+    constexpr bool kFloatMax = kGather || C >= 44;
+    uint32_t mx;
+    if constexpr (kFloatMax) {
+      float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int i = 0; i < CP; ++i) {
-      if constexpr (!kGather) {
-        if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+      for (int i = 0; i < CP; ++i) {
+        if constexpr (!kGather) {
+          if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+        }
+        m4[i & 3] = fmaxf(m4[i & 3], __uint_as_float(v[i]));
       }
-      m4[i & 3] = max(m4[i & 3], v[i]);
+      mx = seg.max_u32(__float_as_uint(fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]))));
+    } else {
+      uint32_t m4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int i = 0; i < CP; ++i) {
+        if constexpr (!kGather) {
+          if ((vis[i >> 5] >> (i & 31)) & 1u) v[i] = 0u;
+        }
+        m4[i & 3] = max(m4[i & 3], v[i]);
+      }
+      mx = seg.max_u32(max(max(m4[0], m4[1]), max(m4[2], m4[3])));
     }
-    uint32_t mx = seg.max_u32(max(max(m4[0], m4[1]), max(m4[2], m4[3])));
     if constexpr (G > 1) {
       if (hl == 0) gs->wmax[wg] = mx;
       group_wait();

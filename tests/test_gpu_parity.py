@@ -153,6 +153,27 @@ def test_compacting_walk_zero_weights(aco, orc_all_cores, n, lanes, warps):
     assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
 
 
+# rho = 0.9 for 60 iterations decays the trails nobody reinforces into the
+# subnormal range, so late in a tour the largest unvisited weight can be
+# subnormal: the max pass (a float max in the compacted phases and for direct
+# chunks of 44 or more) must keep it, as the oracle's integer max does.
+@pytest.mark.parametrize("n", [600, 1500])
+def test_compacting_walk_subnormal_weights(aco, orc_all_cores, n):
+    orc = orc_all_cores
+    inst = I.uniform_instance(n, 10000, seed=n + 3)
+    m, iters = 16, 60
+    ref = orc.run(inst.dist, m, iters, 9, rho=0.9)
+    with aco.Colony(inst.dist, m, seed=9, rho=0.9) as c:
+        aco.aco_iterate(c.h, iters)
+        tau = aco.aco_get_pheromone(c.h, n)
+        ch = aco.aco_choice_info(c.h, n)
+        tour, best = aco.aco_best_tour(c.h, n)
+    tiny = np.finfo(np.float32).tiny
+    assert ((ch > 0) & (ch < tiny)).sum() > n  # subnormal weights exist
+    assert np.array_equal(tau, ref["tau32"])
+    assert best == ref["best_len"] and np.array_equal(tour, ref["best_tour"])
+
+
 @pytest.mark.parametrize("wl,ants", [("n1002", 12), ("n2392", 6)])
 def test_full_size_first_iteration_sampled(aco, orc, wl, ants):
     w = getattr(I, "workload_" + wl)()
