@@ -246,16 +246,22 @@ struct Seg {
     return H == 32 ? b : (b >> (sub * H)) & ((1u << H) - 1u);
   }
   __device__ __forceinline__ uint32_t max_u32(uint32_t v) const {
-    if (H == 32) return __reduce_max_sync(FULL, v);
+    if constexpr (H == 32) {
+      return __reduce_max_sync(FULL, v);
+    } else {
 #pragma unroll
-    for (int o = H / 2; o > 0; o >>= 1) v = max(v, shfl_xor(v, o));
-    return v;
+      for (int o = H / 2; o > 0; o >>= 1) v = max(v, shfl_xor(v, o));
+      return v;
+    }
   }
   __device__ __forceinline__ uint32_t min_u32(uint32_t v) const {
-    if (H == 32) return __reduce_min_sync(FULL, v);
+    if constexpr (H == 32) {
+      return __reduce_min_sync(FULL, v);
+    } else {
 #pragma unroll
-    for (int o = H / 2; o > 0; o >>= 1) v = min(v, shfl_xor(v, o));
-    return v;
+      for (int o = H / 2; o > 0; o >>= 1) v = min(v, shfl_xor(v, o));
+      return v;
+    }
   }
   __device__ __forceinline__ unsigned long long inclusive_scan(unsigned long long x) const {
 #pragma unroll
